@@ -1,0 +1,299 @@
+"""QTT oracle: plain FP64 CPU reference for the QTT matrix x dense-vector
+product and the solves built on it.
+
+TEST INFRASTRUCTURE ONLY.  Only the test-suite, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import this package.  The CUDA
+library never links or calls it, and the two share no code: the only thing
+both sides read is the seeded input data from
+``paper_1511_06029_gb300.inputs``.
+
+The arithmetic lives in ``qtt_oracle.c`` (plain C, compiled with
+``-ffp-contract=off`` so that every multiply and add rounds separately, the
+same on x86-64 and aarch64).  This module only marshals numpy arrays.
+
+An operator is any object with ``.ranks`` (list of d+1 ints, ends equal to 1)
+and ``.cores`` (list of d float64 arrays shaped (r_k, 2, 2, r_{k+1}), index
+order [alpha_k][row bit i][column bit j][alpha_{k+1}]).  Vectors are numpy
+arrays of shape (N,) or (nrhs, N); element t of a vector is indexed least
+significant bit first, bit k belonging to core k (Sec. 2.1 and 2.4 of the
+paper: Matlab reshape order, finest level first).
+
+Function -> passage it follows:
+  apply, apply_ld   y = A x from the TT entry formula (Sec. 2.2, eq.
+                    TTdeccores; Sec. 3.1 matrix tensorisation), cores
+                    contracted last-to-first (Algorithm 2 runs first-to-last)
+  dense             A(i, j) as the chain of slice products (same passages)
+  dense_matvec      brute-force O(N^2) product
+  transpose         A^T: row and column bit swapped in every core
+  tt_sum            A + B by rank concatenation (Corollary 1, Sec. 3.3)
+  tt_product        A B core by core (Sec. 4.2, compressed product)
+  solve_direct      x = P f (Tables 1-2 "Solve": inverse applied to dense RHS)
+  solve_refine      x <- x + P (f - A x)  (mixed-precision refinement)
+  solve_gmres       right-preconditioned GMRES(m) (Sec. 5.3: QTT inverse of
+                    the preconditioned system used inside GMRES)
+  power_norm        ||K||_2 by power iteration on K^T K
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qtt_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libqtt_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+QO_OK, QO_EINVAL, QO_ENOMEM, QO_ENOTCONV = 0, 1, 2, 4
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C source into a shared library (plain gcc)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            I, L, P = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+            D = ctypes.c_double
+            sig = {
+                "qo_apply": [I, P, P, L, P, L, P, L, I],
+                "qo_apply_ld": [I, P, P, L, P, L, P, L, I],
+                "qo_dense": [I, P, P, P],
+                "qo_dense_matvec": [L, P, L, P, L, P, L],
+                "qo_transpose": [I, P, P, P],
+                "qo_sum": [I, P, P, P, P, P, P],
+                "qo_product": [I, P, P, P, P, P, P],
+                "qo_solve_direct": [I, P, P, L, P, P, I],
+                "qo_solve_refine": [I, D, P, P, P, P, L, P, P, D, I, P, P, I],
+                "qo_solve_gmres": [I, D, P, P, P, P, L, P, P, D, I, I, P, P, I],
+                "qo_power_norm": [I, P, P, P, I, D, P, P, I],
+                "qo_num_params": [I, P],
+            }
+            for name, args in sig.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st == QO_OK:
+        return
+    names = {QO_EINVAL: "invalid argument", QO_ENOMEM: "out of memory",
+             QO_ENOTCONV: "not converged"}
+    raise OracleError(f"oracle {what}: {names.get(st, st)}")
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _flat(op):
+    ranks = np.ascontiguousarray(np.asarray(op.ranks, dtype=np.int32))
+    d = len(ranks) - 1
+    for k, c in enumerate(op.cores):
+        if c.shape != (ranks[k], 2, 2, ranks[k + 1]):
+            raise OracleError(f"core {k} has shape {c.shape}, expected "
+                              f"{(ranks[k], 2, 2, ranks[k + 1])}")
+    flat = np.ascontiguousarray(
+        np.concatenate([np.asarray(c, dtype=np.float64).ravel() for c in op.cores]))
+    return d, ranks, flat
+
+
+class Op:
+    """Minimal operator container for results built by the oracle."""
+
+    def __init__(self, ranks, cores):
+        self.ranks = [int(v) for v in ranks]
+        self.cores = cores
+
+    @property
+    def d(self):
+        return len(self.ranks) - 1
+
+
+def _unflat(ranks, flat):
+    cores, off = [], 0
+    for k in range(len(ranks) - 1):
+        n = 4 * ranks[k] * ranks[k + 1]
+        cores.append(flat[off:off + n].reshape(ranks[k], 2, 2, ranks[k + 1]).copy())
+        off += n
+    return Op(ranks, cores)
+
+
+def _as_block(x, N):
+    x = np.asarray(x, dtype=np.float64)
+    single = x.ndim == 1
+    xb = np.ascontiguousarray(x.reshape(1, -1) if single else x)
+    if xb.shape[1] != N:
+        raise OracleError(f"vector length {xb.shape[1]} != N = {N}")
+    return xb, single
+
+
+def apply(op, x, threads: int = 0, long_double: bool = False) -> np.ndarray:
+    """y = A x (FP64; ``long_double=True`` carries the sweep in long double)."""
+    lib = _load()
+    d, ranks, flat = _flat(op)
+    N = 1 << d
+    xb, single = _as_block(x, N)
+    y = np.empty_like(xb)
+    fn = lib.qo_apply_ld if long_double else lib.qo_apply
+    _check(fn(d, _ptr(ranks), _ptr(flat), xb.shape[0], _ptr(xb), N, _ptr(y), N,
+              threads), "apply")
+    return y[0] if single else y
+
+
+def dense(op) -> np.ndarray:
+    """Dense N x N reconstruction (d <= 13)."""
+    lib = _load()
+    d, ranks, flat = _flat(op)
+    N = 1 << d
+    A = np.empty((N, N), dtype=np.float64)
+    _check(lib.qo_dense(d, _ptr(ranks), _ptr(flat), _ptr(A)), "dense")
+    return A
+
+
+def dense_matvec(A, x) -> np.ndarray:
+    lib = _load()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    N = A.shape[0]
+    xb, single = _as_block(x, N)
+    y = np.empty_like(xb)
+    _check(lib.qo_dense_matvec(N, _ptr(A), xb.shape[0], _ptr(xb), N, _ptr(y), N),
+           "dense_matvec")
+    return y[0] if single else y
+
+
+def transpose(op) -> Op:
+    lib = _load()
+    d, ranks, flat = _flat(op)
+    out = np.empty_like(flat)
+    _check(lib.qo_transpose(d, _ptr(ranks), _ptr(flat), _ptr(out)), "transpose")
+    return _unflat(list(ranks), out)
+
+
+def tt_sum(A, B) -> Op:
+    lib = _load()
+    d, ra, fa = _flat(A)
+    d2, rb, fb = _flat(B)
+    if d != d2:
+        raise OracleError("sum of operators with different d")
+    rc = np.zeros(d + 1, dtype=np.int32)
+    rcl = [1] + [int(ra[k] + rb[k]) for k in range(1, d)] + [1]
+    n = sum(4 * rcl[k] * rcl[k + 1] for k in range(d))
+    out = np.zeros(n, dtype=np.float64)
+    _check(lib.qo_sum(d, _ptr(ra), _ptr(fa), _ptr(rb), _ptr(fb), _ptr(rc), _ptr(out)),
+           "sum")
+    return _unflat(list(rc), out)
+
+
+def tt_product(A, B) -> Op:
+    lib = _load()
+    d, ra, fa = _flat(A)
+    d2, rb, fb = _flat(B)
+    if d != d2:
+        raise OracleError("product of operators with different d")
+    rc = np.zeros(d + 1, dtype=np.int32)
+    rcl = [int(ra[k] * rb[k]) for k in range(d + 1)]
+    n = sum(4 * rcl[k] * rcl[k + 1] for k in range(d))
+    out = np.zeros(n, dtype=np.float64)
+    _check(lib.qo_product(d, _ptr(ra), _ptr(fa), _ptr(rb), _ptr(fb), _ptr(rc), _ptr(out)),
+           "product")
+    return _unflat(list(rc), out)
+
+
+def solve_direct(P, f, threads: int = 0) -> np.ndarray:
+    return apply(P, f, threads=threads)
+
+
+def _solve_common(K, P, f):
+    d = len(K.ranks) - 1 if K is not None else len(P.ranks) - 1
+    N = 1 << d
+    fb, single = _as_block(f, N)
+    if K is not None:
+        _, rk, gk = _flat(K)
+    else:
+        rk, gk = np.ones(d + 1, dtype=np.int32), None
+    if P is not None:
+        _, rp, gp = _flat(P)
+    else:
+        rp, gp = np.ones(d + 1, dtype=np.int32), None
+    return d, N, fb, single, rk, gk, rp, gp
+
+
+def _gptr(g):
+    return None if g is None else _ptr(g)
+
+
+def solve_refine(K, P, f, a: float = 1.0, tol: float = 1e-13,
+                 max_iter: int = 200, threads: int = 0, raise_on_fail=True):
+    """Refinement for (a I + K) x = f: x_0 = P f, x <- x + P (f - A x).
+    Returns (x, iters, relres)."""
+    lib = _load()
+    d, N, fb, single, rk, gk, rp, gp = _solve_common(K, P, f)
+    x = np.zeros_like(fb)
+    nr = fb.shape[0]
+    iters = np.zeros(nr, dtype=np.int32)
+    rel = np.zeros(nr, dtype=np.float64)
+    st = lib.qo_solve_refine(d, a, _ptr(rk), _gptr(gk), _ptr(rp), _gptr(gp), nr,
+                             _ptr(fb), _ptr(x), tol, max_iter, _ptr(iters), _ptr(rel),
+                             threads)
+    if st != QO_ENOTCONV or raise_on_fail:
+        _check(st, "refine")
+    return (x[0] if single else x), iters, rel
+
+
+def solve_gmres(K, P, f, a: float = 1.0, tol: float = 1e-13, restart: int = 30,
+                max_iter: int = 500, threads: int = 0, raise_on_fail=True):
+    """Right-preconditioned GMRES(restart) for (a I + K) x = f, x_0 = 0.
+    Returns (x, iters, relres)."""
+    lib = _load()
+    d, N, fb, single, rk, gk, rp, gp = _solve_common(K, P, f)
+    x = np.zeros_like(fb)
+    nr = fb.shape[0]
+    iters = np.zeros(nr, dtype=np.int32)
+    rel = np.zeros(nr, dtype=np.float64)
+    st = lib.qo_solve_gmres(d, a, _ptr(rk), _gptr(gk), _ptr(rp), _gptr(gp), nr,
+                            _ptr(fb), _ptr(x), tol, restart, max_iter, _ptr(iters),
+                            _ptr(rel), threads)
+    if st != QO_ENOTCONV or raise_on_fail:
+        _check(st, "gmres")
+    return (x[0] if single else x), iters, rel
+
+
+def power_norm(op, v0, max_iter: int = 100, rtol: float = 1e-6, threads: int = 0):
+    """||A||_2 estimate by power iteration on A^T A from v0.
+    Returns (sigma, iterations)."""
+    lib = _load()
+    d, ranks, flat = _flat(op)
+    v0 = np.ascontiguousarray(v0, dtype=np.float64)
+    sigma = ctypes.c_double(0.0)
+    it = ctypes.c_int(0)
+    _check(lib.qo_power_norm(d, _ptr(ranks), _ptr(flat), _ptr(v0), max_iter, rtol,
+                             ctypes.byref(sigma), ctypes.byref(it), threads),
+           "power_norm")
+    return sigma.value, it.value

@@ -1,0 +1,245 @@
+"""Pins for the CPU oracle, none of which reuse the oracle's own code path.
+
+Each test checks the oracle against something the paper or mathematics fixes:
+a hand-derived example, numpy's Kronecker product, brute force by numpy
+matmul, integer-exact arithmetic, algebraic identities, and a long-double
+re-run bounding its rounding error.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1511_06029_gb300 import inputs
+from conftest import rel_l2
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_hand_example():
+    vals = {"A": []}
+    with open(os.path.join(GOLDEN, "hand_d2_rank2.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *nums = line.split()
+            nums = [float(v) for v in nums]
+            if key == "A":
+                vals["A"].append(nums)
+            else:
+                vals[key] = nums
+    c0 = np.array(vals["core0"]).reshape(1, 2, 2, 2)
+    c1 = np.array(vals["core1"]).reshape(2, 2, 2, 1)
+    op = inputs.QTTData([1, 2, 1], [c0, c1])
+    return op, np.array(vals["A"]), np.array(vals["x"]), np.array(vals["y"])
+
+
+def test_hand_example(oracle_mod):
+    """Sec. 2.2 entry formula with the Sec. 2.1 index order, worked by hand."""
+    op, A, x, y = _read_hand_example()
+    assert np.array_equal(oracle_mod.dense(op), A)
+    assert np.array_equal(oracle_mod.apply(op, x), y)
+
+
+@pytest.mark.parametrize("k", [0, 1, 3])
+def test_index_convention_shift(oracle_mod, k):
+    """Least-significant-bit-first convention: a rank-1 operator whose core k
+    is [[0, 1], [0, 0]] (others I_2) maps j = i + 2^k onto i for every i with
+    bit k clear, and nothing else."""
+    d = 5
+    mats = [np.eye(2)] * d
+    mats[k] = np.array([[0.0, 1.0], [0.0, 0.0]])
+    A = oracle_mod.dense(inputs.kronecker(mats))
+    N = 1 << d
+    expect = np.zeros((N, N))
+    for i in range(N):
+        if not (i >> k) & 1:
+            expect[i, i + (1 << k)] = 1.0
+    assert np.array_equal(A, expect)
+
+
+@pytest.mark.parametrize("d", [1, 2, 7, 12])
+def test_identity_is_bitwise(oracle_mod, d):
+    """All ranks 1, every core I_2 (identity has QTT rank 1, Sec. 3.3):
+    y = x exactly."""
+    x = inputs.gaussian_rhs(1 << d, 3, seed=d)
+    assert np.array_equal(oracle_mod.apply(inputs.identity(d), x), x)
+
+
+@pytest.mark.parametrize("d", [1, 3, 6])
+def test_kronecker_matches_numpy(oracle_mod, d):
+    """Rank-1 QTT = G_{d-1} kron ... kron G_0 (bit 0 fastest), checked
+    against numpy.kron, for both the dense form and the apply."""
+    rng = np.random.default_rng(10 + d)
+    mats = [rng.standard_normal((2, 2)) for _ in range(d)]
+    op = inputs.kronecker(mats)
+    K = np.array([[1.0]])
+    for m in mats:
+        K = np.kron(m, K)
+    A = oracle_mod.dense(op)
+    assert np.allclose(A, K, rtol=1e-14, atol=1e-15)
+    x = rng.standard_normal(1 << d)
+    assert rel_l2(oracle_mod.apply(op, x), K @ x) <= 1e-14
+
+
+@pytest.mark.parametrize("d,rmax,seed", [(4, 3, 1), (8, 6, 2), (10, 16, 3), (12, 4, 4)])
+def test_dense_bruteforce(oracle_mod, d, rmax, seed):
+    """Sweep apply vs the dense reconstruction times x (numpy matmul)."""
+    op = inputs.random_cores(d, inputs.random_ranks(d, rmax, seed), seed)
+    A = oracle_mod.dense(op)
+    x = inputs.gaussian_rhs(1 << d, 2, seed + 100)
+    y_dense = x @ A.T
+    assert rel_l2(oracle_mod.apply(op, x), y_dense) <= 1e-13
+    assert rel_l2(oracle_mod.dense_matvec(A, x), y_dense) <= 1e-14
+
+
+def test_dense_entries_by_slice_products(oracle_mod):
+    """qo_dense against entries formed here by explicit numpy slice products
+    (the entry formula, no shared code)."""
+    d = 9
+    op = inputs.random_cores(d, inputs.random_ranks(d, 7, 5), 5)
+    A = oracle_mod.dense(op)
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        i, j = (int(v) for v in rng.integers(0, 1 << d, size=2))
+        v = np.ones((1, 1))
+        for k in range(d):
+            v = v @ op.cores[k][:, (i >> k) & 1, (j >> k) & 1, :]
+        assert abs(A[i, j] - v[0, 0]) <= 1e-13 * max(1.0, abs(v[0, 0]))
+
+
+@pytest.mark.parametrize("d,rmax,seed", [(6, 4, 1), (10, 4, 2), (12, 3, 3)])
+def test_integer_exact(oracle_mod, d, rmax, seed):
+    """Cores in {-1, 0, 1} and integer x: every intermediate is an integer
+    below 2^53, so the sweep and the brute-force product agree bitwise."""
+    op = inputs.random_cores(d, inputs.random_ranks(d, rmax, seed), seed, integer=True)
+    x = np.random.default_rng(seed).integers(-8, 9, size=(2, 1 << d)).astype(np.float64)
+    A = oracle_mod.dense(op)
+    assert np.array_equal(oracle_mod.apply(op, x), x @ A.T)
+
+
+def test_long_double_bound(oracle_mod):
+    """The FP64 sweep is within 1e-14 (relative L2) of the same sweep in
+    long double: the oracle's own rounding is far below the 1e-12 parity
+    tolerance it judges."""
+    op = inputs.synthetic_operator(14, 32, 2)
+    x = inputs.gaussian_rhs(op.N, 1, 3)[0]
+    y = oracle_mod.apply(op, x)
+    yl = oracle_mod.apply(op, x, long_double=True)
+    assert rel_l2(y, yl) <= 1e-14
+
+
+def test_sum_and_product(oracle_mod):
+    """apply(A + B) = apply(A) + apply(B); apply(A B, x) = A (B x); dense
+    forms against numpy sums and matmuls (rank addition and the core-wise
+    product, Sec. 3.3 and Sec. 4.2)."""
+    d = 7
+    A = inputs.random_cores(d, inputs.random_ranks(d, 4, 11), 11)
+    B = inputs.random_cores(d, inputs.random_ranks(d, 3, 12), 12)
+    S = oracle_mod.tt_sum(A, B)
+    Pm = oracle_mod.tt_product(A, B)
+    DA, DB = oracle_mod.dense(A), oracle_mod.dense(B)
+    assert np.allclose(oracle_mod.dense(S), DA + DB, rtol=1e-13, atol=1e-12)
+    assert rel_l2(oracle_mod.dense(Pm), DA @ DB) <= 1e-13
+    x = inputs.gaussian_rhs(1 << d, 1, 13)[0]
+    assert rel_l2(oracle_mod.apply(S, x), oracle_mod.apply(A, x) + oracle_mod.apply(B, x)) <= 1e-13
+    assert rel_l2(oracle_mod.apply(Pm, x), oracle_mod.apply(A, oracle_mod.apply(B, x))) <= 1e-13
+    assert S.ranks == [1] + [A.ranks[k] + B.ranks[k] for k in range(1, d)] + [1]
+    assert Pm.ranks == [A.ranks[k] * B.ranks[k] for k in range(d + 1)]
+
+
+def test_transpose_adjoint(oracle_mod):
+    """dense(A^T) = dense(A)^T and <y, A x> = <A^T y, x>."""
+    d = 8
+    A = inputs.random_cores(d, inputs.random_ranks(d, 5, 21), 21)
+    AT = oracle_mod.transpose(A)
+    assert np.array_equal(oracle_mod.dense(AT), oracle_mod.dense(A).T)
+    x, y = inputs.gaussian_rhs(1 << d, 2, 22)
+    lhs = float(y @ oracle_mod.apply(A, x))
+    rhs = float(oracle_mod.apply(AT, y) @ x)
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+
+
+def test_multiple_rhs_are_independent(oracle_mod):
+    op = inputs.synthetic_operator(9, 8, 1)
+    X = inputs.gaussian_rhs(op.N, 4, 2)
+    Y = oracle_mod.apply(op, X)
+    for c in range(4):
+        assert np.array_equal(Y[c], oracle_mod.apply(op, X[c]))
+
+
+def test_power_norm_matches_lapack(oracle_mod):
+    op = inputs.random_cores(7, inputs.random_ranks(7, 4, 31), 31)
+    v0 = np.random.default_rng(1).standard_normal(op.N)
+    s, _ = oracle_mod.power_norm(op, v0, max_iter=2000, rtol=1e-13)
+    ref = np.linalg.norm(oracle_mod.dense(op), 2)
+    assert abs(s - ref) <= 1e-6 * ref
+
+
+# ------------------------------------------------------------------ solves
+def _small_solve_problem(d=8):
+    K = inputs.random_cores(d, inputs.random_ranks(d, 4, 41), 41)
+    return K
+
+
+def _scaled(oracle_mod, K, target=0.5):
+    s = np.linalg.norm(oracle_mod.dense(K), 2)
+    return K.scaled(target / s)
+
+
+def test_gmres_matches_dense_solve(oracle_mod):
+    """GMRES(m) without and with a preconditioner reaches the LAPACK
+    solution of the dense (a I + K) x = f."""
+    d = 8
+    K = _scaled(oracle_mod, _small_solve_problem(d), 0.9)
+    A = np.eye(1 << d) + oracle_mod.dense(K)
+    f = inputs.gaussian_rhs(1 << d, 2, 42)
+    xs = np.linalg.solve(A, f.T).T
+    x, it, rel = oracle_mod.solve_gmres(K, None, f, a=1.0, tol=1e-13, restart=10,
+                                        max_iter=400)
+    assert rel_l2(x, xs) <= 1e-11 and (rel <= 1e-13).all()
+    P = inputs.neumann_preconditioner_unrounded(K)
+    x2, it2, rel2 = oracle_mod.solve_gmres(K, P, f, a=1.0, tol=1e-13, restart=30)
+    assert rel_l2(x2, xs) <= 1e-11
+    assert it2.max() < it.max()
+
+
+def test_gmres_zero_rhs(oracle_mod):
+    K = _scaled(oracle_mod, _small_solve_problem(6))
+    x, it, rel = oracle_mod.solve_gmres(K, None, np.zeros(64), a=1.0)
+    assert np.array_equal(x, np.zeros(64)) and it[0] == 0
+
+
+def test_refine_contracts_like_neumann(oracle_mod):
+    """With the unrounded P = I - K + K^2, the error of refinement contracts by
+    the error operator -K^3 each step (Neumann series): iterations needed for
+    1e-13 are bounded by ceil(13 / -log10 ||K^3||) + 1."""
+    d = 8
+    K = _scaled(oracle_mod, _small_solve_problem(d), 0.5)
+    P = inputs.neumann_preconditioner_unrounded(K)
+    DK = oracle_mod.dense(K)
+    E = np.eye(1 << d) - oracle_mod.dense(P) @ (np.eye(1 << d) + DK)
+    assert np.allclose(E, -DK @ DK @ DK, atol=1e-14)
+    f = inputs.gaussian_rhs(1 << d, 1, 43)[0]
+    x, it, rel = oracle_mod.solve_refine(K, P, f, a=1.0, tol=1e-13)
+    xs = np.linalg.solve(np.eye(1 << d) + DK, f)
+    assert rel_l2(x, xs) <= 1e-12
+    c = np.linalg.norm(DK @ DK @ DK, 2)
+    assert it[0] <= int(np.ceil(13 / -np.log10(c))) + 2
+
+
+def test_refine_not_converged_reports(oracle_mod):
+    K = _scaled(oracle_mod, _small_solve_problem(6), 0.5)
+    f = inputs.gaussian_rhs(64, 1, 44)[0]
+    x, it, rel = oracle_mod.solve_refine(K, None, f, a=1.0, tol=1e-13, max_iter=1,
+                                         raise_on_fail=False)
+    assert it[0] == 1 and rel[0] > 1e-13
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.solve_refine(K, None, f, a=1.0, tol=1e-13, max_iter=1)
+
+
+def test_direct_is_apply(oracle_mod):
+    P = inputs.synthetic_operator(9, 8, 3)
+    f = inputs.gaussian_rhs(P.N, 2, 4)
+    assert np.array_equal(oracle_mod.solve_direct(P, f), oracle_mod.apply(P, f))
