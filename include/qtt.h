@@ -1,0 +1,187 @@
+/*
+ * qtt.h -- C-ABI of libqtt: QTT matrix x dense-vector products on one GB300
+ * GPU (sm_103a), and the solves built on them.
+ *
+ * The operation is the "matrix-vector product for an uncompressed vector" of
+ * Corona, Rahimian and Zorin, "A Tensor-Train accelerated solver for integral
+ * equations in complex geometries" (Sec. 4.2, Algorithm 2): a matrix A of
+ * size 2^d x 2^d held in quantized tensor-train (QTT) format is applied to
+ * dense vectors of length N = 2^d by contracting one core at a time.
+ *
+ * Conventions used by every entry point:
+ *   - Cores.  A QTT matrix has d cores; core k (k = 0..d-1) is
+ *     G_k(alpha_k, i_k, j_k, alpha_{k+1}) with ranks ranks[k], ranks[k+1]
+ *     and ranks[0] = ranks[d] = 1 (Sec. 2.2, eq. (TTdeccores) and the dummy
+ *     ranks; matrix cores on the product tree with b_k = (i_k, j_k),
+ *     Sec. 3.1).  They are passed as ONE host array of doubles holding the
+ *     cores one after another, each in C order
+ *     [ranks[k]][2 (row bit i_k)][2 (column bit j_k)][ranks[k+1]].
+ *   - Index.  Element t of a vector is indexed least-significant bit first:
+ *     t = sum_k t_k 2^k, bit k belonging to core k (the paper's Matlab
+ *     reshape order, Sec. 2.1, with the finest tree level first, Sec. 2.4).
+ *     A(i, j) = G_0[i_0, j_0] G_1[i_1, j_1] ... G_{d-1}[i_{d-1}, j_{d-1}].
+ *   - Vectors.  nrhs vectors of length N stored one after another with
+ *     leading dimension ld >= N elements (column-major N x nrhs), in DEVICE
+ *     memory owned by the caller unless an entry point says otherwise.
+ *   - Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Calls are asynchronous on that stream unless stated.
+ *   - Errors.  No exception crosses the ABI.  Every size and pointer is
+ *     validated before any launch; invalid input returns QTT_ERR_INVALID_ARG
+ *     and launches nothing.  Device memory is checked against free memory
+ *     before allocation and a shortfall returns QTT_ERR_OOM.  A CUDA error
+ *     returns QTT_ERR_CUDA (the message is kept for qtt_last_error()).
+ *   - Threads.  Distinct operators may be used from distinct threads.  One
+ *     operator may be applied concurrently on several streams: it is
+ *     read-only after qtt_create.
+ */
+#ifndef QTT_H_
+#define QTT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qtt_op qtt_op; /* opaque; cores resident in device memory */
+
+typedef enum {
+  QTT_OK = 0,
+  QTT_ERR_INVALID_ARG = 1,
+  QTT_ERR_OOM = 2,
+  QTT_ERR_CUDA = 3,
+  QTT_ERR_NOT_CONVERGED = 4,
+  QTT_ERR_TIMEOUT = 5,
+  QTT_ERR_UNSUPPORTED = 6
+} qtt_status;
+
+/* Element / arithmetic types.  QTT_TF32 names FP32 storage with operands
+ * rounded to TF32 (round to nearest) before each multiply. */
+typedef enum { QTT_F64 = 0, QTT_F32 = 1, QTT_TF32 = 2, QTT_BF16 = 3 } qtt_dtype;
+
+/* Bits of `precision_mask` in qtt_create: which packed copies of the cores
+ * to build besides FP64 (always built). */
+#define QTT_PACK_F32 (1u << 1)
+#define QTT_PACK_TF32 (1u << 2)
+#define QTT_PACK_BF16 (1u << 3)
+
+/* qtt_create -- copy a QTT matrix to the device (Algorithm 2, step 5: each
+ * core is permuted once into the (2 r_{k+1}) x (2 r_k) matrix M_k that the
+ * contraction multiplies; here that packing happens once, at creation).
+ *   out    : receives the operator handle (set to NULL on failure).
+ *   d      : number of cores, 1 <= d <= 30.
+ *   ranks  : host array of d+1 ints, ranks[0] = ranks[d] = 1, 1 <= ranks[k]
+ *            <= 4096.
+ *   cores  : host array, sum_k 4 ranks[k] ranks[k+1] doubles (layout above).
+ *            Copied; the caller keeps ownership.
+ *   precision_mask : QTT_PACK_* bits for the reduced-precision copies.
+ *   stream : stream for the uploads; the call returns after they finish.
+ * Errors: QTT_ERR_INVALID_ARG (bad d, ranks, NULL pointers),
+ *         QTT_ERR_OOM, QTT_ERR_CUDA. */
+qtt_status qtt_create(qtt_op **out, int d, const int *ranks,
+                      const double *cores, unsigned precision_mask,
+                      void *stream);
+
+/* qtt_destroy -- free the operator's device memory after all work queued on
+ * the streams it was used on has finished.  NULL is a no-op. */
+qtt_status qtt_destroy(qtt_op *A);
+
+/* Queries (host-side, no device work). */
+int qtt_op_d(const qtt_op *A);
+int qtt_op_rank(const qtt_op *A, int k); /* ranks[k], 0 <= k <= d, else -1 */
+/* 4 N sum_k r_k r_{k+1}: floating-point operations of one apply per right-
+ * hand side (Sec. 4.2: 2 m_k r_{k+1} r_k N per core, m_k = n_k = 2). */
+double qtt_op_flops(const qtt_op *A);
+
+/* qtt_apply -- y = A x for nrhs right-hand sides (Algorithm 2, the
+ * uncompressed-vector product).  The sweep runs over k = 0..d-1; step k
+ * contracts column bit j_k and rank alpha_k of the intermediate with core k
+ * and produces row bit i_k and rank alpha_{k+1} (the column merge, the
+ * product phi_k = M_k b_k and the row split of Algorithm 2 fused: the
+ * merge and split are addressing only).
+ *   x, y     : device pointers, N x nrhs, leading dimension ld (elements),
+ *              element type io_dtype.  x and y must not overlap.
+ *   nrhs     : >= 0 (0 is a no-op).
+ *   ld       : >= N.
+ *   io_dtype : element type of x and y.
+ *   compute  : arithmetic of the contraction: QTT_F64 (FP64 multiply-adds),
+ *              QTT_F32 (FP32), QTT_TF32 (TF32 operands, FP32 accumulate) or
+ *              QTT_BF16 (BF16 cores and intermediates, FP32 accumulate).
+ *              The operator must have been created with the matching
+ *              QTT_PACK_* bit for the reduced precisions.
+ *   stream   : cudaStream_t.
+ * Scratch for the intermediate (max_k r_k x N x nrhs elements, two
+ * buffers) is taken stream-ordered from a pool owned by the library.
+ * Errors: QTT_ERR_INVALID_ARG, QTT_ERR_UNSUPPORTED (combination not built),
+ *         QTT_ERR_OOM, QTT_ERR_CUDA. */
+qtt_status qtt_apply(const qtt_op *A, const void *x, void *y, int64_t nrhs,
+                     int64_t ld, qtt_dtype io_dtype, qtt_dtype compute,
+                     void *stream);
+
+/* qtt_residual -- r = f - (a x + K x), all FP64, the forward residual of the
+ * second-kind system (a I + K) x = f (Sec. 3, eq. (nystrom): A = a I +
+ * B K W C), with the subtraction fused into the last core step of the K
+ * apply.  f, x, r: device FP64, N x nrhs, leading dimension ld; r must not
+ * overlap f or x.  Errors as qtt_apply. */
+qtt_status qtt_residual(const qtt_op *K, double a, const double *f,
+                        const double *x, double *r, int64_t nrhs, int64_t ld,
+                        void *stream);
+
+/* ---------------------------------------------------------------- solves */
+typedef enum {
+  QTT_SOLVE_DIRECT = 0, /* x = P f: a QTT inverse used as a direct solver
+                           (Tables 1-2, "Solve" column).  K unused. */
+  QTT_SOLVE_GMRES = 1,  /* right-preconditioned GMRES(restart) with P
+                           (Sec. 5.3: QTT preconditioner inside GMRES). */
+  QTT_SOLVE_REFINE = 2  /* iterative refinement x <- x + P (f - (a I + K) x)
+                           with the residual in FP64 and P applied in
+                           prm->precond_compute. */
+} qtt_solve_kind;
+
+typedef struct {
+  qtt_solve_kind kind;
+  double a;              /* A = a I + K */
+  double tol;            /* stop when ||f - A x||_2 <= tol ||f||_2 */
+  int restart;           /* GMRES cycle length m (>= 1) */
+  int max_iter;          /* cap on P applications (REFINE) or Arnoldi steps */
+  qtt_dtype precond_compute; /* arithmetic of the P applies */
+} qtt_solve_params;
+
+typedef struct {
+  int iters;           /* P applications (REFINE), Arnoldi steps (GMRES) */
+  double rel_residual; /* final ||f - A x|| / ||f||, FP64 */
+  qtt_status status;   /* QTT_OK or QTT_ERR_NOT_CONVERGED */
+} qtt_solve_info;
+
+/* qtt_solve -- solve (a I + K) x = f for nrhs right-hand sides.
+ *   K     : forward operator (may be NULL for DIRECT).
+ *   P     : preconditioner / approximate inverse (NULL = identity; required
+ *           for DIRECT).
+ *   f, x  : device FP64, N x nrhs, leading dimension ld.  x is output only
+ *           (the initial guess is 0 for GMRES, P f for REFINE).
+ *   info  : host array of nrhs entries, filled on return.
+ * The call synchronises `stream` (convergence tests read one norm per RHS
+ * and iteration back to the host).  Returns QTT_ERR_NOT_CONVERGED if any
+ * right-hand side missed tol within max_iter (x holds the last iterate).
+ * Scratch (Krylov basis (restart+1) x N x nrhs FP64 for GMRES) comes from
+ * the library's pool; QTT_ERR_OOM if it does not fit. */
+qtt_status qtt_solve(const qtt_op *K, const qtt_op *P, const double *f,
+                     double *x, int64_t nrhs, int64_t ld,
+                     const qtt_solve_params *prm, qtt_solve_info *info,
+                     void *stream);
+
+/* ------------------------------------------------------------ diagnostics */
+const char *qtt_status_string(qtt_status s);
+/* Message of the last failing call on this thread ("" if none). */
+const char *qtt_last_error(void);
+/* Synchronise `stream` and report device-side errors (QTT_ERR_CUDA for a
+ * sticky CUDA error, QTT_ERR_TIMEOUT if a bounded wait in a library kernel
+ * gave up). */
+qtt_status qtt_sync_status(void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTT_H_ */

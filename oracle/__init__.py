@@ -23,6 +23,7 @@ Function -> passage it follows:
                     TTdeccores; Sec. 3.1 matrix tensorisation), cores
                     contracted last-to-first (Algorithm 2 runs first-to-last)
   dense             A(i, j) as the chain of slice products (same passages)
+  entries           single A(i, j), same formula, for full-size samples
   dense_matvec      brute-force O(N^2) product
   transpose         A^T: row and column bit swapped in every core
   tt_sum            A + B by rank concatenation (Corollary 1, Sec. 3.3)
@@ -91,6 +92,7 @@ def _load():
                 "qo_solve_gmres": [I, D, P, P, P, P, L, P, P, D, I, I, P, P, I],
                 "qo_power_norm": [I, P, P, P, I, D, P, P, I],
                 "qo_num_params": [I, P],
+                "qo_entries": [I, P, P, L, P, P, P],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -175,6 +177,18 @@ def dense(op) -> np.ndarray:
     A = np.empty((N, N), dtype=np.float64)
     _check(lib.qo_dense(d, _ptr(ranks), _ptr(flat), _ptr(A)), "dense")
     return A
+
+
+def entries(op, I, J) -> np.ndarray:
+    """A(I[n], J[n]) for index arrays I, J (entry formula, O(d r^2) each)."""
+    lib = _load()
+    d, ranks, flat = _flat(op)
+    I = np.ascontiguousarray(I, dtype=np.int64)
+    J = np.ascontiguousarray(J, dtype=np.int64)
+    out = np.empty(I.shape[0], dtype=np.float64)
+    _check(lib.qo_entries(d, _ptr(ranks), _ptr(flat), I.shape[0], _ptr(I), _ptr(J),
+                          _ptr(out)), "entries")
+    return out
 
 
 def dense_matvec(A, x) -> np.ndarray:

@@ -530,3 +530,41 @@ int qo_power_norm(int d, const int *r, const double *G, const double *v0,
   free(GT); free(v); free(u); free(w);
   return st;
 }
+
+/* Single entries A(I[n], J[n]) by the entry formula: the chain of slice
+ * products G_0[i_0, j_0] ... G_{d-1}[i_{d-1}, j_{d-1}] (Sec. 2.2), evaluated
+ * left to right; O(d r^2) per entry, so entries of a full-size operator can
+ * be checked one by one. */
+int qo_entries(int d, const int *r, const double *G, int64_t n,
+               const int64_t *I, const int64_t *J, double *out) {
+  int st = check_tt(d, r);
+  if (st) return st;
+  int rmax = 1;
+  for (int k = 0; k <= d; ++k)
+    if (r[k] > rmax) rmax = r[k];
+  double *v = (double *)malloc(sizeof(double) * rmax);
+  double *w = (double *)malloc(sizeof(double) * rmax);
+  if (!v || !w) {
+    free(v);
+    free(w);
+    return QO_ENOMEM;
+  }
+  for (int64_t e = 0; e < n; ++e) {
+    v[0] = 1.0;
+    for (int k = 0; k < d; ++k) {
+      const double *Gk = G + core_offset(r, k);
+      const int ra = r[k], rb = r[k + 1];
+      const int i = (int)((I[e] >> k) & 1), j = (int)((J[e] >> k) & 1);
+      for (int b = 0; b < rb; ++b) {
+        double s = 0.0;
+        for (int a = 0; a < ra; ++a) s += v[a] * Gk[((a * 2 + i) * 2 + j) * rb + b];
+        w[b] = s;
+      }
+      for (int b = 0; b < rb; ++b) v[b] = w[b];
+    }
+    out[e] = v[0];
+  }
+  free(v);
+  free(w);
+  return QO_OK;
+}

@@ -1,0 +1,333 @@
+// C-ABI of libqtt: operator lifetime, argument validation, scratch pool and
+// dispatch of the apply to the kernels.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "qtt_internal.h"
+
+namespace qtt {
+
+static thread_local std::string g_last_error;
+
+qtt_status fail(qtt_status s, const std::string &msg) {
+  g_last_error = msg;
+  return s;
+}
+
+qtt_status cuda_fail(cudaError_t e, const char *where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();  // allocation failures are not sticky; clear them
+    return fail(QTT_ERR_OOM, m);
+  }
+  return fail(QTT_ERR_CUDA, m);
+}
+
+// ------------------------------------------------------------ scratch pool
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
+cudaMemPool_t pool_for_current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = UINT64_MAX;  // keep freed blocks for the next call
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = p;
+  }
+  return g_pool[dev];
+}
+}  // namespace
+
+size_t scratch_available() {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
+  cudaMemPool_t p = pool_for_current_device();
+  if (!p) return free_b;
+  uint64_t reserved = 0, used = 0;
+  cudaMemPoolGetAttribute(p, cudaMemPoolAttrReservedMemCurrent, &reserved);
+  cudaMemPoolGetAttribute(p, cudaMemPoolAttrUsedMemCurrent, &used);
+  const size_t cached = reserved > used ? (size_t)(reserved - used) : 0;
+  // Leave a margin for the driver and other allocators in the process.
+  const size_t margin = (size_t)512 << 20;
+  return free_b > margin ? free_b - margin + cached : cached;
+}
+
+qtt_status scratch_alloc(void **ptr, size_t bytes, cudaStream_t stream) {
+  *ptr = nullptr;
+  if (bytes == 0) return QTT_OK;
+  cudaMemPool_t p = pool_for_current_device();
+  if (!p) return fail(QTT_ERR_CUDA, "cannot create the scratch memory pool");
+  if (bytes > scratch_available())
+    return fail(QTT_ERR_OOM, "scratch of " + std::to_string(bytes) +
+                                 " bytes exceeds free device memory");
+  cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes, p, stream);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return cuda_fail(e, "cudaMallocFromPoolAsync");
+  }
+  return QTT_OK;
+}
+
+void scratch_free(void *ptr, cudaStream_t stream) {
+  if (ptr) cudaFreeAsync(ptr, stream);
+}
+
+// ------------------------------------------------------------ validation
+static bool valid_dtype(qtt_dtype t) {
+  return t == QTT_F64 || t == QTT_F32 || t == QTT_TF32 || t == QTT_BF16;
+}
+
+// Apply of an FP64 operator, optionally with an epilogue on the last step.
+qtt_status apply_f64(const qtt_op *A, const double *x, double *y, int64_t nrhs,
+                     int64_t ld, cudaStream_t st, const Epilogue &epi) {
+  const int d = A->d;
+  const int64_t N = (int64_t)1 << d;
+  // Scratch: two ping-pong buffers of rmax_inner x N per right-hand side.
+  const size_t per_rhs = d > 1 ? (size_t)2 * A->rmax_inner * (size_t)N * sizeof(double) : 0;
+  int64_t chunk = nrhs;
+  if (per_rhs) {
+    const size_t avail = scratch_available();
+    const int64_t fit = (int64_t)(avail / per_rhs);
+    if (fit < 1)
+      return fail(QTT_ERR_OOM, "apply scratch for one right-hand side (" +
+                                   std::to_string(per_rhs) + " bytes) does not fit");
+    chunk = std::min<int64_t>(nrhs, fit);
+  }
+  void *scratch = nullptr;
+  qtt_status s = scratch_alloc(&scratch, per_rhs * (size_t)chunk, st);
+  if (s != QTT_OK) return s;
+  double *buf[2] = {nullptr, nullptr};
+  if (per_rhs) {
+    buf[0] = static_cast<double *>(scratch);
+    buf[1] = buf[0] + (size_t)A->rmax_inner * (size_t)N * (size_t)chunk;
+  }
+  for (int64_t c0 = 0; c0 < nrhs; c0 += chunk) {
+    const int64_t nc = std::min<int64_t>(chunk, nrhs - c0);
+    for (int k = 0; k < d; ++k) {
+      StepF64 p;
+      std::memset(&p, 0, sizeof(p));
+      p.k = k;
+      p.rin = A->ranks[k];
+      p.rout = A->ranks[k + 1];
+      p.N = N;
+      p.nrhs = nc;
+      p.M = A->m64 + A->off[k];
+      if (k == 0) {
+        p.in = x + c0 * ld;
+        p.in_rhs_stride = ld;
+      } else {
+        p.in = buf[(k - 1) & 1];
+        p.in_rhs_stride = (int64_t)p.rin * N;
+      }
+      if (k == d - 1) {
+        p.out = y + c0 * ld;
+        p.out_rhs_stride = ld;
+        if (epi.on) {
+          p.epi = 1;
+          p.u = epi.u ? epi.u + c0 * ld : nullptr;
+          p.v = epi.v ? epi.v + c0 * ld : nullptr;
+          p.uv_rhs_stride = ld;
+          p.s_acc = epi.s_acc;
+          p.s_u = epi.s_u;
+          p.s_v = epi.s_v;
+        }
+      } else {
+        p.out = buf[k & 1];
+        p.out_rhs_stride = (int64_t)p.rout * N;
+      }
+      cudaError_t e = launch_step_f64(p, st);
+      if (e != cudaSuccess) {
+        scratch_free(scratch, st);
+        return cuda_fail(e, "step_f64 launch");
+      }
+    }
+  }
+  scratch_free(scratch, st);
+  return QTT_OK;
+}
+
+}  // namespace qtt
+
+using namespace qtt;
+
+// ================================================================== C-ABI
+extern "C" {
+
+const char *qtt_status_string(qtt_status s) {
+  switch (s) {
+    case QTT_OK: return "ok";
+    case QTT_ERR_INVALID_ARG: return "invalid argument";
+    case QTT_ERR_OOM: return "out of device memory";
+    case QTT_ERR_CUDA: return "CUDA error";
+    case QTT_ERR_NOT_CONVERGED: return "not converged";
+    case QTT_ERR_TIMEOUT: return "device wait timed out";
+    case QTT_ERR_UNSUPPORTED: return "unsupported combination";
+  }
+  return "unknown status";
+}
+
+const char *qtt_last_error(void) { return g_last_error.c_str(); }
+
+qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores,
+                      unsigned precision_mask, void *stream) {
+  if (!out) return fail(QTT_ERR_INVALID_ARG, "qtt_create: out is NULL");
+  *out = nullptr;
+  if (d < 1 || d > 30) return fail(QTT_ERR_INVALID_ARG, "qtt_create: d must be in [1, 30]");
+  if (!ranks || !cores) return fail(QTT_ERR_INVALID_ARG, "qtt_create: NULL ranks or cores");
+  if (ranks[0] != 1 || ranks[d] != 1)
+    return fail(QTT_ERR_INVALID_ARG, "qtt_create: ranks[0] and ranks[d] must be 1");
+  for (int k = 0; k <= d; ++k)
+    if (ranks[k] < 1 || ranks[k] > 4096)
+      return fail(QTT_ERR_INVALID_ARG, "qtt_create: ranks must be in [1, 4096]");
+  if (precision_mask & ~(unsigned)(QTT_PACK_F32 | QTT_PACK_TF32 | QTT_PACK_BF16))
+    return fail(QTT_ERR_INVALID_ARG, "qtt_create: unknown precision_mask bits");
+
+  qtt_op *A = new (std::nothrow) qtt_op();
+  if (!A) return fail(QTT_ERR_OOM, "qtt_create: host allocation failed");
+  A->d = d;
+  cudaGetDevice(&A->device);
+  A->ranks.assign(ranks, ranks + d + 1);
+  A->off.resize(d + 1);
+  int64_t off = 0;
+  double sig = 0.0;
+  for (int k = 0; k < d; ++k) {
+    A->off[k] = off;
+    off += (int64_t)4 * ranks[k] * ranks[k + 1];
+    sig += (double)ranks[k] * ranks[k + 1];
+  }
+  A->off[d] = off;
+  A->nparams = off;
+  A->flops_per_rhs = 4.0 * std::ldexp(1.0, d) * sig;
+  A->rmax_inner = 1;
+  for (int k = 1; k < d; ++k) A->rmax_inner = std::max(A->rmax_inner, ranks[k]);
+  A->packs = precision_mask;
+
+  // Permute each core G_k[a][i][j][b] into M_k packed as [b][a][j][i].
+  std::vector<double> packed((size_t)off);
+  for (int k = 0; k < d; ++k) {
+    const int ra = ranks[k], rb = ranks[k + 1];
+    const double *G = cores + A->off[k];
+    double *M = packed.data() + A->off[k];
+    for (int a = 0; a < ra; ++a)
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+          for (int b = 0; b < rb; ++b)
+            M[(((size_t)b * ra + a) * 2 + j) * 2 + i] = G[(((size_t)a * 2 + i) * 2 + j) * rb + b];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)off * sizeof(double);
+  cudaError_t e = cudaMalloc(&A->m64, bytes);
+  if (e != cudaSuccess) {
+    delete A;
+    return cuda_fail(e, "qtt_create: cudaMalloc");
+  }
+  e = cudaMemcpyAsync(A->m64, packed.data(), bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    qtt_destroy(A);
+    return cuda_fail(e, "qtt_create: upload");
+  }
+  *out = A;
+  return QTT_OK;
+}
+
+qtt_status qtt_destroy(qtt_op *A) {
+  if (!A) return QTT_OK;
+  cudaDeviceSynchronize();
+  if (A->m64) cudaFree(A->m64);
+  if (A->m32) cudaFree(A->m32);
+  if (A->mtf32) cudaFree(A->mtf32);
+  if (A->mbf16) cudaFree(A->mbf16);
+  delete A;
+  return QTT_OK;
+}
+
+int qtt_op_d(const qtt_op *A) { return A ? A->d : -1; }
+
+int qtt_op_rank(const qtt_op *A, int k) {
+  if (!A || k < 0 || k > A->d) return -1;
+  return A->ranks[k];
+}
+
+double qtt_op_flops(const qtt_op *A) { return A ? A->flops_per_rhs : 0.0; }
+
+qtt_status qtt_apply(const qtt_op *A, const void *x, void *y, int64_t nrhs, int64_t ld,
+                     qtt_dtype io_dtype, qtt_dtype compute, void *stream) {
+  if (!A) return fail(QTT_ERR_INVALID_ARG, "qtt_apply: NULL operator");
+  if (!valid_dtype(io_dtype) || !valid_dtype(compute))
+    return fail(QTT_ERR_INVALID_ARG, "qtt_apply: unknown dtype");
+  const int64_t N = (int64_t)1 << A->d;
+  if (nrhs < 0) return fail(QTT_ERR_INVALID_ARG, "qtt_apply: nrhs < 0");
+  if (nrhs == 0) return QTT_OK;
+  if (ld < N) return fail(QTT_ERR_INVALID_ARG, "qtt_apply: ld < N");
+  if (!x || !y) return fail(QTT_ERR_INVALID_ARG, "qtt_apply: NULL vector");
+  const size_t esz = io_dtype == QTT_F64 ? 8 : (io_dtype == QTT_BF16 ? 2 : 4);
+  {
+    const char *xb = static_cast<const char *>(x), *yb = static_cast<const char *>(y);
+    const size_t span = ((size_t)(nrhs - 1) * (size_t)ld + (size_t)N) * esz;
+    if (xb < yb + span && yb < xb + span)
+      return fail(QTT_ERR_INVALID_ARG, "qtt_apply: x and y overlap");
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (compute == QTT_F64 && io_dtype == QTT_F64)
+    return apply_f64(A, static_cast<const double *>(x), static_cast<double *>(y), nrhs, ld,
+                     st, Epilogue());
+  return fail(QTT_ERR_UNSUPPORTED, "qtt_apply: io/compute combination not built");
+}
+
+qtt_status qtt_residual(const qtt_op *K, double a, const double *f, const double *x,
+                        double *r, int64_t nrhs, int64_t ld, void *stream) {
+  if (!K) return fail(QTT_ERR_INVALID_ARG, "qtt_residual: NULL operator");
+  const int64_t N = (int64_t)1 << K->d;
+  if (nrhs < 0 || (nrhs > 0 && ld < N))
+    return fail(QTT_ERR_INVALID_ARG, "qtt_residual: bad nrhs or ld");
+  if (nrhs == 0) return QTT_OK;
+  if (!f || !x || !r) return fail(QTT_ERR_INVALID_ARG, "qtt_residual: NULL vector");
+  const size_t span = ((size_t)(nrhs - 1) * (size_t)ld + (size_t)N) * sizeof(double);
+  const char *rb = reinterpret_cast<const char *>(r);
+  for (const double *v : {f, x}) {
+    const char *vb = reinterpret_cast<const char *>(v);
+    if (vb < rb + span && rb < vb + span)
+      return fail(QTT_ERR_INVALID_ARG, "qtt_residual: r overlaps f or x");
+  }
+  Epilogue e;
+  e.on = true;
+  e.v = f;
+  e.s_v = 1.0;
+  e.u = x;
+  e.s_u = -a;
+  e.s_acc = -1.0;
+  return apply_f64(K, x, r, nrhs, ld, static_cast<cudaStream_t>(stream), e);
+}
+
+qtt_status qtt_solve(const qtt_op *K, const qtt_op *P, const double *f, double *x,
+                     int64_t nrhs, int64_t ld, const qtt_solve_params *prm,
+                     qtt_solve_info *info, void *stream) {
+  (void)K; (void)P; (void)f; (void)x; (void)nrhs; (void)ld; (void)prm; (void)info;
+  (void)stream;
+  return fail(QTT_ERR_UNSUPPORTED, "qtt_solve: not built yet");
+}
+
+qtt_status qtt_sync_status(void *stream) {
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "qtt_sync_status");
+  return QTT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Internal declarations shared by the CUDA translation units of libqtt.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qtt.h"
+
+namespace qtt {
+
+// Record a message for qtt_last_error() and return the status.
+qtt_status fail(qtt_status s, const std::string &msg);
+qtt_status cuda_fail(cudaError_t e, const char *where);
+
+#define QTT_CUDA_TRY(call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return ::qtt::cuda_fail(e_, #call); \
+  } while (0)
+
+// Stream-ordered scratch from the library's pool (one pool per device, keeps
+// freed blocks cached).  Returns QTT_ERR_OOM if `bytes` cannot be had.
+qtt_status scratch_alloc(void **ptr, size_t bytes, cudaStream_t stream);
+void scratch_free(void *ptr, cudaStream_t stream);
+// Bytes the pool could hand out right now without growing past free memory.
+size_t scratch_available();
+
+}  // namespace qtt
+
+// One QTT matrix resident on the device.  Core k is packed as the matrix
+// M_k of Algorithm 2 (rows (alpha_{k+1}, i_k), columns (alpha_k, j_k)) in
+// the order each kernel reads it:
+//   m64 / m32 / mbf16 : [alpha_{k+1}][alpha_k][j_k][i_k], i.e. for each output
+//                       rank b a run of 2 r_k pairs (i = 0, i = 1).
+struct qtt_op {
+  int d = 0;
+  int device = 0;
+  std::vector<int> ranks;       // d + 1
+  std::vector<int64_t> off;     // element offset of core k in the packed arrays
+  int64_t nparams = 0;          // sum_k 4 r_k r_{k+1}
+  int rmax_inner = 1;           // max_{0<k<d} r_k (intermediate width)
+  double flops_per_rhs = 0.0;   // 4 N sum_k r_k r_{k+1}
+  unsigned packs = 0;           // QTT_PACK_* built
+  double *m64 = nullptr;
+  float *m32 = nullptr;         // FP32 copy (QTT_PACK_F32)
+  float *mtf32 = nullptr;       // FP32 storage of TF32-rounded values
+  __nv_bfloat16 *mbf16 = nullptr;
+};
+
+namespace qtt {
+
+// FP64 core step (Algorithm 2, one k).  in/out rhs strides in elements.
+struct StepF64 {
+  const double *in;
+  int64_t in_rhs_stride;
+  double *out;
+  int64_t out_rhs_stride;
+  const double *M;  // packed core k
+  int k, rin, rout;
+  int64_t N;
+  int64_t nrhs;
+  // Epilogue of the last step (rout == 1), when `epi` is set:
+  //   out = s_v v + s_u u + s_acc acc      (u, v may be NULL)
+  // residual f - a x - K x: v = f, u = x, s_v = 1, s_u = -a, s_acc = -1;
+  // operator a z + K z: u = z, s_u = a; accumulate y += K z: u = out.
+  int epi;
+  const double *u;
+  const double *v;
+  int64_t uv_rhs_stride;
+  double s_acc, s_u, s_v;
+};
+cudaError_t launch_step_f64(const StepF64 &s, cudaStream_t stream);
+
+// Epilogue request for a whole apply (applies to its last step).
+struct Epilogue {
+  bool on = false;
+  const double *u = nullptr;
+  const double *v = nullptr;
+  double s_acc = 1.0, s_u = 0.0, s_v = 0.0;
+};
+
+// FP64 apply of A to nrhs vectors (ld = leading dimension of x and y) with
+// an optional epilogue; scratch from the pool.  Host-side, asynchronous.
+qtt_status apply_f64(const qtt_op *A, const double *x, double *y, int64_t nrhs, int64_t ld,
+                     cudaStream_t st, const Epilogue &epi);
+
+}  // namespace qtt

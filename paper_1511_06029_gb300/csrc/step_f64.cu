@@ -1,0 +1,115 @@
+// FP64 core step of the QTT apply (Algorithm 2, one iteration of the sweep).
+//
+// Step k maps the intermediate y_k (r_k planes of N positions) to y_{k+1}
+// (r_{k+1} planes).  Position p keeps its bits; bit k holds the column bit
+// j_k on input and the row bit i_k on output, so the column merge and row
+// split of Algorithm 2 are pure addressing.  For every pair of positions
+// (p0, p1 = p0 | 2^k) and every output rank b:
+//   out[b][p_i] = sum_{a, j} G_k(a, i, j, b) in[a][p_j]      (i, j in {0,1})
+// which is phi_k = M_k b_k for the column of that pair.  The flop count is
+// 4 r_k r_{k+1} N (Sec. 4.2).
+//
+// On GB300 the FP64 pipe is the limit by a wide margin (the step moves
+// (r_k + r_{k+1}) x 8 bytes per position against 4 r_k r_{k+1} flops), so
+// the kernel is shaped for DFMA issue, not bandwidth: each thread owns one
+// output rank b (both row bits) and TN position pairs, giving 2 TN
+// independent FMA chains; the warp shares b, so each core element is a
+// broadcast load, and the 32 lanes read 32 consecutive pairs (coalesced).
+#include "qtt_internal.h"
+
+namespace qtt {
+namespace {
+
+constexpr int kTN = 4;       // position pairs per thread
+constexpr int kWarpsY = 8;   // output ranks per CTA (one per warp)
+
+template <int TN>
+__global__ void __launch_bounds__(32 * kWarpsY)
+step_f64_kernel(StepF64 s) {
+  const int b = blockIdx.y * blockDim.y + threadIdx.y;
+  if (b >= s.rout) return;
+  const int64_t c = blockIdx.z;
+  const int64_t npairs = s.N >> 1;
+  const int64_t bit = (int64_t)1 << s.k;
+  const int64_t low = bit - 1;
+  const int64_t q0 = (int64_t)blockIdx.x * (32 * TN) + threadIdx.x;
+
+  int64_t p0[TN];
+  bool ok[TN];
+#pragma unroll
+  for (int m = 0; m < TN; ++m) {
+    const int64_t q = q0 + 32 * m;
+    ok[m] = q < npairs;
+    p0[m] = ((q & ~low) << 1) | (q & low);
+  }
+  const double *in = s.in + c * s.in_rhs_stride;
+  const double2 *Mb = reinterpret_cast<const double2 *>(s.M) + (int64_t)b * 2 * s.rin;
+
+  double acc0[TN], acc1[TN];
+#pragma unroll
+  for (int m = 0; m < TN; ++m) acc0[m] = acc1[m] = 0.0;
+
+  for (int a = 0; a < s.rin; ++a) {
+    const double *ina = in + (int64_t)a * s.N;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const double2 g = __ldg(Mb + 2 * a + j);  // (i = 0, i = 1)
+      const int64_t sh = j ? bit : 0;
+#pragma unroll
+      for (int m = 0; m < TN; ++m) {
+        const double v = ok[m] ? __ldg(ina + p0[m] + sh) : 0.0;
+        acc0[m] = fma(g.x, v, acc0[m]);
+        acc1[m] = fma(g.y, v, acc1[m]);
+      }
+    }
+  }
+
+  double *out = s.out + c * s.out_rhs_stride + (int64_t)b * s.N;
+  if (s.epi) {
+    const double *u = s.u ? s.u + c * s.uv_rhs_stride : nullptr;
+    const double *v = s.v ? s.v + c * s.uv_rhs_stride : nullptr;
+#pragma unroll
+    for (int m = 0; m < TN; ++m) {
+      if (!ok[m]) continue;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int64_t p = p0[m] + (i ? bit : 0);
+        double t = v ? s.s_v * v[p] : 0.0;
+        if (u) t += s.s_u * u[p];
+        out[p] = t + s.s_acc * (i ? acc1[m] : acc0[m]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < TN; ++m) {
+      if (!ok[m]) continue;
+      out[p0[m]] = acc0[m];
+      out[p0[m] + bit] = acc1[m];
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_step_f64(const StepF64 &s, cudaStream_t stream) {
+  const int64_t npairs = s.N >> 1;
+  const int by = s.rout < kWarpsY ? s.rout : kWarpsY;
+  const int64_t gx = (npairs + 32 * kTN - 1) / (32 * kTN);
+  const int64_t gy = (s.rout + by - 1) / by;
+  dim3 block(32, by, 1);
+  for (int64_t c0 = 0; c0 < s.nrhs; c0 += 65535) {
+    StepF64 t = s;
+    const int64_t nc = (s.nrhs - c0) < 65535 ? (s.nrhs - c0) : 65535;
+    t.in += c0 * s.in_rhs_stride;
+    t.out += c0 * s.out_rhs_stride;
+    if (t.u) t.u += c0 * s.uv_rhs_stride;
+    if (t.v) t.v += c0 * s.uv_rhs_stride;
+    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nc);
+    step_f64_kernel<kTN><<<grid, block, 0, stream>>>(t);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace qtt

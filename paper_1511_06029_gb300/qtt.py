@@ -1,0 +1,233 @@
+"""Python binding of libqtt (ctypes; argument marshalling only).
+
+Every step of the apply and the solves runs in the library's CUDA kernels;
+this module converts torch tensors to pointers, sizes and streams.  There is
+no CPU fallback: if ``libqtt.so`` has not been built, or no GPU is present,
+the calls raise.
+
+Names follow the C-ABI in ``include/qtt.h``:
+
+    op = Operator(data, packs=("bf16",))   # qtt_create (data: ranks + cores)
+    y  = op.apply(x, compute="f64")        # qtt_apply
+    r  = op.residual(f, x, a=1.0)          # qtt_residual
+    x, info = solve(K, P, f, kind="gmres") # qtt_solve
+    op.close()                             # qtt_destroy
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqtt.so")
+
+QTT_OK, QTT_ERR_INVALID_ARG, QTT_ERR_OOM, QTT_ERR_CUDA = 0, 1, 2, 3
+QTT_ERR_NOT_CONVERGED, QTT_ERR_TIMEOUT, QTT_ERR_UNSUPPORTED = 4, 5, 6
+DTYPES = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3}
+PACKS = {"f32": 1 << 1, "tf32": 1 << 2, "bf16": 1 << 3}
+SOLVE_KINDS = {"direct": 0, "gmres": 1, "refine": 2}
+
+# Every function the header declares, with its ctypes signature.
+_I, _U, _L, _D, _P = ctypes.c_int, ctypes.c_uint, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+SIGNATURES = {
+    "qtt_create": (_I, [ctypes.POINTER(_P), _I, _P, _P, _U, _P]),
+    "qtt_destroy": (_I, [_P]),
+    "qtt_op_d": (_I, [_P]),
+    "qtt_op_rank": (_I, [_P, _I]),
+    "qtt_op_flops": (_D, [_P]),
+    "qtt_apply": (_I, [_P, _P, _P, _L, _L, _I, _I, _P]),
+    "qtt_residual": (_I, [_P, _D, _P, _P, _P, _L, _L, _P]),
+    "qtt_solve": (_I, [_P, _P, _P, _P, _L, _L, _P, _P, _P]),
+    "qtt_status_string": (ctypes.c_char_p, [_I]),
+    "qtt_last_error": (ctypes.c_char_p, []),
+    "qtt_sync_status": (_I, [_P]),
+}
+
+
+class QTTError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str = ""):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({msg})")
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("kind", _I), ("a", _D), ("tol", _D), ("restart", _I),
+                ("max_iter", _I), ("precond_compute", _I)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", _I), ("rel_residual", _D), ("status", _I)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libqtt.so and bind every declared symbol (raises if missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise QTTError(-1, "load_library",
+                               f"{path} not built; run `python -m paper_1511_06029_gb300.build`")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != QTT_OK:
+        lib = load_library()
+        msg = lib.qtt_last_error().decode() or lib.qtt_status_string(st).decode()
+        raise QTTError(st, where, msg)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise QTTError(-1, "libqtt", "a CUDA device is required (no CPU fallback)")
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+_TORCH_DTYPE = {"f64": "float64", "f32": "float32", "tf32": "float32", "bf16": "bfloat16"}
+
+
+def _io_name(t) -> str:
+    torch = _torch()
+    m = {torch.float64: "f64", torch.float32: "f32", torch.bfloat16: "bf16"}
+    if t.dtype not in m:
+        raise QTTError(QTT_ERR_INVALID_ARG, "libqtt", f"unsupported tensor dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def _block(t, N, what):
+    """(nrhs, N) view with unit inner stride -> (nrhs, ld)."""
+    if not t.is_cuda:
+        raise QTTError(QTT_ERR_INVALID_ARG, what, "tensor must be on the GPU")
+    if t.dim() == 1:
+        if t.shape[0] != N or t.stride(0) != 1:
+            raise QTTError(QTT_ERR_INVALID_ARG, what, "bad vector shape/stride")
+        return 1, N
+    if t.dim() != 2 or t.shape[1] != N or t.stride(1) != 1:
+        raise QTTError(QTT_ERR_INVALID_ARG, what, f"expected (nrhs, {N}) with unit stride")
+    if t.shape[0] > 1 and t.stride(0) < N:
+        raise QTTError(QTT_ERR_INVALID_ARG, what, "rows overlap (row stride < N)")
+    return t.shape[0], (t.stride(0) if t.shape[0] > 1 else N)
+
+
+class Operator:
+    """A QTT matrix resident on the GPU (qtt_create / qtt_destroy)."""
+
+    def __init__(self, data, packs=(), stream=None):
+        lib = load_library()
+        _torch()
+        ranks = np.ascontiguousarray(np.asarray(data.ranks, dtype=np.int32))
+        d = len(ranks) - 1
+        flat = np.ascontiguousarray(np.concatenate(
+            [np.ascontiguousarray(c, dtype=np.float64).ravel() for c in data.cores]))
+        mask = 0
+        for p in packs:
+            mask |= PACKS[p]
+        h = ctypes.c_void_p()
+        _check(lib.qtt_create(ctypes.byref(h), d, ranks.ctypes.data_as(_P),
+                              flat.ctypes.data_as(_P), mask, _stream_handle(stream)),
+               "qtt_create")
+        self._h = h
+        self.d = d
+        self.N = 1 << d
+        self.ranks = [int(v) for v in ranks]
+        self.packs = tuple(packs)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise QTTError(QTT_ERR_INVALID_ARG, "Operator", "operator was closed")
+        return self._h
+
+    def flops(self, nrhs: int = 1) -> float:
+        return load_library().qtt_op_flops(self.handle) * nrhs
+
+    def apply(self, x, out=None, compute: str = "f64", stream=None):
+        """y = A x on the GPU (qtt_apply).  x: (N,) or (nrhs, N) CUDA tensor of
+        float64 / float32 / bfloat16; y has the same dtype and shape."""
+        torch = _torch()
+        nrhs, ld = _block(x, self.N, "qtt_apply")
+        if out is None:
+            out = torch.empty_like(x, memory_format=torch.contiguous_format)
+        n2, ld2 = _block(out, self.N, "qtt_apply")
+        if n2 != nrhs or out.dtype != x.dtype:
+            raise QTTError(QTT_ERR_INVALID_ARG, "qtt_apply", "out shape/dtype mismatch")
+        if ld2 != ld:
+            raise QTTError(QTT_ERR_INVALID_ARG, "qtt_apply", "x and out need the same row stride")
+        io = _io_name(x)
+        _check(load_library().qtt_apply(self.handle, ctypes.c_void_p(x.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), nrhs, ld,
+                                        DTYPES[io], DTYPES[compute], _stream_handle(stream)),
+               "qtt_apply")
+        return out
+
+    def residual(self, f, x, a: float = 1.0, out=None, stream=None):
+        """r = f - (a x + K x) in FP64 (qtt_residual)."""
+        torch = _torch()
+        nrhs, ld = _block(f, self.N, "qtt_residual")
+        if out is None:
+            out = torch.empty_like(f)
+        for t in (x, out):
+            n2, ld2 = _block(t, self.N, "qtt_residual")
+            if n2 != nrhs or ld2 != ld or t.dtype != torch.float64:
+                raise QTTError(QTT_ERR_INVALID_ARG, "qtt_residual", "shape/stride/dtype mismatch")
+        _check(load_library().qtt_residual(self.handle, a, ctypes.c_void_p(f.data_ptr()),
+                                           ctypes.c_void_p(x.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr()), nrhs, ld,
+                                           _stream_handle(stream)), "qtt_residual")
+        return out
+
+    def close(self):
+        if self._h is not None:
+            load_library().qtt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(K, P, f, kind: str = "gmres", a: float = 1.0, tol: float = 1e-10,
+          restart: int = 30, max_iter: int = 300, precond_compute: str = "f64",
+          out=None, stream=None, raise_on_fail: bool = True):
+    """Solve (a I + K) x = f (qtt_solve).  Returns (x, info) with info a list
+    of (iters, rel_residual, status) per right-hand side."""
+    torch = _torch()
+    N = (K or P).N
+    nrhs, ld = _block(f, N, "qtt_solve")
+    if out is None:
+        out = torch.empty_like(f)
+    prm = SolveParams(SOLVE_KINDS[kind], a, tol, restart, max_iter, DTYPES[precond_compute])
+    info = (SolveInfo * nrhs)()
+    st = load_library().qtt_solve(K.handle if K is not None else None,
+                                  P.handle if P is not None else None,
+                                  ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                  nrhs, ld, ctypes.byref(prm), info, _stream_handle(stream))
+    if st != QTT_OK and (st != QTT_ERR_NOT_CONVERGED or raise_on_fail):
+        _check(st, "qtt_solve")
+    return out, [(i.iters, i.rel_residual, i.status) for i in info]
+
+
+def sync_status(stream=None):
+    _check(load_library().qtt_sync_status(_stream_handle(stream)), "qtt_sync_status")

@@ -243,3 +243,12 @@ def test_direct_is_apply(oracle_mod):
     P = inputs.synthetic_operator(9, 8, 3)
     f = inputs.gaussian_rhs(P.N, 2, 4)
     assert np.array_equal(oracle_mod.solve_direct(P, f), oracle_mod.apply(P, f))
+
+
+def test_entries_match_dense(oracle_mod):
+    op = inputs.random_cores(9, inputs.random_ranks(9, 6, 51), 51)
+    A = oracle_mod.dense(op)
+    rng = np.random.default_rng(52)
+    I = rng.integers(0, 512, size=300)
+    J = rng.integers(0, 512, size=300)
+    assert np.allclose(oracle_mod.entries(op, I, J), A[I, J], rtol=1e-13, atol=1e-15)
