@@ -119,6 +119,30 @@ qtt_status qtt_apply(const qtt_op *A, const void *x, void *y, int64_t nrhs,
                      int64_t ld, qtt_dtype io_dtype, qtt_dtype compute,
                      void *stream);
 
+/* qtt_apply_noalloc -- y = A x in FP64 without allocating any memory.  The
+ * paper has no counterpart: this exists for callers that cannot allocate
+ * device memory at the time they apply an operator -- for instance a process
+ * whose device memory is already reserved by another allocator (a framework
+ * arena or a budget fixed at start-up), or a latency-bound loop where an
+ * allocation call could synchronise the device or fail under fragmentation.
+ * Same product, layout and arguments as qtt_apply with io_dtype = compute =
+ * QTT_F64; the two intermediate buffers of the sweep live in one static
+ * device array of 64 MiB (8,388,608 doubles) that every GPU loading the
+ * library holds until the process exits.
+ *   Limit : d > 1 needs 2 x max_{0<k<d} ranks[k] x N x nrhs <= 8,388,608
+ *           doubles; larger calls return QTT_ERR_INVALID_ARG (use qtt_apply).
+ *   Set-up: the first call on each device looks up the array's device
+ *           address (with that device current); make that first call before
+ *           any stream capture.
+ *   Races : every call on a device shares the one array, which keeps the
+ *           last call's contents (nothing in it needs to start at zero).
+ *           Calls whose work overlaps on the GPU -- on different streams, or
+ *           from different threads -- race on it; order them.
+ * Calls no cudaMalloc, cudaFree or other allocating routine.
+ * Errors: QTT_ERR_INVALID_ARG, QTT_ERR_CUDA. */
+qtt_status qtt_apply_noalloc(const qtt_op *A, const double *x, double *y,
+                             int64_t nrhs, int64_t ld, void *stream);
+
 /* qtt_residual -- r = f - (a x + K x), all FP64, the forward residual of the
  * second-kind system (a I + K) x = f (Sec. 3, eq. (nystrom): A = a I +
  * B K W C), with the subtraction fused into the last core step of the K

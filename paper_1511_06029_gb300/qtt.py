@@ -40,6 +40,7 @@ SIGNATURES = {
     "qtt_op_flops": (_D, [_P]),
     "qtt_apply": (_I, [_P, _P, _P, _L, _L, _I, _I, _P]),
     "qtt_residual": (_I, [_P, _D, _P, _P, _P, _L, _L, _P]),
+    "qtt_apply_noalloc": (_I, [_P, _P, _P, _L, _L, _P]),
     "qtt_solve": (_I, [_P, _P, _P, _P, _L, _L, _P, _P, _P]),
     "qtt_status_string": (ctypes.c_char_p, [_I]),
     "qtt_last_error": (ctypes.c_char_p, []),
