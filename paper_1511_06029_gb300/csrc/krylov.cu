@@ -43,14 +43,17 @@ dots_partial_kernel(VecSet V, int nv, VecSet W, int64_t N, int B, double *partia
   (void)nv;
 }
 
-__global__ void reduce_partials_kernel(const double *partial, int B, int64_t count,
-                                       double *out, double *out2) {
+// partial[(i * nc + c) * B + b] -> out[i * nrhs + c0 + c] (sum over b in order)
+__global__ void reduce_partials_kernel(const double *partial, int B, int64_t nc, int nv,
+                                       int64_t nrhs, int64_t c0, double *out, double *out2) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= count) return;
+  if (idx >= nc * nv) return;
   double s = 0.0;
   for (int b = 0; b < B; ++b) s += partial[idx * B + b];
-  if (out2) out2[idx] += s;  // accumulate (second Gram-Schmidt pass)
-  if (out) out[idx] = s;
+  const int64_t i = idx / nc, c = idx % nc;
+  const int64_t o = i * nrhs + c0 + c;
+  if (out2) out2[o] += s;  // accumulate (second Gram-Schmidt pass)
+  if (out) out[o] = s;
 }
 
 // W[c] -= sum_i h[i * nrhs + c] V_i[c]
@@ -113,6 +116,16 @@ __global__ void copy_kernel(VecSet D, VecSet S, int64_t N) {
     dd[t] = s[t];
 }
 
+// D[c] += alpha S[c]
+__global__ void axpy_kernel(VecSet D, VecSet S, double alpha, int64_t N) {
+  const int64_t c = blockIdx.y;
+  const double *s = S.ptr + c * S.ld;
+  double *dd = D.ptr + c * D.ld;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < N;
+       t += (int64_t)gridDim.x * blockDim.x)
+    dd[t] += alpha * s[t];
+}
+
 unsigned grid_x(int64_t N) {
   int64_t g = (N + kThreads - 1) / kThreads;
   if (g > 4096) g = 4096;
@@ -141,15 +154,11 @@ cudaError_t vec_dots(VecSet V, int nv, VecSet W, int64_t N, int64_t nrhs, double
     dots_partial_kernel<<<dim3(B, (unsigned)nc, nv), kThreads, 0, st>>>(Vc, nv, Wc, N, B, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    for (int i = 0; i < nv; ++i) {
-      const int64_t count = nc;
-      double *o = out ? out + (int64_t)i * nrhs + c0 : nullptr;
-      double *o2 = accumulate_into ? accumulate_into + (int64_t)i * nrhs + c0 : nullptr;
-      reduce_partials_kernel<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(
-          partial + (int64_t)i * nc * B, B, count, o, o2);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-    }
+    const int64_t count = nc * nv;
+    reduce_partials_kernel<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(
+        partial, B, nc, nv, nrhs, c0, out, accumulate_into);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -183,6 +192,14 @@ cudaError_t vec_scale(VecSet D, VecSet S, const double *scale, int64_t N, int64_
   if (nrhs <= 0) return cudaSuccess;
   if (nrhs > 65535) return cudaErrorInvalidValue;
   scale_kernel<<<dim3(grid_x(N), (unsigned)nrhs), kThreads, 0, st>>>(D, S, scale, N);
+  return cudaGetLastError();
+}
+
+cudaError_t vec_axpy(VecSet D, VecSet S, double alpha, int64_t N, int64_t nrhs,
+                     cudaStream_t st) {
+  if (nrhs <= 0) return cudaSuccess;
+  if (nrhs > 65535) return cudaErrorInvalidValue;
+  axpy_kernel<<<dim3(grid_x(N), (unsigned)nrhs), kThreads, 0, st>>>(D, S, alpha, N);
   return cudaGetLastError();
 }
 

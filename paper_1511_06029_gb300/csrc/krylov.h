@@ -39,6 +39,9 @@ cudaError_t vec_normalize(VecSet D, VecSet S, const double *sumsq, int64_t N, in
 // D[c] = S[c] * scale[c]
 cudaError_t vec_scale(VecSet D, VecSet S, const double *scale, int64_t N, int64_t nrhs,
                       cudaStream_t st);
+// D[c] += alpha S[c]
+cudaError_t vec_axpy(VecSet D, VecSet S, double alpha, int64_t N, int64_t nrhs,
+                     cudaStream_t st);
 cudaError_t vec_copy(VecSet D, VecSet S, int64_t N, int64_t nrhs, cudaStream_t st);
 
 }  // namespace qtt

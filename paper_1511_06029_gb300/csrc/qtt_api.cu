@@ -9,6 +9,7 @@
 #include <new>
 
 #include "qtt_internal.h"
+#include "step_lp.h"
 
 namespace qtt {
 
@@ -88,6 +89,19 @@ void scratch_free(void *ptr, cudaStream_t stream) {
   if (ptr) cudaFreeAsync(ptr, stream);
 }
 
+// Host copy of the device TF32 rounding: round to nearest even at 13 dropped
+// mantissa bits (finite values).
+static float host_tf32_rne(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0x0fffu + ((u >> 13) & 1u);
+    u &= 0xffffe000u;
+  }
+  std::memcpy(&x, &u, 4);
+  return x;
+}
+
 // ------------------------------------------------------------ validation
 static bool valid_dtype(qtt_dtype t) {
   return t == QTT_F64 || t == QTT_F32 || t == QTT_TF32 || t == QTT_BF16;
@@ -155,6 +169,96 @@ qtt_status apply_f64(const qtt_op *A, const double *x, double *y, int64_t nrhs,
       if (e != cudaSuccess) {
         scratch_free(scratch, st);
         return cuda_fail(e, "step_f64 launch");
+      }
+    }
+  }
+  scratch_free(scratch, st);
+  return QTT_OK;
+}
+
+static size_t dtype_size(qtt_dtype t) {
+  return t == QTT_F64 ? 8 : (t == QTT_BF16 ? 2 : 4);
+}
+
+qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype xt, void *y,
+                    qtt_dtype yt, int64_t nrhs, int64_t ld, cudaStream_t st,
+                    const LpEpilogue &epi) {
+  int mode;
+  const void *cores;
+  switch (compute) {
+    case QTT_F32: mode = LP_F32; cores = A->m32; break;
+    case QTT_TF32: mode = LP_TF32; cores = A->mtf32; break;
+    case QTT_BF16: mode = LP_BF16; cores = A->mbf16; break;
+    default: return fail(QTT_ERR_INVALID_ARG, "apply_lp: compute must be F32, TF32 or BF16");
+  }
+  if (!cores)
+    return fail(QTT_ERR_INVALID_ARG,
+                "apply: operator was created without the packed copy for this precision "
+                "(QTT_PACK_* bit missing)");
+  const qtt_dtype mid = compute == QTT_BF16 ? QTT_BF16 : QTT_F32;
+  const size_t esz = dtype_size(mid);
+  const size_t core_esz = compute == QTT_BF16 ? 2 : 4;
+  const int d = A->d;
+  const int64_t N = (int64_t)1 << d;
+  const size_t per_rhs = d > 1 ? (size_t)2 * A->rmax_inner * (size_t)N * esz : 0;
+  int64_t chunk = nrhs;
+  if (per_rhs) {
+    const int64_t fit = (int64_t)(scratch_available() / per_rhs);
+    if (fit < 1)
+      return fail(QTT_ERR_OOM, "apply scratch for one right-hand side does not fit");
+    chunk = std::min<int64_t>(nrhs, fit);
+  }
+  void *scratch = nullptr;
+  qtt_status s = scratch_alloc(&scratch, per_rhs * (size_t)chunk, st);
+  if (s != QTT_OK) return s;
+  char *buf[2] = {nullptr, nullptr};
+  if (per_rhs) {
+    buf[0] = static_cast<char *>(scratch);
+    buf[1] = buf[0] + (size_t)A->rmax_inner * (size_t)N * (size_t)chunk * esz;
+  }
+  const size_t xsz = dtype_size(xt), ysz = dtype_size(yt);
+  for (int64_t c0 = 0; c0 < nrhs; c0 += chunk) {
+    const int64_t nc = std::min<int64_t>(chunk, nrhs - c0);
+    for (int k = 0; k < d; ++k) {
+      StepLP p;
+      std::memset(&p, 0, sizeof(p));
+      p.k = k;
+      p.rin = A->ranks[k];
+      p.rout = A->ranks[k + 1];
+      p.rout_pad = A->rpad[k + 1];
+      p.N = N;
+      p.nrhs = nc;
+      p.mode = mode;
+      p.M = static_cast<const char *>(cores) + (size_t)A->offlp[k] * core_esz;
+      if (k == 0) {
+        p.in = static_cast<const char *>(x) + (size_t)c0 * ld * xsz;
+        p.in_rhs_stride = ld;
+        p.in_type = xt;
+      } else {
+        p.in = buf[(k - 1) & 1];
+        p.in_rhs_stride = (int64_t)p.rin * N;
+        p.in_type = mid;
+      }
+      if (k == d - 1) {
+        p.out = static_cast<char *>(y) + (size_t)c0 * ld * ysz;
+        p.out_rhs_stride = ld;
+        p.out_type = yt;
+        if (epi.on) {
+          p.epi = 1;
+          p.u = epi.u ? static_cast<const char *>(epi.u) + (size_t)c0 * ld * ysz : nullptr;
+          p.u_rhs_stride = ld;
+          p.s_acc = epi.s_acc;
+          p.s_u = epi.s_u;
+        }
+      } else {
+        p.out = buf[k & 1];
+        p.out_rhs_stride = (int64_t)p.rout * N;
+        p.out_type = mid;
+      }
+      cudaError_t e = launch_step_lp(p, st);
+      if (e != cudaSuccess) {
+        scratch_free(scratch, st);
+        return cuda_fail(e, "step_lp launch");
       }
     }
   }
@@ -243,6 +347,55 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores
     qtt_destroy(A);
     return cuda_fail(e, "qtt_create: upload");
   }
+  // Reduced-precision copies: [a][j][b padded][i] per core.
+  if (precision_mask) {
+    A->rpad.assign(d + 1, 1);
+    A->offlp.assign(d + 1, 0);
+    int64_t o = 0;
+    for (int k = 0; k < d; ++k) {
+      A->rpad[k + 1] = lp_rank_pad(ranks[k + 1]);
+      A->offlp[k] = o;
+      o += (int64_t)4 * ranks[k] * A->rpad[k + 1];
+    }
+    A->offlp[d] = o;
+    A->nlp = o;
+    std::vector<float> lp((size_t)o, 0.0f);
+    for (int k = 0; k < d; ++k) {
+      const int ra = ranks[k], rb = ranks[k + 1], rp = A->rpad[k + 1];
+      const double *G = cores + A->off[k];
+      float *L = lp.data() + A->offlp[k];
+      for (int a = 0; a < ra; ++a)
+        for (int i = 0; i < 2; ++i)
+          for (int j = 0; j < 2; ++j)
+            for (int b = 0; b < rb; ++b)
+              L[(((size_t)a * 2 + j) * rp + b) * 2 + i] =
+                  (float)G[(((size_t)a * 2 + i) * 2 + j) * rb + b];
+    }
+    auto upload = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
+      cudaError_t e2 = cudaMalloc(dst, bytes);
+      if (e2 != cudaSuccess) return e2;
+      e2 = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st);
+      if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+      return e2;
+    };
+    cudaError_t e2 = cudaSuccess;
+    if (precision_mask & QTT_PACK_F32)
+      e2 = upload(reinterpret_cast<void **>(&A->m32), lp.data(), lp.size() * sizeof(float));
+    if (e2 == cudaSuccess && (precision_mask & QTT_PACK_TF32)) {
+      std::vector<float> t(lp);
+      for (float &v : t) v = host_tf32_rne(v);
+      e2 = upload(reinterpret_cast<void **>(&A->mtf32), t.data(), t.size() * sizeof(float));
+    }
+    if (e2 == cudaSuccess && (precision_mask & QTT_PACK_BF16)) {
+      std::vector<__nv_bfloat16> h(lp.size());
+      for (size_t q = 0; q < lp.size(); ++q) h[q] = __float2bfloat16_rn(lp[q]);
+      e2 = upload(reinterpret_cast<void **>(&A->mbf16), h.data(), h.size() * 2);
+    }
+    if (e2 != cudaSuccess) {
+      qtt_destroy(A);
+      return cuda_fail(e2, "qtt_create: reduced-precision upload");
+    }
+  }
   *out = A;
   return QTT_OK;
 }
@@ -285,10 +438,15 @@ qtt_status qtt_apply(const qtt_op *A, const void *x, void *y, int64_t nrhs, int6
       return fail(QTT_ERR_INVALID_ARG, "qtt_apply: x and y overlap");
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (compute == QTT_F64 && io_dtype == QTT_F64)
+  if (compute == QTT_F64) {
+    if (io_dtype != QTT_F64)
+      return fail(QTT_ERR_UNSUPPORTED, "qtt_apply: FP64 compute needs FP64 vectors");
     return apply_f64(A, static_cast<const double *>(x), static_cast<double *>(y), nrhs, ld,
                      st, Epilogue());
-  return fail(QTT_ERR_UNSUPPORTED, "qtt_apply: io/compute combination not built");
+  }
+  if (io_dtype == QTT_TF32)
+    return fail(QTT_ERR_INVALID_ARG, "qtt_apply: TF32 is not a storage type (use F32)");
+  return apply_lp(A, compute, x, io_dtype, y, io_dtype, nrhs, ld, st, LpEpilogue());
 }
 
 qtt_status qtt_residual(const qtt_op *K, double a, const double *f, const double *x,
@@ -314,14 +472,6 @@ qtt_status qtt_residual(const qtt_op *K, double a, const double *f, const double
   e.s_u = -a;
   e.s_acc = -1.0;
   return apply_f64(K, x, r, nrhs, ld, static_cast<cudaStream_t>(stream), e);
-}
-
-qtt_status qtt_solve(const qtt_op *K, const qtt_op *P, const double *f, double *x,
-                     int64_t nrhs, int64_t ld, const qtt_solve_params *prm,
-                     qtt_solve_info *info, void *stream) {
-  (void)K; (void)P; (void)f; (void)x; (void)nrhs; (void)ld; (void)prm; (void)info;
-  (void)stream;
-  return fail(QTT_ERR_UNSUPPORTED, "qtt_solve: not built yet");
 }
 
 qtt_status qtt_sync_status(void *stream) {

@@ -49,6 +49,10 @@ struct qtt_op {
   float *m32 = nullptr;         // FP32 copy (QTT_PACK_F32)
   float *mtf32 = nullptr;       // FP32 storage of TF32-rounded values
   __nv_bfloat16 *mbf16 = nullptr;
+  // Reduced-precision packing [a][j][b padded to rpad[k+1]][i]:
+  std::vector<int> rpad;        // padded output rank per core (index k+1)
+  std::vector<int64_t> offlp;   // element offset of core k
+  int64_t nlp = 0;              // total packed elements
 };
 
 namespace qtt {
@@ -82,6 +86,17 @@ struct Epilogue {
   const double *v = nullptr;
   double s_acc = 1.0, s_u = 0.0, s_v = 0.0;
 };
+
+// Reduced-precision apply (compute = QTT_F32 / QTT_TF32 / QTT_BF16); x of
+// type xt, y of type yt; epilogue on the last step: y = s_acc acc + s_u u.
+struct LpEpilogue {
+  bool on = false;
+  const void *u = nullptr;
+  double s_acc = 1.0, s_u = 0.0;
+};
+qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype xt, void *y,
+                    qtt_dtype yt, int64_t nrhs, int64_t ld, cudaStream_t st,
+                    const LpEpilogue &epi);
 
 // FP64 apply of A to nrhs vectors (ld = leading dimension of x and y) with
 // an optional epilogue; scratch from the pool.  Host-side, asynchronous.

@@ -1,0 +1,36 @@
+// Reduced-precision core step (FP32 pipe) -- see step_lp.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/qtt.h"
+
+namespace qtt {
+
+enum LpMode { LP_F32 = 0, LP_TF32 = 1, LP_BF16 = 2 };
+
+struct StepLP {
+  const void *in;          // element type in_type
+  int64_t in_rhs_stride;
+  void *out;               // element type out_type
+  int64_t out_rhs_stride;
+  const void *M;           // packed core k: [a][j][rout_pad][i], float or bf16
+  int k, rin, rout, rout_pad;
+  int64_t N, nrhs;
+  int mode;                // LpMode
+  qtt_dtype in_type, out_type;
+  // Epilogue (last step): out = s_acc acc + s_u u, u of out_type (may be out).
+  int epi;
+  const void *u;
+  int64_t u_rhs_stride;
+  double s_acc, s_u;
+};
+
+// Rank padding of the packed reduced-precision cores (multiple of the
+// per-thread rank tile).
+int lp_rank_pad(int r);
+cudaError_t launch_step_lp(const StepLP &s, cudaStream_t st);
+
+}  // namespace qtt
