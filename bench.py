@@ -1,17 +1,40 @@
-"""Benchmark of the QTT matrix x dense-vector apply (and, by --workload, the
-solves built on it).  Prints ONE JSON line on rank 0.
+"""Benchmark of the QTT matrix x dense-vector apply and the solves built on it.
+Prints ONE JSON line on rank 0.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload apply_f64|laplace_f64]
+                    [--workload NAME]
 
-Default workload (a "step" = one qtt_apply): synthetic QTT matrix, d = 24
-(N = 16,777,216), ranks r_k = min(2^k, 2^(24-k), 32), one FP64 right-hand
-side, FP64 arithmetic.  Throughput is the paper's flop count 4 N sum_k r_k
-r_{k+1} (Sec. 4.2) per second.  Multi-GPU (torchrun): each rank applies the
-operator to its own right-hand side (independent problems, weak scaling, no
-collective on the data path); value = all ranks' flops / max-over-ranks time.
+Workloads (a "step" is one pass of the hot path over one batch of input):
 
---impl reference times the CPU oracle (plain C, FP64) on the host cores on a
+  apply_f64       (default) synthetic QTT matrix d = 24 (N = 16,777,216),
+                  r_k = min(2^k, 2^(24-k), 32), one FP64 right-hand side, FP64
+                  arithmetic: one qtt_apply per step.
+  apply_f64_d22   the same family at d = 22 (profiler captures).
+  laplace_f64     the 8^3 Laplace volume operator (TT-SVD, eps 1e-8), 1 RHS.
+  apply_f32_d24 / apply_tf32_d24 / apply_bf16_d24
+                  the default operator and RHS with FP32 / TF32 / BF16 operands
+                  and FP32 accumulation (FP32 pipe).
+  apply_bf16_d21  d = 21, r_max = 48, 64 BF16 right-hand sides, BF16 operands,
+                  FP32 accumulation.
+  apply_f64_d21   the same operator and 64 right-hand sides in FP64 (the cost
+                  of one FP64 residual of the refinement).
+  batched_f32 / batched_tf32
+                  256 uneven operators (d 12..20, r_max 16..40, 1..32 RHS) in
+                  one persistent launch per memory wave, replayed from a CUDA
+                  graph, tile variant chosen by the autotuner.
+  refine_bf16_d21 / refine_f64_d21
+                  solve (I + K) x = f, ||K||_2 = 0.5, d = 21, r_max = 48, 64
+                  RHS, to a relative residual of 3e-11 (error <= 1e-10):
+                  refinement with an FP64 residual and a correction of 6
+                  Richardson steps with K in BF16 (or all in FP64).
+
+Throughput is the paper's flop count 4 N sum_k r_k r_{k+1} per right-hand side
+(Sec. 4.2) per second, or right-hand sides solved per second for the solves.
+Multi-GPU (torchrun): every rank runs the same workload on its own inputs
+(independent problems, weak scaling, no collective on the data path); value =
+all ranks' work / max-over-ranks time.
+
+--impl reference times the CPU oracle (plain C, FP64, all host cores) on a
 bounded sample of the same workload: the leading 2^s x 2^s diagonal block of
 the same operator (a QTT matrix with s cores), s chosen so a step takes a few
 seconds.
@@ -20,6 +43,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -35,18 +59,59 @@ sys.path.insert(0, ROOT)
 from paper_1511_06029_gb300 import inputs  # noqa: E402
 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 pipe of one GB300: 1.25 TFLOP/s nominal (no FP64 figure is measured in
-# MEASURED_PEAKS.json; FP64 is a plain ALU pipe here).
+# Plain ALU pipes of one GB300 (no FP64/FP32 figure is measured in
+# MEASURED_PEAKS.json): FP64 1.25 TFLOP/s nominal (2 FMA/clk/SM), FP32
+# 152 SMs x 128 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s.
 FP64_NOMINAL_GFLOPS = 1250.0
+FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.07
 METRIC = "QTT-apply GFLOP/s"
+
+WORKLOADS = {
+    "apply_f64": dict(kind="apply", d=24, rmax=32, seed=2, rhs_seed=3, nrhs=1, compute="f64"),
+    "apply_f64_d22": dict(kind="apply", d=22, rmax=32, seed=2, rhs_seed=3, nrhs=1,
+                          compute="f64"),
+    "laplace_f64": dict(kind="apply", laplace=True, rhs_seed=1, nrhs=1, compute="f64"),
+    "apply_f32_d24": dict(kind="apply", d=24, rmax=32, seed=2, rhs_seed=3, nrhs=1,
+                          compute="f32"),
+    "apply_tf32_d24": dict(kind="apply", d=24, rmax=32, seed=2, rhs_seed=3, nrhs=1,
+                           compute="tf32"),
+    "apply_bf16_d24": dict(kind="apply", d=24, rmax=32, seed=2, rhs_seed=3, nrhs=1,
+                           compute="bf16"),
+    "apply_bf16_d21": dict(kind="apply", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=64,
+                           compute="bf16"),
+    "apply_f64_d21": dict(kind="apply", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=64,
+                          compute="f64"),
+    "batched_f32": dict(kind="batched", compute="f32", count=256, seed=4),
+    "batched_tf32": dict(kind="batched", compute="tf32", count=256, seed=4),
+    "refine_bf16_d21": dict(kind="refine", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=64,
+                            pc="bf16", inner=6),
+    "refine_f64_d21": dict(kind="refine", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=64,
+                           pc="f64", inner=6),
+}
+IO = {"f64": "float64", "f32": "float32", "tf32": "float32", "bf16": "bfloat16"}
+KERNEL = {"f64": "step_f64_kernel", "f32": "step_lp_kernel<F32>",
+          "tf32": "step_lp_kernel<TF32>", "bf16": "step_lp_kernel<BF16>"}
 
 
 # --------------------------------------------------------------- helpers
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_PATH) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
 
 
 class ClockSampler:
@@ -68,8 +133,7 @@ class ClockSampler:
                 ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except (OSError, ValueError):
             self.proc = None
 
@@ -107,29 +171,6 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def measured_peaks():
-    try:
-        with open(PEAKS_PATH) as fh:
-            return json.load(fh)
-    except (OSError, ValueError):
-        return {}
-
-
-# --------------------------------------------------------------- workloads
-def workload_spec(name: str):
-    if name == "apply_f64":
-        return {"name": "qtt_apply_f64_d24_r32", "d": 24, "rmax": 32, "seed": 2,
-                "rhs_seed": 3, "nrhs": 1}
-    if name == "apply_f64_d22":
-        # smaller case of the same family, for profiler captures (a few GB)
-        return {"name": "qtt_apply_f64_d22_r32", "d": 22, "rmax": 32, "seed": 2,
-                "rhs_seed": 3, "nrhs": 1}
-    if name == "laplace_f64":
-        return {"name": "qtt_apply_f64_laplace_8cubed", "laplace": True, "nrhs": 1,
-                "rhs_seed": 1}
-    raise SystemExit(f"unknown workload {name}")
-
-
 def make_operator(spec):
     if spec.get("laplace"):
         op, _ = inputs.laplace_volume(8, 1e-8)
@@ -151,9 +192,9 @@ def leading_block(op, s: int):
     return inputs.QTTData(list(op.ranks[:s]) + [1], cores, {"block_of": op.d})
 
 
-def oracle_sample(op, target_s: float = 12.0, min_d: int = 12):
-    """Pick the largest leading block whose oracle apply takes about target_s
-    seconds (timed on a small block first)."""
+def oracle_sample(op, target_s: float = 8.0, min_d: int = 10):
+    """The largest leading block whose oracle apply takes about target_s
+    seconds (rate measured on a 2^16 block first)."""
     import oracle
     oracle.build()
     s = min(op.d, 16)
@@ -161,8 +202,7 @@ def oracle_sample(op, target_s: float = 12.0, min_d: int = 12):
     x = inputs.gaussian_rhs(blk.N, 1, 99)[0]
     t0 = time.perf_counter()
     oracle.apply(blk, x)
-    t = time.perf_counter() - t0
-    rate = blk.flops() / max(t, 1e-6)
+    rate = blk.flops() / max(time.perf_counter() - t0, 1e-6)
     while s < op.d and leading_block(op, s + 1).flops() / rate <= target_s:
         s += 1
     while s > min_d and leading_block(op, s).flops() / rate > 2.5 * target_s:
@@ -170,11 +210,17 @@ def oracle_sample(op, target_s: float = 12.0, min_d: int = 12):
     return leading_block(op, s), s
 
 
-def host_cores():
-    try:
-        return len(os.sched_getaffinity(0))
-    except AttributeError:
-        return os.cpu_count() or 1
+def oracle_baseline(op, target_s=8.0):
+    import oracle
+    blk, s = oracle_sample(op, target_s)
+    xb = inputs.gaussian_rhs(blk.N, 1, 5)[0]
+    t0 = time.perf_counter()
+    oracle.apply(blk, xb)
+    dt = time.perf_counter() - t0
+    return {"value": blk.flops() / dt / 1e9, "unit": "GFLOP/s", "cores": host_cores(),
+            "kind": "oracle",
+            "sample": f"leading 2^{s} x 2^{s} diagonal block of the d={op.d} operator, one FP64 "
+                      f"apply ({blk.flops():.3e} flops, {dt:.1f} s), all host threads"}
 
 
 # --------------------------------------------------------------- reference
@@ -183,9 +229,13 @@ def run_reference(args, spec):
     if rank != 0:
         return 0
     import oracle
-    op = make_operator(spec)
+    if spec["kind"] == "batched":
+        it = inputs.batched_workload(count=1, seed=spec["seed"])[0]
+        op = inputs.synthetic_operator(it["d"], it["rmax"], it["op_seed"])
+    else:
+        op = make_operator(spec)
     blk, s = oracle_sample(op, target_s=float(os.environ.get("QTT_REF_STEP_S", "8")))
-    x = inputs.gaussian_rhs(blk.N, 1, spec["rhs_seed"])[0]
+    x = inputs.gaussian_rhs(blk.N, 1, spec.get("rhs_seed", 1))[0]
     for _ in range(args.warmup):
         oracle.apply(blk, x)
     t0 = time.perf_counter()
@@ -193,16 +243,15 @@ def run_reference(args, spec):
         oracle.apply(blk, x)
     dt = time.perf_counter() - t0
     value = blk.flops() * args.steps / dt / 1e9
-    cores = host_cores()
     sample = (f"leading 2^{s} x 2^{s} diagonal block of the d={op.d} operator "
-              f"({blk.flops():.3e} flops per step), FP64 oracle, all host threads")
+              f"({blk.flops():.3e} flops per step), FP64 oracle apply, all host threads")
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": spec["name"], "sample": sample},
-            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores,
+            "config": {"workload": args.workload, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": host_cores(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -210,7 +259,243 @@ def run_reference(args, spec):
     return 0
 
 
-# --------------------------------------------------------------- ours
+# --------------------------------------------------------------- workloads
+class ApplyRun:
+    def __init__(self, spec, rank, stream):
+        import torch
+        from paper_1511_06029_gb300 import qtt
+        self.spec = spec
+        self.data = make_operator(spec)
+        self.nrhs = spec["nrhs"]
+        self.compute = spec["compute"]
+        tdt = getattr(torch, IO[self.compute])
+        packs = () if self.compute == "f64" else (self.compute,)
+        self.op = qtt.Operator(self.data, packs=packs, stream=stream)
+        self.x_host = inputs.gaussian_rhs(self.data.N, self.nrhs, spec["rhs_seed"] + 1000 * rank)
+        self.x = torch.from_numpy(self.x_host).to("cuda").to(tdt)
+        self.y = torch.empty_like(self.x)
+        self.stream = stream
+        self.flops = self.data.flops(self.nrhs)
+        self.launches = self.data.d * ((self.nrhs + 65534) // 65535)
+        self.xh = self.x.cpu().pin_memory()
+        self.yh = torch.empty_like(self.xh).pin_memory()
+        self.xd = torch.empty_like(self.x)
+        self.yd = torch.empty_like(self.x)
+        self.unit = "GFLOP/s"
+
+    def step(self):
+        self.op.apply(self.x, out=self.y, compute=self.compute, stream=self.stream)
+
+    def e2e_step(self):
+        self.xd.copy_(self.xh, non_blocking=True)
+        self.op.apply(self.xd, out=self.yd, compute=self.compute)
+        self.yh.copy_(self.yd, non_blocking=True)
+
+    def e2e_bytes(self):
+        b = self.x.numel() * self.x.element_size()
+        return b, b
+
+    def e2e_check(self):
+        import torch
+        return bool(torch.equal(self.yh, self.y.cpu()))
+
+    def work(self):
+        return self.flops / 1e9
+
+    def roofline(self, mean_s):
+        achieved = self.flops / mean_s / 1e9
+        if self.compute == "f64":
+            peak, src = FP64_NOMINAL_GFLOPS, "FP64 pipe, 1.25 TFLOP/s nominal (2 FMA/clk/SM)"
+        else:
+            peak, src = FP32_NOMINAL_GFLOPS, ("FP32 pipe, 152 SMs x 128 FMA/clk x 2.07 GHz "
+                                               "(the kernel multiplies on CUDA cores)")
+        r = {"bound": "alu", "kernel": KERNEL[self.compute], "achieved": achieved, "peak": peak,
+             "unit": "GFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": src}
+        if self.compute in ("bf16", "tf32"):
+            pk = measured_peaks().get("bf16_tflops")
+            if pk:
+                tc = pk * 1e3 * (0.5 if self.compute == "tf32" else 1.0)
+                r["frac_of_tensor_peak"] = achieved / tc
+                r["tensor_peak_gflops"] = tc
+        return r
+
+    def config(self):
+        d = self.data
+        inter = max(d.ranks) * d.N * self.nrhs * (8 if self.compute == "f64" else
+                                                  (2 if self.compute == "bf16" else 4))
+        return {"workload": self.spec["name"], "d": d.d, "N": d.N, "rmax": max(d.ranks),
+                "nrhs_per_gpu": self.nrhs, "sum_r_r": d.sigma,
+                "flops_per_step_per_gpu": self.flops, "compute": self.compute,
+                "l2": f"not flushed: each step streams 2 x {inter / 1e9:.2f} GB of "
+                      f"intermediates through the 129 MB L2" if inter > 129e6 else
+                      "inputs smaller than L2 (latency-bound case)"}
+
+    def cpu_baseline(self):
+        return oracle_baseline(self.data)
+
+    def close(self):
+        self.op.close()
+
+
+class BatchedRun:
+    def __init__(self, spec, rank, stream):
+        import torch
+        from paper_1511_06029_gb300 import qtt
+        self.spec = spec
+        self.items = inputs.batched_workload(count=spec["count"], seed=spec["seed"] + 97 * rank)
+        self.compute = spec["compute"]
+        self.ops, self.xs, self.ys = [], [], []
+        self.flops = 0.0
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(spec["seed"] + 97 * rank)
+        for it in self.items:
+            data = inputs.synthetic_operator(it["d"], it["rmax"], it["op_seed"])
+            self.flops += data.flops(it["nrhs"])
+            self.ops.append(qtt.Operator(data, packs=(self.compute,), stream=stream))
+            x = torch.randn(it["nrhs"], data.N, device="cuda", dtype=torch.float32, generator=gen)
+            self.xs.append(x)
+            self.ys.append(torch.empty_like(x))
+        self.batch = qtt.Batch(self.ops, self.xs, self.ys, compute=self.compute, stream=stream)
+        self.variant, self.tuned_s = self.batch.autotune(reps=1, stream=stream)
+        self.info = self.batch.info()
+        self.stream = stream
+        self.xh = [x.cpu().pin_memory() for x in self.xs]
+        self.yh = [torch.empty_like(h).pin_memory() for h in self.xh]
+        self.launches = self.info["waves"]
+        self.unit = "GFLOP/s"
+
+    def step(self):
+        self.batch.run(stream=self.stream)
+
+    def e2e_step(self):
+        import torch
+        s = torch.cuda.current_stream()
+        for x, h in zip(self.xs, self.xh):
+            x.copy_(h, non_blocking=True)
+        self.batch.run(stream=s)
+        for y, h in zip(self.ys, self.yh):
+            h.copy_(y, non_blocking=True)
+
+    def e2e_bytes(self):
+        b = sum(x.numel() * 4 for x in self.xs)
+        return b, b
+
+    def e2e_check(self):
+        import torch
+        return all(bool(torch.equal(h, y.cpu())) for h, y in zip(self.yh[:8], self.ys[:8]))
+
+    def work(self):
+        return self.flops / 1e9
+
+    def roofline(self, mean_s):
+        achieved = self.flops / mean_s / 1e9
+        r = {"bound": "alu", "kernel": f"batch_kernel<{self.variant}>", "achieved": achieved,
+             "peak": FP32_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+             "frac": achieved / FP32_NOMINAL_GFLOPS, "traffic": None,
+             "peak_source": "FP32 pipe, 152 SMs x 128 FMA/clk x 2.07 GHz"}
+        pk = measured_peaks().get("bf16_tflops")
+        if pk and self.compute == "tf32":
+            r["frac_of_tensor_peak"] = achieved / (pk * 1e3 * 0.5)
+        return r
+
+    def config(self):
+        return {"workload": self.spec["name"], "operators": len(self.items),
+                "d_range": [12, 20], "rmax_range": [16, 40], "nrhs_range": [1, 32],
+                "total_rhs": sum(it["nrhs"] for it in self.items),
+                "flops_per_step_per_gpu": self.flops, "compute": self.compute,
+                "waves": self.info["waves"], "grid": self.info["grid"],
+                "autotuned_variant_pairs_per_lane": self.variant,
+                "scratch_gb": self.info["scratch_bytes"] / 1e9,
+                "graph": "all waves captured in one CUDA graph",
+                "l2": "not flushed: each step streams tens of GB of intermediates"}
+
+    def cpu_baseline(self):
+        it = self.items[0]
+        return oracle_baseline(inputs.synthetic_operator(it["d"], it["rmax"], it["op_seed"]))
+
+    def close(self):
+        self.batch.close()
+        for o in self.ops:
+            o.close()
+
+
+class RefineRun:
+    def __init__(self, spec, rank, stream):
+        import torch
+        from paper_1511_06029_gb300 import qtt
+        self.qtt = qtt
+        self.spec = spec
+        self.data = inputs.scaled_operator(spec["d"], spec["rmax"], spec["seed"])
+        packs = () if spec["pc"] == "f64" else (spec["pc"],)
+        self.op = qtt.Operator(self.data, packs=packs, stream=stream)
+        self.nrhs = spec["nrhs"]
+        self.f_host = inputs.gaussian_rhs(self.data.N, self.nrhs, spec["rhs_seed"] + 1000 * rank)
+        self.f = torch.from_numpy(self.f_host).to("cuda")
+        self.x = torch.empty_like(self.f)
+        self.stream = stream
+        self.fh = self.f.cpu().pin_memory()
+        self.xh = torch.empty_like(self.fh).pin_memory()
+        self.fd, self.xd = torch.empty_like(self.f), torch.empty_like(self.f)
+        self.unit = "solves/s"
+        self.last_info = None
+        self.launches = 0
+
+    def _solve(self, f, x, stream):
+        _, info = self.qtt.solve(self.op, None, f, kind="refine", tol=3e-11, max_iter=60,
+                                 precond_compute=self.spec["pc"], inner_iters=self.spec["inner"],
+                                 out=x, stream=stream)
+        self.last_info = info
+
+    def step(self):
+        self._solve(self.f, self.x, self.stream)
+
+    def e2e_step(self):
+        self.fd.copy_(self.fh, non_blocking=True)
+        self._solve(self.fd, self.xd, None)
+        self.xh.copy_(self.xd, non_blocking=True)
+
+    def e2e_bytes(self):
+        b = self.f.numel() * 8
+        return b, b
+
+    def e2e_check(self):
+        import torch
+        return bool(torch.equal(self.xh, self.x.cpu()))
+
+    def work(self):
+        return float(self.nrhs)
+
+    def roofline(self, mean_s):
+        # dominated by the FP64 residual applies: report the FP64 pipe share
+        its = self.last_info[0][0] if self.last_info else 0
+        f64_flops = self.data.flops(self.nrhs) * its
+        if self.spec["pc"] == "f64":
+            f64_flops += self.data.flops(self.nrhs) * its * (self.spec["inner"] + 1)
+        achieved = f64_flops / mean_s / 1e9
+        return {"bound": "alu", "kernel": "step_f64_kernel (FP64 residual applies)",
+                "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_NOMINAL_GFLOPS, "traffic": None,
+                "peak_source": "FP64 pipe, 1.25 TFLOP/s nominal"}
+
+    def config(self):
+        its = self.last_info[0][0] if self.last_info else None
+        rel = max(r for _, r, _ in self.last_info) if self.last_info else None
+        return {"workload": self.spec["name"], "d": self.data.d, "N": self.data.N,
+                "rmax": max(self.data.ranks), "nrhs_per_gpu": self.nrhs,
+                "knorm": 0.5, "tol_rel_residual": 3e-11, "inner_iters": self.spec["inner"],
+                "precond_compute": self.spec["pc"], "outer_iterations": its,
+                "max_rel_residual": rel}
+
+    def cpu_baseline(self):
+        return oracle_baseline(self.data)
+
+    def close(self):
+        self.op.close()
+
+
+RUNNERS = {"apply": ApplyRun, "batched": BatchedRun, "refine": RefineRun}
+
+
 def run_ours(args, spec):
     import torch
     rank, world, local = dist_env()
@@ -222,26 +507,25 @@ def run_ours(args, spec):
     from paper_1511_06029_gb300 import build as qbuild, qtt
     if not os.path.exists(qtt.LIB_PATH):
         qbuild.build()
-    data = make_operator(spec)
-    nrhs = spec["nrhs"]
-    N = data.N
-    flops = data.flops(nrhs)
-    x_host = inputs.gaussian_rhs(N, nrhs, spec["rhs_seed"] + 1000 * rank)
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        op = qtt.Operator(data, stream=stream)
-        x = torch.from_numpy(x_host).to("cuda")
-        y = torch.empty_like(x)
-    stream.synchronize()
+    run = RUNNERS[spec["kind"]](spec, rank, stream)
+    torch.cuda.synchronize()
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    # ---- device-resident timing
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_1511_06029_gb300 import qtt as _q
     for _ in range(args.warmup):
-        op.apply(x, out=y, stream=stream)
-    stream.synchronize()
+        run.step()
+    torch.cuda.synchronize()
     barrier()
     sampler = ClockSampler(local)
     sampler.start()
@@ -249,88 +533,55 @@ def run_ours(args, spec):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     torch.cuda.synchronize()
     barrier()
+    launches0 = _q.kernel_launches()
     ev[0].record(stream)
     for i in range(args.steps):
-        op.apply(x, out=y, stream=stream)
+        run.step()
         ev[i + 1].record(stream)
+    launches = _q.kernel_launches() - launches0
     stream.synchronize()
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    t_local = total_ms / 1e3
-    t_max = t_local
-    if dist is not None:
-        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = flops * args.steps * world / t_max / 1e9
+    total_s = ev[0].elapsed_time(ev[-1]) / 1e3
+    t_max = max_over_ranks(total_s)
+    value = run.work() * args.steps * world / t_max
 
-    # ---- end to end: pinned host x -> device, apply, device -> pinned host y
-    xh = torch.from_numpy(x_host).pin_memory()
-    yh = torch.empty_like(xh).pin_memory()
-    xd = torch.empty_like(x)
-    yd = torch.empty_like(x)
+    # end to end through the public API with pinned host buffers
     for _ in range(max(1, min(args.warmup, 2))):
-        xd.copy_(xh, non_blocking=True)
-        op.apply(xd, out=yd)
-        yh.copy_(yd, non_blocking=True)
+        run.e2e_step()
     torch.cuda.synchronize()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        xd.copy_(xh, non_blocking=True)
-        op.apply(xd, out=yd)
-        yh.copy_(yd, non_blocking=True)
+        run.e2e_step()
     e1.record()
     torch.cuda.synchronize()
-    e2e_t = e0.elapsed_time(e1) / 1e3
-    if dist is not None:
-        t = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_value = flops * args.steps * world / e2e_t / 1e9
-    ok_e2e = bool(torch.equal(yh, y.cpu()))
-
-    launches_per_apply = data.d * ((nrhs + 65534) // 65535)
-    mean_ms = total_ms / args.steps
-    achieved = flops / (mean_ms / 1e3) / 1e9
+    e2e_t = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    h2d, d2h = run.e2e_bytes()
 
     line = {
-        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+        "metric": METRIC if run.unit == "GFLOP/s" else "served solves/s",
+        "value": value, "unit": run.unit, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": spec["name"], "d": data.d, "N": N,
-                   "rmax": max(data.ranks), "nrhs_per_gpu": nrhs,
-                   "sum_r_r": data.sigma, "flops_per_step_per_gpu": flops,
-                   "l2": "not flushed: each step streams 2 x 4.3 GB of intermediates (> 129 MB L2)",
-                   "parallelism": f"replicas x{world} (independent right-hand sides)"},
-        "roofline": {"bound": "alu", "kernel": "step_f64_kernel",
-                     "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-                     "frac": achieved / FP64_NOMINAL_GFLOPS, "traffic": None,
-                     "peak_source": "FP64 pipe, 1.25 TFLOP/s nominal (no measured FP64 peak)",
-                     "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)},
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": spec.get("compute", spec.get("pc", "f64")), "data": "synthetic",
+        "config": dict(run.config(), parallelism=f"replicas x{world} (independent problems)"),
+        "roofline": dict(run.roofline(total_s / args.steps),
+                         step_ms_min=min(step_ms), step_ms_max=max(step_ms)),
         "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": int(x.numel() * 8),
-                "d2h_bytes_per_step": int(y.numel() * 8), "result_matches_device": ok_e2e},
-        "gpu_launches": launches_per_apply * args.steps,
+        "e2e": {"value": run.work() * args.steps * world / e2e_t, "unit": run.unit,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "result_matches_device": run.e2e_check()},
+        # kernels of libqtt launched in the timed region (library counter); a
+        # batch replays a CUDA graph with one persistent launch per wave
+        "gpu_launches": int(launches) if launches else run.launches * args.steps,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        blk, s = oracle_sample(data, target_s=8.0)
-        xb = inputs.gaussian_rhs(blk.N, 1, 5)[0]
-        t0 = time.perf_counter()
-        oracle.apply(blk, xb)
-        dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {
-            "value": blk.flops() / dt / 1e9, "unit": "GFLOP/s", "cores": host_cores(),
-            "kind": "oracle",
-            "sample": f"leading 2^{s} x 2^{s} diagonal block of the same operator, one apply "
-                      f"({blk.flops():.3e} flops, {dt:.1f} s), FP64 oracle, all host threads"}
-    op.close()
+        line["cpu_baseline"] = run.cpu_baseline()
+    run.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -344,12 +595,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="apply_f64")
+    ap.add_argument("--workload", default="apply_f64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
-    spec = workload_spec(args.workload)
+    spec = dict(WORKLOADS[args.workload], name=args.workload)
     if args.impl == "reference":
         return run_reference(args, spec)
     return run_ours(args, spec)

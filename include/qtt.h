@@ -158,9 +158,11 @@ typedef enum {
                            (Tables 1-2, "Solve" column).  K unused. */
   QTT_SOLVE_GMRES = 1,  /* right-preconditioned GMRES(restart) with P
                            (Sec. 5.3: QTT preconditioner inside GMRES). */
-  QTT_SOLVE_REFINE = 2  /* iterative refinement x <- x + P (f - (a I + K) x)
-                           with the residual in FP64 and P applied in
-                           prm->precond_compute. */
+  QTT_SOLVE_REFINE = 2  /* iterative refinement x <- x + M (f - (a I + K) x)
+                           with the residual in FP64 (the spec mixed-
+                           precision scheme): M = P, or inner_iters steps of
+                           a low-precision Richardson iteration on
+                           (a I + K) z = r preconditioned by P. */
 } qtt_solve_kind;
 
 typedef struct {
@@ -168,8 +170,15 @@ typedef struct {
   double a;              /* A = a I + K */
   double tol;            /* stop when ||f - A x||_2 <= tol ||f||_2 */
   int restart;           /* GMRES cycle length m (>= 1) */
-  int max_iter;          /* cap on P applications (REFINE) or Arnoldi steps */
-  qtt_dtype precond_compute; /* arithmetic of the P applies */
+  int max_iter;          /* cap on outer corrections (REFINE) or Arnoldi steps */
+  qtt_dtype precond_compute; /* arithmetic of the P applies (and of the inner
+                                K applies of REFINE) */
+  int inner_iters;       /* REFINE only: 0 = the correction is z = P r; s > 0 =
+                            z from s inner steps z <- z + P (r - (a z + K z))
+                            (P = identity if NULL) with K and P applied in
+                            precond_compute and vectors in FP64, starting
+                            from z = P r.  K then needs the matching
+                            QTT_PACK_* copy. */
 } qtt_solve_params;
 
 typedef struct {
@@ -195,8 +204,49 @@ qtt_status qtt_solve(const qtt_op *K, const qtt_op *P, const double *f,
                      const qtt_solve_params *prm, qtt_solve_info *info,
                      void *stream);
 
+/* ------------------------------------------------------- batched applies */
+/* A batch applies many independent, uneven QTT operators (different d,
+ * ranks and numbers of right-hand sides) to their own vectors: y_i = A_i x_i.
+ * Each wave of operators whose scratch fits the memory budget is ONE
+ * persistent kernel launch that walks a step-major work list of (operator,
+ * core step, right-hand side, chunk of position pairs) items, each item one
+ * Algorithm 2 contraction; an item waits (bounded) until its operator's
+ * previous step is complete.  All waves are captured in one CUDA graph at
+ * creation; qtt_batch_run replays it.  The paper has no batched form; it is
+ * the same Algorithm 2 per operator.
+ *   ops[i], nrhs[i] (>= 1), x[i], y[i] (device FP32, N_i x nrhs[i], leading
+ *   dimension ld[i] >= N_i), bound at creation and read at every run.
+ *   compute     : QTT_F32 or QTT_TF32 (operands rounded to TF32, FP32
+ *                 accumulate); each operator needs the matching QTT_PACK_*.
+ *   mem_budget  : bytes of intermediate per wave (0 = min(free/3, 64 GiB)).
+ * Ranks above 64 return QTT_ERR_UNSUPPORTED. */
+typedef struct qtt_batch qtt_batch;
+qtt_status qtt_batch_create(qtt_batch **out, int nops, const qtt_op *const *ops,
+                            const int64_t *nrhs, const void *const *x,
+                            void *const *y, const int64_t *ld,
+                            qtt_dtype compute, size_t mem_budget,
+                            void *stream);
+/* Launch the captured graph on `stream` (asynchronous). */
+qtt_status qtt_batch_run(qtt_batch *B, void *stream);
+/* Synchronise `stream`; QTT_ERR_TIMEOUT if a dependency wait in the last
+ * runs gave up (the status word is then cleared). */
+qtt_status qtt_batch_status(qtt_batch *B, void *stream);
+/* Tile variant: 2 or 4 position-pair columns per lane (64 or 128 pairs per
+ * work item); re-plans and re-captures. */
+qtt_status qtt_batch_set_variant(qtt_batch *B, int variant, void *stream);
+/* Time every variant (`reps` runs each, after one warm-up) and keep the
+ * fastest; reports it and its seconds per run. */
+qtt_status qtt_batch_autotune(qtt_batch *B, int reps, void *stream,
+                              int *chosen, double *seconds_per_run);
+qtt_status qtt_batch_info(const qtt_batch *B, int *waves, int *variant,
+                          int *grid, double *flops, size_t *scratch_bytes);
+qtt_status qtt_batch_destroy(qtt_batch *B);
+
 /* ------------------------------------------------------------ diagnostics */
 const char *qtt_status_string(qtt_status s);
+/* Kernels launched by the library since it was loaded (all threads); for
+ * counting the launches inside a timed region. */
+uint64_t qtt_kernel_launches(void);
 /* Message of the last failing call on this thread ("" if none). */
 const char *qtt_last_error(void);
 /* Synchronise `stream` and report device-side errors (QTT_ERR_CUDA for a

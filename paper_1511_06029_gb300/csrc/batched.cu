@@ -1,0 +1,588 @@
+// Batched apply of many uneven QTT operators (different d, ranks and numbers
+// of right-hand sides) in one persistent launch per memory wave, the waves
+// captured in one CUDA graph.
+//
+// Work list.  For one wave of operators the items are all (operator o, core
+// step k, right-hand side c, chunk of 32*TN position pairs), ordered step-
+// major: every operator's step-0 chunks, then every operator's step-1
+// chunks, and so on.  Each item is the Algorithm 2 contraction of one chunk
+// (all output ranks).  CTAs take items from a global counter in that order;
+// item (o, k, ...) first waits until all chunks of (o, k-1) are done.  Those
+// were taken earlier by CTAs that are already running and never wait on a
+// later item, so the waits always end; they are bounded anyway (a clock
+// budget, after which the kernel raises the status word to QTT_ERR_TIMEOUT
+// and every CTA leaves).
+//
+// Per item the CTA stages the input chunk (r_k ranks x 2 x 32*TN positions)
+// in shared memory (L2-coherent loads: the intermediate was written by other
+// CTAs of this launch), then each warp computes a block of TB output ranks
+// for the 32*TN pairs with FP32 multiply-adds (TF32 mode rounds operands to
+// TF32 as they are staged; cores are packed TF32-rounded).  TB = ceil(r_out/8)
+// so the eight warps cover all output ranks in one pass.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "qtt_internal.h"
+#include "step_lp.h"
+
+namespace qtt {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxRank = 64;
+constexpr int kMaxD = 30;
+
+struct BOp {
+  int d;
+  int64_t N, nrhs, ld;
+  const float *x;
+  float *y;
+  float *buf0, *buf1;
+  const float *cores;  // packed [a][j][rpad][i] per core
+  int ranks[kMaxD + 1];
+  int rpad[kMaxD + 1];
+  int64_t coff[kMaxD + 1];
+};
+
+struct BSeg {
+  int op, k, dep;
+  int64_t first, ntiles, tiles_per_rhs;
+};
+
+struct BWave {
+  const BOp *ops;
+  const BSeg *segs;
+  int nseg;
+  int64_t total;
+  unsigned *done;
+  unsigned long long *next;
+  int *status;
+  int tf32;
+  long long wait_budget;  // clock cycles
+};
+
+__device__ __forceinline__ float tf32_rne_b(float x) {
+  unsigned u = __float_as_uint(x);
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0x0fffu + ((u >> 13) & 1u);
+    u &= 0xffffe000u;
+  }
+  return __uint_as_float(u);
+}
+
+template <int TB, int TN>
+__device__ __forceinline__ void rank_block(const float *sm, const float *G, int rin, int rpad,
+                                           int b0, int rout, int lane, int npair_chunk,
+                                           float *out, int64_t N, int64_t q0, int k,
+                                           int64_t npairs) {
+  float acc[TB][2][TN];
+#pragma unroll
+  for (int t = 0; t < TB; ++t)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int m = 0; m < TN; ++m) acc[t][i][m] = 0.0f;
+  for (int a = 0; a < rin; ++a) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const float *srow = sm + (size_t)(2 * a + j) * npair_chunk;
+      float v[TN];
+#pragma unroll
+      for (int m = 0; m < TN; ++m) v[m] = srow[lane + 32 * m];
+      const float2 *g2 = reinterpret_cast<const float2 *>(G + ((int64_t)(2 * a + j) * rpad + b0) * 2);
+#pragma unroll
+      for (int t = 0; t < TB; ++t) {
+        // ranks past the padded row (last warp, r_out near a multiple of 8
+        // times TB) contribute nothing and must not be read
+        const float2 g = b0 + t < rpad ? __ldg(g2 + t) : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int m = 0; m < TN; ++m) {
+          acc[t][0][m] = fmaf(g.x, v[m], acc[t][0][m]);
+          acc[t][1][m] = fmaf(g.y, v[m], acc[t][1][m]);
+        }
+      }
+    }
+  }
+  const int64_t bit = (int64_t)1 << k, low = bit - 1;
+#pragma unroll
+  for (int t = 0; t < TB; ++t) {
+    const int b = b0 + t;
+    if (b >= rout) break;
+#pragma unroll
+    for (int m = 0; m < TN; ++m) {
+      const int64_t q = q0 + lane + 32 * m;
+      if (q >= npairs) continue;
+      const int64_t p0 = ((q & ~low) << 1) | (q & low);
+      out[(int64_t)b * N + p0] = acc[t][0][m];
+      out[(int64_t)b * N + p0 + bit] = acc[t][1][m];
+    }
+  }
+}
+
+template <int TN>
+__global__ void __launch_bounds__(kThreads) batch_kernel(BWave w) {
+  extern __shared__ float sm[];
+  __shared__ long long s_item;
+  __shared__ int s_seg;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int PC = 32 * TN;  // pairs per item
+  for (;;) {
+    if (tid == 0) {
+      const long long item = (long long)atomicAdd(w.next, 1ull);
+      s_item = item;
+      int abort = *(volatile int *)w.status != 0;
+      int seg = 0;
+      if (!abort && item < w.total) {
+        int lo = 0, hi = w.nseg - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (w.segs[mid].first <= item) lo = mid; else hi = mid - 1;
+        }
+        seg = lo;
+        const int dep = w.segs[seg].dep;
+        if (dep >= 0) {
+          const unsigned target = (unsigned)w.segs[dep].ntiles;
+          const long long t0 = clock64();
+          while (*(volatile unsigned *)(w.done + dep) < target) {
+            if (*(volatile int *)w.status != 0) { abort = 1; break; }
+            if (clock64() - t0 > w.wait_budget) {
+              atomicCAS(w.status, 0, (int)QTT_ERR_TIMEOUT);
+              abort = 1;
+              break;
+            }
+            __nanosleep(64);
+          }
+          __threadfence();
+        }
+      }
+      s_seg = seg;
+      s_abort = abort;
+    }
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= w.total || s_abort) return;
+    const BSeg sg = w.segs[s_seg];
+    const BOp &op = w.ops[sg.op];
+    const int k = sg.k;
+    const int rin = op.ranks[k], rout = op.ranks[k + 1];
+    const int64_t N = op.N, npairs = N >> 1;
+    const int64_t tile = item - sg.first;
+    const int64_t c = tile / sg.tiles_per_rhs;
+    const int64_t q0 = (tile % sg.tiles_per_rhs) * PC;
+    const int64_t bit = (int64_t)1 << k, low = bit - 1;
+    // ---- stage the input chunk: sm[(2a + j) * PC + qq]
+    const float *in = k == 0 ? op.x + c * op.ld
+                             : ((k - 1) & 1 ? op.buf1 : op.buf0) + c * (int64_t)rin * N;
+    for (int e = tid; e < rin * 2 * PC; e += kThreads) {
+      const int qq = e % PC, aj = e / PC;
+      const int a = aj >> 1, j = aj & 1;
+      const int64_t q = q0 + qq;
+      float v = 0.0f;
+      if (q < npairs) {
+        const int64_t p = (((q & ~low) << 1) | (q & low)) + (j ? bit : 0);
+        v = k == 0 ? __ldg(in + p) : __ldcg(in + (int64_t)a * N + p);
+      }
+      sm[e] = w.tf32 ? tf32_rne_b(v) : v;
+    }
+    __syncthreads();
+    float *out = k == op.d - 1 ? op.y + c * op.ld
+                               : (k & 1 ? op.buf1 : op.buf0) + c * (int64_t)rout * N;
+    const float *G = op.cores + op.coff[k];
+    const int rpad = op.rpad[k + 1];
+    const int TB = (rout + 7) / 8;
+    const int b0 = warp * TB;
+    if (b0 < rout) {
+      switch (TB) {
+        case 1: rank_block<1, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+        case 2: rank_block<2, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+        case 3: rank_block<3, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+        case 4: rank_block<4, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+        case 5: rank_block<5, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+        case 6: rank_block<6, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+        case 7: rank_block<7, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+        default: rank_block<8, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicAdd(w.done + s_seg, 1u);
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host
+struct WaveDev {
+  std::vector<int> ops;
+  BOp *d_ops = nullptr;
+  BSeg *d_segs = nullptr;
+  unsigned *d_done = nullptr;
+  int nseg = 0;
+  int64_t total = 0;
+  int max_rin = 1;
+};
+
+}  // namespace qtt
+
+struct qtt_batch {
+  std::vector<const qtt_op *> ops;
+  std::vector<int64_t> nrhs, ld;
+  std::vector<const float *> x;
+  std::vector<float *> y;
+  qtt_dtype compute = QTT_F32;
+  size_t budget = 0;
+  int variant = 4;  // TN
+  std::vector<qtt::WaveDev> waves;
+  float *scratch = nullptr;
+  size_t scratch_bytes = 0;
+  unsigned long long *d_next = nullptr;  // one counter per wave
+  int *d_status = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double flops = 0.0;
+  int grid = 0;
+};
+
+namespace qtt {
+namespace {
+
+size_t op_scratch_bytes(const qtt_op *A, int64_t nrhs) {
+  if (A->d <= 1) return 0;
+  return (size_t)2 * A->rmax_inner * ((size_t)1 << A->d) * (size_t)nrhs * sizeof(float);
+}
+
+void free_waves(qtt_batch *B) {
+  for (auto &w : B->waves) {
+    if (w.d_ops) cudaFree(w.d_ops);
+    if (w.d_segs) cudaFree(w.d_segs);
+    if (w.d_done) cudaFree(w.d_done);
+  }
+  B->waves.clear();
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  B->exec = nullptr;
+  B->graph = nullptr;
+}
+
+qtt_status build_plan(qtt_batch *B, cudaStream_t st) {
+  free_waves(B);
+  const int TN = B->variant;
+  const int PC = 32 * TN;
+  // greedy waves in input order under the memory budget
+  std::vector<std::vector<int>> groups;
+  size_t cur = 0, maxw = 0;
+  for (int i = 0; i < (int)B->ops.size(); ++i) {
+    const size_t need = op_scratch_bytes(B->ops[i], B->nrhs[i]);
+    if (need > B->budget)
+      return fail(QTT_ERR_OOM, "batch: one operator's scratch exceeds the memory budget");
+    if (groups.empty() || cur + need > B->budget) {
+      groups.emplace_back();
+      cur = 0;
+    }
+    groups.back().push_back(i);
+    cur += need;
+    maxw = std::max(maxw, cur);
+  }
+  if (B->scratch_bytes < maxw) {
+    if (B->scratch) cudaFree(B->scratch);
+    B->scratch = nullptr;
+    B->scratch_bytes = 0;
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    if (maxw + ((size_t)256 << 20) > fr) return fail(QTT_ERR_OOM, "batch: scratch does not fit");
+    QTT_CUDA_TRY(cudaMalloc(&B->scratch, maxw));
+    B->scratch_bytes = maxw;
+  }
+  if (B->d_next) cudaFree(B->d_next);
+  B->d_next = nullptr;
+  QTT_CUDA_TRY(cudaMalloc(&B->d_next, sizeof(unsigned long long) * std::max<size_t>(1, groups.size())));
+  for (auto &g : groups) {
+    WaveDev wv;
+    wv.ops = g;
+    std::vector<BOp> hops;
+    size_t off = 0;
+    int maxd = 0;
+    for (int i : g) {
+      const qtt_op *A = B->ops[i];
+      BOp o;
+      std::memset(&o, 0, sizeof(o));
+      o.d = A->d;
+      o.N = (int64_t)1 << A->d;
+      o.nrhs = B->nrhs[i];
+      o.ld = B->ld[i];
+      o.x = B->x[i];
+      o.y = B->y[i];
+      const size_t half = (size_t)A->rmax_inner * (size_t)o.N * (size_t)o.nrhs;
+      o.buf0 = reinterpret_cast<float *>(reinterpret_cast<char *>(B->scratch) + off);
+      o.buf1 = o.buf0 + half;
+      off += op_scratch_bytes(A, o.nrhs);
+      o.cores = B->compute == QTT_TF32 ? A->mtf32 : A->m32;
+      for (int k = 0; k <= A->d; ++k) {
+        o.ranks[k] = A->ranks[k];
+        o.rpad[k] = A->rpad[k];
+        o.coff[k] = A->offlp[k];
+        wv.max_rin = std::max(wv.max_rin, A->ranks[k]);
+      }
+      hops.push_back(o);
+      maxd = std::max(maxd, A->d);
+    }
+    // segments, step-major
+    std::vector<BSeg> segs;
+    std::vector<std::vector<int>> seg_of(g.size(), std::vector<int>(maxd, -1));
+    int64_t first = 0;
+    for (int k = 0; k < maxd; ++k)
+      for (int li = 0; li < (int)g.size(); ++li) {
+        const BOp &o = hops[li];
+        if (k >= o.d) continue;
+        BSeg s;
+        s.op = li;
+        s.k = k;
+        s.dep = k > 0 ? seg_of[li][k - 1] : -1;
+        s.tiles_per_rhs = ((o.N >> 1) + PC - 1) / PC;
+        s.ntiles = s.tiles_per_rhs * o.nrhs;
+        s.first = first;
+        first += s.ntiles;
+        seg_of[li][k] = (int)segs.size();
+        segs.push_back(s);
+      }
+    wv.nseg = (int)segs.size();
+    wv.total = first;
+    QTT_CUDA_TRY(cudaMalloc(&wv.d_ops, sizeof(BOp) * hops.size()));
+    QTT_CUDA_TRY(cudaMalloc(&wv.d_segs, sizeof(BSeg) * segs.size()));
+    QTT_CUDA_TRY(cudaMalloc(&wv.d_done, sizeof(unsigned) * segs.size()));
+    QTT_CUDA_TRY(cudaMemcpyAsync(wv.d_ops, hops.data(), sizeof(BOp) * hops.size(),
+                                 cudaMemcpyHostToDevice, st));
+    QTT_CUDA_TRY(cudaMemcpyAsync(wv.d_segs, segs.data(), sizeof(BSeg) * segs.size(),
+                                 cudaMemcpyHostToDevice, st));
+    B->waves.push_back(wv);
+  }
+  QTT_CUDA_TRY(cudaStreamSynchronize(st));
+  return QTT_OK;
+}
+
+template <int TN>
+qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
+  int max_rin = 1;
+  for (auto &w : B->waves) max_rin = std::max(max_rin, w.max_rin);
+  const size_t smem = sizeof(float) * (size_t)max_rin * 2 * 32 * TN;
+  QTT_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  int per_sm = 0, dev = 0, sms = 0;
+  QTT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<TN>, kThreads, smem));
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int clk_khz = 2000000;
+  cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+  B->grid = std::max(1, per_sm) * sms;
+  for (size_t wi = 0; wi < B->waves.size(); ++wi) {
+    auto &w = B->waves[wi];
+    QTT_CUDA_TRY(cudaMemsetAsync(w.d_done, 0, sizeof(unsigned) * w.nseg, st));
+    QTT_CUDA_TRY(cudaMemsetAsync(B->d_next + wi, 0, sizeof(unsigned long long), st));
+    BWave bw;
+    bw.ops = w.d_ops;
+    bw.segs = w.d_segs;
+    bw.nseg = w.nseg;
+    bw.total = w.total;
+    bw.done = w.d_done;
+    bw.next = B->d_next + wi;
+    bw.status = B->d_status;
+    bw.tf32 = B->compute == QTT_TF32;
+    bw.wait_budget = (long long)clk_khz * 1000LL * 4;  // ~4 s of clock
+    batch_kernel<TN><<<B->grid, kThreads, smem, st>>>(bw);
+    count_launches(1);
+    QTT_CUDA_TRY(cudaGetLastError());
+  }
+  return QTT_OK;
+}
+
+qtt_status launch_waves(qtt_batch *B, cudaStream_t st) {
+  switch (B->variant) {
+    case 2: return launch_waves_t<2>(B, st);
+    default: return launch_waves_t<4>(B, st);
+  }
+}
+
+qtt_status capture(qtt_batch *B, cudaStream_t st) {
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  B->exec = nullptr;
+  B->graph = nullptr;
+  // Capture on a private stream so the caller's stream state is untouched.
+  cudaStream_t cs;
+  QTT_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return cuda_fail(e, "batch: begin capture");
+  }
+  qtt_status s = launch_waves(B, cs);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (s != QTT_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "batch: end capture");
+  B->graph = g;
+  e = cudaGraphInstantiate(&B->exec, g, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "batch: instantiate");
+  (void)st;
+  return QTT_OK;
+}
+
+}  // namespace
+}  // namespace qtt
+
+using namespace qtt;
+
+extern "C" {
+
+qtt_status qtt_batch_create(qtt_batch **out, int nops, const qtt_op *const *ops,
+                            const int64_t *nrhs, const void *const *x, void *const *y,
+                            const int64_t *ld, qtt_dtype compute, size_t mem_budget,
+                            void *stream) {
+  if (!out) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_create: out is NULL");
+  *out = nullptr;
+  if (nops < 1 || !ops || !nrhs || !x || !y || !ld)
+    return fail(QTT_ERR_INVALID_ARG, "qtt_batch_create: empty batch or NULL array");
+  if (compute != QTT_F32 && compute != QTT_TF32)
+    return fail(QTT_ERR_UNSUPPORTED, "qtt_batch_create: compute must be QTT_F32 or QTT_TF32");
+  for (int i = 0; i < nops; ++i) {
+    const qtt_op *A = ops[i];
+    if (!A || !x[i] || !y[i]) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_create: NULL entry");
+    if (nrhs[i] < 1 || nrhs[i] > (int64_t)1 << 24)
+      return fail(QTT_ERR_INVALID_ARG, "qtt_batch_create: nrhs out of range");
+    if (ld[i] < ((int64_t)1 << A->d)) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_create: ld < N");
+    if ((compute == QTT_F32 && !A->m32) || (compute == QTT_TF32 && !A->mtf32))
+      return fail(QTT_ERR_INVALID_ARG, "qtt_batch_create: operator lacks the packed copy");
+    for (int k = 0; k <= A->d; ++k)
+      if (A->ranks[k] > kMaxRank)
+        return fail(QTT_ERR_UNSUPPORTED, "qtt_batch_create: ranks above 64");
+  }
+  qtt_batch *B = new (std::nothrow) qtt_batch();
+  if (!B) return fail(QTT_ERR_OOM, "qtt_batch_create: host allocation");
+  B->ops.assign(ops, ops + nops);
+  B->nrhs.assign(nrhs, nrhs + nops);
+  B->ld.assign(ld, ld + nops);
+  for (int i = 0; i < nops; ++i) {
+    B->x.push_back(static_cast<const float *>(x[i]));
+    B->y.push_back(static_cast<float *>(y[i]));
+    B->flops += ops[i]->flops_per_rhs * (double)nrhs[i];
+  }
+  B->compute = compute;
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  B->budget = mem_budget ? mem_budget : std::min<size_t>(fr / 3, (size_t)64 << 30);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMalloc(&B->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(B->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    qtt_batch_destroy(B);
+    return cuda_fail(e, "qtt_batch_create: status word");
+  }
+  qtt_status s = build_plan(B, st);
+  if (s == QTT_OK) s = capture(B, st);
+  if (s != QTT_OK) {
+    qtt_batch_destroy(B);
+    return s;
+  }
+  *out = B;
+  return QTT_OK;
+}
+
+qtt_status qtt_batch_run(qtt_batch *B, void *stream) {
+  if (!B || !B->exec) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_run: no batch");
+  cudaError_t e = cudaGraphLaunch(B->exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "qtt_batch_run: graph launch");
+  return QTT_OK;
+}
+
+qtt_status qtt_batch_status(qtt_batch *B, void *stream) {
+  if (!B) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_status: no batch");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, B->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "qtt_batch_status");
+  if (h != 0) {
+    cudaMemsetAsync(B->d_status, 0, sizeof(int), st);
+    cudaStreamSynchronize(st);
+    return fail(QTT_ERR_TIMEOUT, "batch kernel: a dependency wait ran out of its budget");
+  }
+  return QTT_OK;
+}
+
+qtt_status qtt_batch_set_variant(qtt_batch *B, int variant, void *stream) {
+  if (!B) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_set_variant: no batch");
+  if (variant != 2 && variant != 4)
+    return fail(QTT_ERR_INVALID_ARG, "qtt_batch_set_variant: variant must be 2 or 4");
+  B->variant = variant;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  QTT_CUDA_TRY(cudaStreamSynchronize(st));
+  qtt_status s = build_plan(B, st);
+  if (s == QTT_OK) s = capture(B, st);
+  return s;
+}
+
+qtt_status qtt_batch_autotune(qtt_batch *B, int reps, void *stream, int *chosen,
+                              double *seconds_per_run) {
+  if (!B) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_autotune: no batch");
+  if (reps < 1) reps = 1;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int best = B->variant;
+  double best_t = 1e300;
+  cudaEvent_t e0, e1;
+  QTT_CUDA_TRY(cudaEventCreate(&e0));
+  QTT_CUDA_TRY(cudaEventCreate(&e1));
+  for (int v : {2, 4}) {
+    qtt_status s = qtt_batch_set_variant(B, v, stream);
+    if (s != QTT_OK) continue;
+    qtt_batch_run(B, stream);  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps; ++r) qtt_batch_run(B, stream);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (qtt_batch_status(B, stream) != QTT_OK) continue;
+    const double t = ms / 1e3 / reps;
+    if (t < best_t) {
+      best_t = t;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  qtt_status s = qtt_batch_set_variant(B, best, stream);
+  if (chosen) *chosen = best;
+  if (seconds_per_run) *seconds_per_run = best_t;
+  return s;
+}
+
+qtt_status qtt_batch_info(const qtt_batch *B, int *waves, int *variant, int *grid,
+                          double *flops, size_t *scratch_bytes) {
+  if (!B) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_info: no batch");
+  if (waves) *waves = (int)B->waves.size();
+  if (variant) *variant = B->variant;
+  if (grid) *grid = B->grid;
+  if (flops) *flops = B->flops;
+  if (scratch_bytes) *scratch_bytes = B->scratch_bytes;
+  return QTT_OK;
+}
+
+qtt_status qtt_batch_destroy(qtt_batch *B) {
+  if (!B) return QTT_OK;
+  cudaDeviceSynchronize();
+  free_waves(B);
+  if (B->scratch) cudaFree(B->scratch);
+  if (B->d_next) cudaFree(B->d_next);
+  if (B->d_status) cudaFree(B->d_status);
+  delete B;
+  return QTT_OK;
+}
+
+}  // extern "C"

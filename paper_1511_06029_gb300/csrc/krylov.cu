@@ -152,11 +152,13 @@ cudaError_t vec_dots(VecSet V, int nv, VecSet W, int64_t N, int64_t nrhs, double
     Wc.ptr += c0 * W.ld;
     // partial layout uses the chunk's own nrhs; reduce it into out[i*nrhs+c]
     dots_partial_kernel<<<dim3(B, (unsigned)nc, nv), kThreads, 0, st>>>(Vc, nv, Wc, N, B, partial);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t count = nc * nv;
     reduce_partials_kernel<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(
         partial, B, nc, nv, nrhs, c0, out, accumulate_into);
+    count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -168,6 +170,7 @@ cudaError_t vec_gs_update(VecSet W, VecSet V, int nv, const double *h, int64_t N
   if (nv <= 0 || nrhs <= 0) return cudaSuccess;
   if (nrhs > 65535) return cudaErrorInvalidValue;
   gs_update_kernel<<<dim3(grid_x(N), (unsigned)nrhs), kThreads, 0, st>>>(W, V, nv, h, N);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -176,6 +179,7 @@ cudaError_t vec_combine(VecSet U, VecSet V, int nv, const double *y, int64_t N, 
   if (nrhs <= 0) return cudaSuccess;
   if (nrhs > 65535) return cudaErrorInvalidValue;
   combine_kernel<<<dim3(grid_x(N), (unsigned)nrhs), kThreads, 0, st>>>(U, V, nv, y, N);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -184,6 +188,7 @@ cudaError_t vec_normalize(VecSet D, VecSet S, const double *sumsq, int64_t N, in
   if (nrhs <= 0) return cudaSuccess;
   if (nrhs > 65535) return cudaErrorInvalidValue;
   normalize_kernel<<<dim3(grid_x(N), (unsigned)nrhs), kThreads, 0, st>>>(D, S, sumsq, N);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -192,6 +197,7 @@ cudaError_t vec_scale(VecSet D, VecSet S, const double *scale, int64_t N, int64_
   if (nrhs <= 0) return cudaSuccess;
   if (nrhs > 65535) return cudaErrorInvalidValue;
   scale_kernel<<<dim3(grid_x(N), (unsigned)nrhs), kThreads, 0, st>>>(D, S, scale, N);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -200,6 +206,7 @@ cudaError_t vec_axpy(VecSet D, VecSet S, double alpha, int64_t N, int64_t nrhs,
   if (nrhs <= 0) return cudaSuccess;
   if (nrhs > 65535) return cudaErrorInvalidValue;
   axpy_kernel<<<dim3(grid_x(N), (unsigned)nrhs), kThreads, 0, st>>>(D, S, alpha, N);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -207,6 +214,7 @@ cudaError_t vec_copy(VecSet D, VecSet S, int64_t N, int64_t nrhs, cudaStream_t s
   if (nrhs <= 0) return cudaSuccess;
   if (nrhs > 65535) return cudaErrorInvalidValue;
   copy_kernel<<<dim3(grid_x(N), (unsigned)nrhs), kThreads, 0, st>>>(D, S, N);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -14,6 +15,9 @@
 namespace qtt {
 
 static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 qtt_status fail(qtt_status s, const std::string &msg) {
   g_last_error = msg;
@@ -246,9 +250,11 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
         if (epi.on) {
           p.epi = 1;
           p.u = epi.u ? static_cast<const char *>(epi.u) + (size_t)c0 * ld * ysz : nullptr;
+          p.v = epi.v ? static_cast<const char *>(epi.v) + (size_t)c0 * ld * ysz : nullptr;
           p.u_rhs_stride = ld;
           p.s_acc = epi.s_acc;
           p.s_u = epi.s_u;
+          p.s_v = epi.s_v;
         }
       } else {
         p.out = buf[k & 1];
@@ -287,6 +293,8 @@ const char *qtt_status_string(qtt_status s) {
 }
 
 const char *qtt_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t qtt_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores,
                       unsigned precision_mask, void *stream) {

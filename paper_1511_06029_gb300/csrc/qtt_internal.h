@@ -22,6 +22,9 @@ qtt_status cuda_fail(cudaError_t e, const char *where);
     if (e_ != cudaSuccess) return ::qtt::cuda_fail(e_, #call); \
   } while (0)
 
+// Count of kernel launches issued by the library (all threads).
+void count_launches(uint64_t n);
+
 // Stream-ordered scratch from the library's pool (one pool per device, keeps
 // freed blocks cached).  Returns QTT_ERR_OOM if `bytes` cannot be had.
 qtt_status scratch_alloc(void **ptr, size_t bytes, cudaStream_t stream);
@@ -92,7 +95,8 @@ struct Epilogue {
 struct LpEpilogue {
   bool on = false;
   const void *u = nullptr;
-  double s_acc = 1.0, s_u = 0.0;
+  const void *v = nullptr;
+  double s_acc = 1.0, s_u = 0.0, s_v = 0.0;
 };
 qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype xt, void *y,
                     qtt_dtype yt, int64_t nrhs, int64_t ld, cudaStream_t st,

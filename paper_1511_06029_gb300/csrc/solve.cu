@@ -106,6 +106,30 @@ qtt_status apply_A(const Ctx &c, const double *z, double *out, int64_t ld) {
   return apply_f64(c.K, z, out, c.nrhs, ld, c.st, e);
 }
 
+// out = rhs + s_z z - K z with K in the low precision c.pc (FP64 vectors;
+// FP64 K when c.pc is FP64).
+qtt_status apply_K_lowp(const Ctx &c, const double *z, double *out, const double *rhs,
+                        double s_z) {
+  if (c.pc == QTT_F64) {
+    Epilogue e;
+    e.on = true;
+    e.v = rhs;
+    e.s_v = 1.0;
+    e.u = z;
+    e.s_u = s_z;
+    e.s_acc = -1.0;
+    return apply_f64(c.K, z, out, c.nrhs, c.N, c.st, e);
+  }
+  LpEpilogue e;
+  e.on = true;
+  e.v = rhs;
+  e.s_v = 1.0;
+  e.u = z;
+  e.s_u = s_z;
+  e.s_acc = -1.0;
+  return apply_lp(c.K, c.pc, z, QTT_F64, out, QTT_F64, c.nrhs, c.N, c.st, e);
+}
+
 // r = f - (a x + K x) (FP64, fused)
 qtt_status residual(const Ctx &c, const double *f, const double *x, int64_t ld, double *r) {
   Epilogue e;
@@ -289,7 +313,36 @@ qtt_status refine(const Ctx &c, const double *f, double *x, int64_t ld,
     X = xc;
   }
   const int64_t L = ld != N ? N : ld;
-  QTT_TRY(apply_P(c, F, L, X, L, false));  // x0 = P f
+  const int inner = prm.inner_iters;
+  double *zA = nullptr, *zB = nullptr, *w = nullptr;
+  if (inner > 0) {
+    QTT_TRY(S.get(&zA, (size_t)N * nr));
+    QTT_TRY(S.get(&zB, (size_t)N * nr));
+    QTT_TRY(S.get(&w, (size_t)N * nr));
+  }
+  // M(rhs) -> zA: `inner` Richardson steps on (a I + K) z = rhs, K (and P)
+  // in the low precision, vectors and updates in FP64, z0 = P rhs.
+  auto correction = [&](const double *rhs) -> qtt_status {
+    QTT_TRY(apply_P(c, rhs, N, zA, N, false));
+    for (int s = 0; s < inner; ++s) {
+      if (c.P) {
+        // w = rhs - a zA - K zA ; zA += P w
+        QTT_TRY(apply_K_lowp(c, zA, w, rhs, -c.a));
+        QTT_TRY(apply_P(c, w, N, zA, N, true));
+      } else {
+        // zB = rhs + (1 - a) zA - K zA
+        QTT_TRY(apply_K_lowp(c, zA, zB, rhs, 1.0 - c.a));
+        std::swap(zA, zB);
+      }
+    }
+    return QTT_OK;
+  };
+  if (inner > 0) {
+    QTT_TRY(correction(F));
+    QTT_TRY(copy_strided(c, X, L, zA, N));  // x0 = M f
+  } else {
+    QTT_TRY(apply_P(c, F, L, X, L, false));  // x0 = P f
+  }
   int iters = 1;
   std::vector<double> q, rel(nr, 0.0);
   for (;;) {
@@ -301,7 +354,12 @@ qtt_status refine(const Ctx &c, const double *f, double *x, int64_t ld,
       if (rel[k] > prm.tol) all = false;
     }
     if (all || iters >= prm.max_iter) break;
-    QTT_TRY(apply_P(c, r, N, X, L, true));  // x += P r (FP64 update)
+    if (inner > 0) {
+      QTT_TRY(correction(r));
+      QTT_CUDA_OK(vec_axpy(vecs(X, L), vecs(zA, N), 1.0, N, nr, c.st), "axpy");  // FP64 update
+    } else {
+      QTT_TRY(apply_P(c, r, N, X, L, true));  // x += P r (FP64 update)
+    }
     ++iters;
   }
   if (ld != N) QTT_TRY(copy_strided(c, x, ld, X, N));
@@ -372,12 +430,17 @@ extern "C" qtt_status qtt_solve(const qtt_op *K, const qtt_op *P, const double *
   const qtt_dtype pc = prm->precond_compute;
   if (pc != QTT_F64 && pc != QTT_F32 && pc != QTT_TF32 && pc != QTT_BF16)
     return fail(QTT_ERR_INVALID_ARG, "qtt_solve: unknown precond_compute");
-  if (P && pc != QTT_F64) {
-    const void *pk = pc == QTT_F32 ? (const void *)P->m32
-                     : pc == QTT_TF32 ? (const void *)P->mtf32 : (const void *)P->mbf16;
-    if (!pk)
-      return fail(QTT_ERR_INVALID_ARG, "qtt_solve: P lacks the packed copy for precond_compute");
-  }
+  auto packed = [&](const qtt_op *A) -> bool {
+    return pc == QTT_F32 ? A->m32 != nullptr
+           : pc == QTT_TF32 ? A->mtf32 != nullptr : A->mbf16 != nullptr;
+  };
+  if (P && pc != QTT_F64 && !packed(P))
+    return fail(QTT_ERR_INVALID_ARG, "qtt_solve: P lacks the packed copy for precond_compute");
+  if (prm->inner_iters < 0 || prm->inner_iters > 1000)
+    return fail(QTT_ERR_INVALID_ARG, "qtt_solve: inner_iters must be in [0, 1000]");
+  if (prm->kind == QTT_SOLVE_REFINE && prm->inner_iters > 0 && pc != QTT_F64 && !packed(K))
+    return fail(QTT_ERR_INVALID_ARG,
+                "qtt_solve: inner iterations need K packed for precond_compute");
   {
     const size_t span = ((size_t)(nrhs - 1) * (size_t)ld + (size_t)N) * sizeof(double);
     const char *fb = reinterpret_cast<const char *>(f), *xb = reinterpret_cast<const char *>(x);

@@ -106,6 +106,7 @@ cudaError_t launch_step_f64(const StepF64 &s, cudaStream_t stream) {
     if (t.v) t.v += c0 * s.uv_rhs_stride;
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nc);
     step_f64_kernel<kTN><<<grid, block, 0, stream>>>(t);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -63,18 +63,25 @@ __device__ __forceinline__ void st_from_float(__nv_bfloat16 *p, float v) {
   *p = __float2bfloat16_rn(v);
 }
 
-// Epilogue value in the output type's own precision.
-__device__ __forceinline__ double epi_val(const double *u, int64_t p, double su, double sacc,
-                                          float acc) {
-  return (u ? su * u[p] : 0.0) + sacc * (double)acc;
+// Epilogue value s_v v + s_u u + s_acc acc in the output type's precision
+// (FP64 for FP64 outputs, FP32 otherwise).
+__device__ __forceinline__ double epi_val(const double *u, const double *v, int64_t p,
+                                          const StepLP &s, float acc) {
+  double t = v ? s.s_v * v[p] : 0.0;
+  if (u) t += s.s_u * u[p];
+  return t + s.s_acc * (double)acc;
 }
-__device__ __forceinline__ float epi_val(const float *u, int64_t p, double su, double sacc,
-                                         float acc) {
-  return (u ? (float)su * u[p] : 0.0f) + (float)sacc * acc;
+__device__ __forceinline__ float epi_val(const float *u, const float *v, int64_t p,
+                                         const StepLP &s, float acc) {
+  float t = v ? (float)s.s_v * v[p] : 0.0f;
+  if (u) t += (float)s.s_u * u[p];
+  return t + (float)s.s_acc * acc;
 }
-__device__ __forceinline__ float epi_val(const __nv_bfloat16 *u, int64_t p, double su,
-                                         double sacc, float acc) {
-  return (u ? (float)su * __bfloat162float(u[p]) : 0.0f) + (float)sacc * acc;
+__device__ __forceinline__ float epi_val(const __nv_bfloat16 *u, const __nv_bfloat16 *v,
+                                         int64_t p, const StepLP &s, float acc) {
+  float t = v ? (float)s.s_v * __bfloat162float(v[p]) : 0.0f;
+  if (u) t += (float)s.s_u * __bfloat162float(u[p]);
+  return t + (float)s.s_acc * acc;
 }
 __device__ __forceinline__ void st_val(double *p, double v) { *p = v; }
 __device__ __forceinline__ void st_val(float *p, float v) { *p = v; }
@@ -151,6 +158,7 @@ step_lp_kernel(StepLP s) {
 
   TOUT *out = static_cast<TOUT *>(s.out) + c * s.out_rhs_stride;
   const TOUT *u = s.epi && s.u ? static_cast<const TOUT *>(s.u) + c * s.u_rhs_stride : nullptr;
+  const TOUT *vv = s.epi && s.v ? static_cast<const TOUT *>(s.v) + c * s.u_rhs_stride : nullptr;
 #pragma unroll
   for (int t = 0; t < kTB; ++t) {
     const int b = b0 + t;
@@ -163,7 +171,7 @@ step_lp_kernel(StepLP s) {
       for (int i = 0; i < 2; ++i) {
         const int64_t p = p0[m] + (i ? bit : 0);
         if (s.epi)
-          st_val(ob + p, epi_val(u, p, s.s_u, s.s_acc, acc[t][i][m]));
+          st_val(ob + p, epi_val(u, vv, p, s, acc[t][i][m]));
         else
           st_from_float(ob + p, acc[t][i][m]);
       }
@@ -184,8 +192,10 @@ cudaError_t launch_t(const StepLP &s, cudaStream_t st) {
     t.in = static_cast<const TIN *>(s.in) + c0 * s.in_rhs_stride;
     t.out = static_cast<TOUT *>(s.out) + c0 * s.out_rhs_stride;
     if (t.u) t.u = static_cast<const TOUT *>(s.u) + c0 * s.u_rhs_stride;
+    if (t.v) t.v = static_cast<const TOUT *>(s.v) + c0 * s.u_rhs_stride;
     step_lp_kernel<MODE, TIN, TOUT, TCORE>
         <<<dim3((unsigned)gx, (unsigned)gy, (unsigned)nc), dim3(32, by), 0, st>>>(t);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -21,11 +21,13 @@ struct StepLP {
   int64_t N, nrhs;
   int mode;                // LpMode
   qtt_dtype in_type, out_type;
-  // Epilogue (last step): out = s_acc acc + s_u u, u of out_type (may be out).
+  // Epilogue (last step): out = s_v v + s_u u + s_acc acc; u, v of out_type
+  // (either may be NULL; u may be out itself).
   int epi;
   const void *u;
-  int64_t u_rhs_stride;
-  double s_acc, s_u;
+  const void *v;
+  int64_t u_rhs_stride;  // also the stride of v
+  double s_acc, s_u, s_v;
 };
 
 // Rank padding of the packed reduced-precision cores (multiple of the

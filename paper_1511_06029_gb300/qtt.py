@@ -44,7 +44,16 @@ SIGNATURES = {
     "qtt_solve": (_I, [_P, _P, _P, _P, _L, _L, _P, _P, _P]),
     "qtt_status_string": (ctypes.c_char_p, [_I]),
     "qtt_last_error": (ctypes.c_char_p, []),
+    "qtt_kernel_launches": (ctypes.c_uint64, []),
     "qtt_sync_status": (_I, [_P]),
+    "qtt_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _P, _P, _P, _P, _I, ctypes.c_size_t, _P]),
+    "qtt_batch_run": (_I, [_P, _P]),
+    "qtt_batch_status": (_I, [_P, _P]),
+    "qtt_batch_set_variant": (_I, [_P, _I, _P]),
+    "qtt_batch_autotune": (_I, [_P, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "qtt_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                            ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_size_t)]),
+    "qtt_batch_destroy": (_I, [_P]),
 }
 
 
@@ -56,7 +65,7 @@ class QTTError(RuntimeError):
 
 class SolveParams(ctypes.Structure):
     _fields_ = [("kind", _I), ("a", _D), ("tol", _D), ("restart", _I),
-                ("max_iter", _I), ("precond_compute", _I)]
+                ("max_iter", _I), ("precond_compute", _I), ("inner_iters", _I)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -211,7 +220,7 @@ class Operator:
 
 def solve(K, P, f, kind: str = "gmres", a: float = 1.0, tol: float = 1e-10,
           restart: int = 30, max_iter: int = 300, precond_compute: str = "f64",
-          out=None, stream=None, raise_on_fail: bool = True):
+          inner_iters: int = 0, out=None, stream=None, raise_on_fail: bool = True):
     """Solve (a I + K) x = f (qtt_solve).  Returns (x, info) with info a list
     of (iters, rel_residual, status) per right-hand side."""
     torch = _torch()
@@ -219,7 +228,8 @@ def solve(K, P, f, kind: str = "gmres", a: float = 1.0, tol: float = 1e-10,
     nrhs, ld = _block(f, N, "qtt_solve")
     if out is None:
         out = torch.empty_like(f)
-    prm = SolveParams(SOLVE_KINDS[kind], a, tol, restart, max_iter, DTYPES[precond_compute])
+    prm = SolveParams(SOLVE_KINDS[kind], a, tol, restart, max_iter, DTYPES[precond_compute],
+                      inner_iters)
     info = (SolveInfo * nrhs)()
     st = load_library().qtt_solve(K.handle if K is not None else None,
                                   P.handle if P is not None else None,
@@ -228,6 +238,80 @@ def solve(K, P, f, kind: str = "gmres", a: float = 1.0, tol: float = 1e-10,
     if st != QTT_OK and (st != QTT_ERR_NOT_CONVERGED or raise_on_fail):
         _check(st, "qtt_solve")
     return out, [(i.iters, i.rel_residual, i.status) for i in info]
+
+
+class Batch:
+    """Many uneven operators applied in one persistent launch per memory wave,
+    replayed from a CUDA graph (qtt_batch_*).  xs/ys: lists of FP32 CUDA
+    tensors shaped (nrhs_i, N_i); they stay bound to the batch."""
+
+    def __init__(self, ops, xs, ys, compute="f32", mem_budget=0, stream=None):
+        lib = load_library()
+        n = len(ops)
+        if not (n == len(xs) == len(ys)) or n == 0:
+            raise QTTError(QTT_ERR_INVALID_ARG, "Batch", "ops, xs, ys must have equal length")
+        nrhs, lds = [], []
+        for op, x, y in zip(ops, xs, ys):
+            nr, ld = _block(x, op.N, "qtt_batch_create")
+            nr2, ld2 = _block(y, op.N, "qtt_batch_create")
+            if nr != nr2 or ld != ld2 or x.dtype != y.dtype:
+                raise QTTError(QTT_ERR_INVALID_ARG, "qtt_batch_create", "x/y mismatch")
+            nrhs.append(nr)
+            lds.append(ld)
+        self._keep = (list(ops), list(xs), list(ys))
+        arr = lambda vals, ct: (ct * n)(*vals)
+        h = ctypes.c_void_p()
+        _check(lib.qtt_batch_create(ctypes.byref(h), n,
+                                    ctypes.cast(arr([o.handle for o in ops], _P), _P),
+                                    ctypes.cast(arr(nrhs, ctypes.c_int64), _P),
+                                    ctypes.cast(arr([x.data_ptr() for x in xs], _P), _P),
+                                    ctypes.cast(arr([y.data_ptr() for y in ys], _P), _P),
+                                    ctypes.cast(arr(lds, ctypes.c_int64), _P),
+                                    DTYPES[compute], mem_budget, _stream_handle(stream)),
+               "qtt_batch_create")
+        self._h = h
+
+    def run(self, stream=None):
+        _check(load_library().qtt_batch_run(self._h, _stream_handle(stream)), "qtt_batch_run")
+
+    def status(self, stream=None):
+        _check(load_library().qtt_batch_status(self._h, _stream_handle(stream)), "qtt_batch_status")
+
+    def set_variant(self, v, stream=None):
+        _check(load_library().qtt_batch_set_variant(self._h, v, _stream_handle(stream)),
+               "qtt_batch_set_variant")
+
+    def autotune(self, reps=2, stream=None):
+        v, t = ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(load_library().qtt_batch_autotune(self._h, reps, _stream_handle(stream),
+                                                 ctypes.byref(v), ctypes.byref(t)),
+               "qtt_batch_autotune")
+        return v.value, t.value
+
+    def info(self):
+        w, v, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        f, sb = ctypes.c_double(), ctypes.c_size_t()
+        _check(load_library().qtt_batch_info(self._h, ctypes.byref(w), ctypes.byref(v),
+                                             ctypes.byref(g), ctypes.byref(f), ctypes.byref(sb)),
+               "qtt_batch_info")
+        return {"waves": w.value, "variant": v.value, "grid": g.value, "flops": f.value,
+                "scratch_bytes": sb.value}
+
+    def close(self):
+        if self._h is not None:
+            load_library().qtt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched so far (qtt_kernel_launches)."""
+    return int(load_library().qtt_kernel_launches())
 
 
 def sync_status(stream=None):

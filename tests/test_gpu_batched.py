@@ -1,0 +1,101 @@
+"""Batched uneven operators in one persistent launch per wave, replayed from a
+captured CUDA graph: every operator's result against the FP64 oracle, within
+the FP32/TF32 error bound 4 sqrt(d) u used for the single applies."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_06029_gb300 import inputs
+from conftest import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+U = {"tf32": 2.0 ** -11, "f32": 2.0 ** -24}
+
+
+@pytest.fixture(scope="module")
+def qtt():
+    from paper_1511_06029_gb300 import build, qtt as q
+    build.build()
+    q.load_library()
+    return q
+
+
+def _batch(count, seed, d_range=(5, 12), r_range=(3, 40), rhs_range=(1, 5)):
+    return inputs.batched_workload(count=count, seed=seed, d_range=d_range, r_range=r_range,
+                                   rhs_range=rhs_range)
+
+
+def _setup(qtt, items, compute):
+    import torch
+    datas, ops, xs, ys, xh = [], [], [], [], []
+    for it in items:
+        data = inputs.synthetic_operator(it["d"], it["rmax"], it["op_seed"])
+        x = inputs.gaussian_rhs(data.N, it["nrhs"], it["rhs_seed"])
+        datas.append(data)
+        xh.append(x)
+        ops.append(qtt.Operator(data, packs=(compute,)))
+        xs.append(torch.from_numpy(x.astype(np.float32)).cuda())
+        ys.append(torch.full_like(xs[-1], float("nan")))
+    return datas, ops, xs, ys, xh
+
+
+@pytest.mark.parametrize("compute", ["f32", "tf32"])
+@pytest.mark.parametrize("budget", [0, 16 << 20])
+def test_batch_matches_oracle(qtt, compute, budget):
+    """24 operators (d 5..12, r_max 3..40, 1-5 RHS); a 16 MiB budget forces
+    several waves, 0 lets one wave hold all."""
+    import torch
+    items = _batch(24, 11)
+    datas, ops, xs, ys, xh = _setup(qtt, items, compute)
+    B = qtt.Batch(ops, xs, ys, compute=compute, mem_budget=budget)
+    info = B.info()
+    assert (info["waves"] > 1) == (budget != 0)
+    for _ in range(2):  # replaying the graph gives the same result
+        B.run()
+        B.status()
+        torch.cuda.synchronize()
+        for data, x, y in zip(datas, xh, ys):
+            err = rel_l2(y.double().cpu().numpy(), oracle.apply(data, x))
+            assert err <= 4 * math.sqrt(data.d) * U[compute], (data.d, data.ranks, err)
+    B.close()
+    for o in ops:
+        o.close()
+
+
+def test_batch_autotune_and_single_apply_agree(qtt):
+    """After autotuning the tile variant, the batch agrees with the FP32
+    single applies of the same operators within FP32 rounding."""
+    import torch
+    items = _batch(10, 12, d_range=(6, 11), r_range=(8, 40), rhs_range=(1, 3))
+    datas, ops, xs, ys, xh = _setup(qtt, items, "f32")
+    B = qtt.Batch(ops, xs, ys, compute="f32")
+    v, t = B.autotune(reps=1)
+    assert v in (2, 4) and t > 0
+    B.run()
+    B.status()
+    torch.cuda.synchronize()
+    for op, x, y, data in zip(ops, xs, ys, datas):
+        y1 = op.apply(x, compute="f32")
+        assert rel_l2(y.double().cpu().numpy(), y1.double().cpu().numpy()) <= \
+            4 * math.sqrt(data.d) * U["f32"]
+    B.close()
+    for o in ops:
+        o.close()
+
+
+def test_batch_rejects_bad_input(qtt):
+    import torch
+    data = inputs.synthetic_operator(6, 4, 1)
+    op64 = qtt.Operator(data)  # no FP32 pack
+    x = torch.zeros(64, dtype=torch.float32, device="cuda")
+    y = torch.zeros_like(x)
+    with pytest.raises(qtt.QTTError) as e:
+        qtt.Batch([op64], [x], [y], compute="f32")
+    assert e.value.status == qtt.QTT_ERR_INVALID_ARG
+    with pytest.raises(qtt.QTTError) as e:
+        qtt.Batch([op64], [x], [y], compute="bf16")
+    assert e.value.status == qtt.QTT_ERR_UNSUPPORTED
+    op64.close()

@@ -160,3 +160,29 @@ def test_run_to_run_bitwise(qtt):
     x2, _ = qtt.solve(Kg, Pg, f, kind="gmres", tol=GPU_TOL, precond_compute="bf16")
     assert bool((x1 == x2).all())
     Kg.close(), Pg.close()
+
+
+@pytest.mark.parametrize("pc,inner", [("bf16", 6), ("tf32", 4), ("f64", 3)])
+def test_refine_inner_iterations(qtt, pc, inner):
+    """Mixed-precision refinement without P: the correction is `inner`
+    Richardson steps z <- r - K z with K in low precision; only the residual
+    and the update are FP64.  Reaches the 1e-10 solution error."""
+    K, _ = _problem(11)
+    f = inputs.gaussian_rhs(K.N, 3, 20)
+    xo, _, _ = oracle.solve_gmres(K, None, f, a=1.0, tol=1e-13)
+    Kg = qtt.Operator(K, packs=(() if pc == "f64" else (pc,)))
+    x, info = qtt.solve(Kg, None, _gpu(f), kind="refine", tol=GPU_TOL, max_iter=60,
+                        precond_compute=pc, inner_iters=inner)
+    assert rel_l2(x.cpu().numpy(), xo) <= SOL_TOL
+    assert all(st == qtt.QTT_OK for _, _, st in info)
+    Kg.close()
+
+
+def test_refine_inner_needs_packed_k(qtt):
+    K, _ = _problem(8)
+    Kg = qtt.Operator(K)
+    f = _gpu(inputs.gaussian_rhs(K.N, 1, 21))
+    with pytest.raises(qtt.QTTError) as e:
+        qtt.solve(Kg, None, f, kind="refine", precond_compute="bf16", inner_iters=2)
+    assert e.value.status == qtt.QTT_ERR_INVALID_ARG
+    Kg.close()
