@@ -16,6 +16,8 @@ Workloads (a "step" is one pass of the hot path over one batch of input):
                   and FP32 accumulation (FP32 pipe).
   apply_bf16_d21  d = 21, r_max = 48, 64 BF16 right-hand sides, BF16 operands,
                   FP32 accumulation.
+  apply_bf16_d20_8
+                  d = 20, r_max = 48, 8 BF16 right-hand sides (profiler captures).
   apply_f64_d21   the same operator and 64 right-hand sides in FP64 (the cost
                   of one FP64 residual of the refinement).
   batched_f32 / batched_tf32
@@ -79,6 +81,8 @@ WORKLOADS = {
                            compute="bf16"),
     "apply_bf16_d21": dict(kind="apply", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=64,
                            compute="bf16"),
+    "apply_bf16_d20_8": dict(kind="apply", d=20, rmax=48, seed=3, rhs_seed=4, nrhs=8,
+                             compute="bf16"),
     "apply_f64_d21": dict(kind="apply", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=64,
                           compute="f64"),
     "batched_f32": dict(kind="batched", compute="f32", count=256, seed=4),

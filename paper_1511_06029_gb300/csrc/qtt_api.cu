@@ -5,12 +5,14 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
 
 #include "qtt_internal.h"
 #include "step_lp.h"
+#include "step_mma.h"
 
 namespace qtt {
 
@@ -180,6 +182,16 @@ qtt_status apply_f64(const qtt_op *A, const double *x, double *y, int64_t nrhs,
   return QTT_OK;
 }
 
+// BF16 steps go to the tensor cores unless QTT_NO_TENSOR_CORES is set (kept
+// for A/B measurements of the CUDA-core kernel).
+static bool use_tensor_cores() {
+  static const bool on = [] {
+    const char *v = std::getenv("QTT_NO_TENSOR_CORES");
+    return !(v && *v && *v != '0');
+  }();
+  return on;
+}
+
 static size_t dtype_size(qtt_dtype t) {
   return t == QTT_F64 ? 8 : (t == QTT_BF16 ? 2 : 4);
 }
@@ -261,7 +273,27 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
         p.out_rhs_stride = (int64_t)p.rout * N;
         p.out_type = mid;
       }
-      cudaError_t e = launch_step_lp(p, st);
+      cudaError_t e;
+      if (compute == QTT_BF16 && use_tensor_cores() && A->mma_bf16 && A->mp[k] &&
+          p.in_type == QTT_BF16 && p.out_type == QTT_BF16 && !p.epi &&
+          mma_step_eligible(k, p.rin, p.rout, N)) {
+        StepMMA m;
+        m.in = static_cast<const __nv_bfloat16 *>(p.in);
+        m.in_rhs_stride = p.in_rhs_stride;
+        m.out = static_cast<__nv_bfloat16 *>(p.out);
+        m.out_rhs_stride = p.out_rhs_stride;
+        m.A = A->mma_bf16 + A->moff[k];
+        m.k = k;
+        m.rin = p.rin;
+        m.rout = p.rout;
+        m.Mp = A->mp[k];
+        m.Kp = A->kp[k];
+        m.N = N;
+        m.nrhs = nc;
+        e = launch_step_mma_bf16(m, st);
+      } else {
+        e = launch_step_lp(p, st);
+      }
       if (e != cudaSuccess) {
         scratch_free(scratch, st);
         return cuda_fail(e, "step_lp launch");
@@ -367,18 +399,18 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores
     }
     A->offlp[d] = o;
     A->nlp = o;
-    std::vector<float> lp((size_t)o, 0.0f);
+    std::vector<double> lpd((size_t)o, 0.0);
     for (int k = 0; k < d; ++k) {
       const int ra = ranks[k], rb = ranks[k + 1], rp = A->rpad[k + 1];
       const double *G = cores + A->off[k];
-      float *L = lp.data() + A->offlp[k];
+      double *L = lpd.data() + A->offlp[k];
       for (int a = 0; a < ra; ++a)
         for (int i = 0; i < 2; ++i)
           for (int j = 0; j < 2; ++j)
             for (int b = 0; b < rb; ++b)
-              L[(((size_t)a * 2 + j) * rp + b) * 2 + i] =
-                  (float)G[(((size_t)a * 2 + i) * 2 + j) * rb + b];
+              L[(((size_t)a * 2 + j) * rp + b) * 2 + i] = G[(((size_t)a * 2 + i) * 2 + j) * rb + b];
     }
+    std::vector<float> lp(lpd.begin(), lpd.end());
     auto upload = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
       cudaError_t e2 = cudaMalloc(dst, bytes);
       if (e2 != cudaSuccess) return e2;
@@ -396,8 +428,37 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores
     }
     if (e2 == cudaSuccess && (precision_mask & QTT_PACK_BF16)) {
       std::vector<__nv_bfloat16> h(lp.size());
-      for (size_t q = 0; q < lp.size(); ++q) h[q] = __float2bfloat16_rn(lp[q]);
+      for (size_t q = 0; q < lp.size(); ++q) h[q] = __double2bfloat16(lpd[q]);
       e2 = upload(reinterpret_cast<void **>(&A->mbf16), h.data(), h.size() * 2);
+      // tensor-core layout [Mp][Kp], rows 2b+i, columns 2a+j
+      A->moff.assign(d + 1, 0);
+      A->mp.assign(d, 0);
+      A->kp.assign(d, 0);
+      int64_t mo = 0;
+      for (int k = 0; k < d; ++k) {
+        if (ranks[k] > kMmaMaxRank || ranks[k + 1] > kMmaMaxRank) continue;
+        A->mp[k] = (2 * ranks[k + 1] + 15) / 16 * 16;
+        A->kp[k] = (2 * ranks[k] + 15) / 16 * 16;
+        A->moff[k] = mo;
+        mo += (int64_t)A->mp[k] * A->kp[k];
+      }
+      A->moff[d] = mo;
+      if (e2 == cudaSuccess && mo > 0) {
+        std::vector<__nv_bfloat16> m((size_t)mo, __float2bfloat16(0.0f));
+        for (int k = 0; k < d; ++k) {
+          if (!A->mp[k]) continue;
+          const int ra = ranks[k], rb = ranks[k + 1], K = A->kp[k];
+          const double *G = cores + A->off[k];
+          __nv_bfloat16 *M = m.data() + A->moff[k];
+          for (int a = 0; a < ra; ++a)
+            for (int i = 0; i < 2; ++i)
+              for (int j = 0; j < 2; ++j)
+                for (int b = 0; b < rb; ++b)
+                  M[(size_t)(2 * b + i) * K + 2 * a + j] =
+                      __double2bfloat16(G[(((size_t)a * 2 + i) * 2 + j) * rb + b]);
+        }
+        e2 = upload(reinterpret_cast<void **>(&A->mma_bf16), m.data(), m.size() * 2);
+      }
     }
     if (e2 != cudaSuccess) {
       qtt_destroy(A);
@@ -415,6 +476,7 @@ qtt_status qtt_destroy(qtt_op *A) {
   if (A->m32) cudaFree(A->m32);
   if (A->mtf32) cudaFree(A->mtf32);
   if (A->mbf16) cudaFree(A->mbf16);
+  if (A->mma_bf16) cudaFree(A->mma_bf16);
   delete A;
   return QTT_OK;
 }

@@ -52,6 +52,12 @@ struct qtt_op {
   float *m32 = nullptr;         // FP32 copy (QTT_PACK_F32)
   float *mtf32 = nullptr;       // FP32 storage of TF32-rounded values
   __nv_bfloat16 *mbf16 = nullptr;
+  // BF16 tensor-core copy: core k as [Mp][Kp] (rows 2b+i, columns 2a+j,
+  // zero padded to multiples of 16) at element offset moff[k]; only for
+  // cores whose ranks are <= 64 (mp[k] = 0 otherwise).
+  __nv_bfloat16 *mma_bf16 = nullptr;
+  std::vector<int64_t> moff;
+  std::vector<int> mp, kp;
   // Reduced-precision packing [a][j][b padded to rpad[k+1]][i]:
   std::vector<int> rpad;        // padded output rank per core (index k+1)
   std::vector<int64_t> offlp;   // element offset of core k
