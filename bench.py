@@ -24,6 +24,13 @@ Workloads (a "step" is one pass of the hot path over one batch of input):
                   256 uneven operators (d 12..20, r_max 16..40, 1..32 RHS) in
                   one persistent launch per memory wave, replayed from a CUDA
                   graph, tile variant chosen by the autotuner.
+  serve           Poisson-arriving solve requests (d 14..22, 1..16 RHS) of
+                  (I + K) x = f, ||K||_2 = 0.5, r_max 32, through the solve
+                  server: GMRES(30) to 1e-10 with the rounded preconditioner
+                  round(I - K + K^2, 1e-4) applied in BF16 and FP64 residuals;
+                  p50/p99 latency, solves/s, and the plain FP64 form (FP64 P
+                  apply, one request at a time) on the same GPU.
+  serve_small     the same with d 14..18.
   refine_bf16_d21 / refine_f64_d21
                   solve (I + K) x = f, ||K||_2 = 0.5, d = 21, r_max = 48, 64
                   RHS, to a relative residual of 3e-11 (error <= 1e-10):
@@ -87,10 +94,19 @@ WORKLOADS = {
                           compute="f64"),
     "batched_f32": dict(kind="batched", compute="f32", count=256, seed=4),
     "batched_tf32": dict(kind="batched", compute="tf32", count=256, seed=4),
+    "serve": dict(kind="serve", d_range=(14, 22), rhs_range=(1, 16), rmax=32, seed_base=5000,
+                  eps=1e-4, seed=5, count=40, slots=6, tol=1e-10, plain_count=40),
+    "serve_small": dict(kind="serve", d_range=(14, 18), rhs_range=(1, 16), rmax=32,
+                        seed_base=5000, eps=1e-4, seed=5, count=40, slots=6, tol=1e-10,
+                        plain_count=40),
     "refine_bf16_d21": dict(kind="refine", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=64,
                             pc="bf16", inner=6),
     "refine_f64_d21": dict(kind="refine", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=64,
                            pc="f64", inner=6),
+    "refine_bf16_d21_2": dict(kind="refine", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=2,
+                              pc="bf16", inner=6),
+    "refine_f64_d21_2": dict(kind="refine", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=2,
+                             pc="f64", inner=6),
 }
 IO = {"f64": "float64", "f32": "float32", "tf32": "float32", "bf16": "bfloat16"}
 KERNEL = {"f64": "step_f64_kernel", "f32": "step_lp_kernel<F32>",
@@ -471,10 +487,12 @@ class RefineRun:
 
     def roofline(self, mean_s):
         # dominated by the FP64 residual applies: report the FP64 pipe share
+        # `its` corrections (each `inner` K applies in precond_compute) and
+        # `its` FP64 residuals
         its = self.last_info[0][0] if self.last_info else 0
         f64_flops = self.data.flops(self.nrhs) * its
         if self.spec["pc"] == "f64":
-            f64_flops += self.data.flops(self.nrhs) * its * (self.spec["inner"] + 1)
+            f64_flops += self.data.flops(self.nrhs) * its * self.spec["inner"]
         achieved = f64_flops / mean_s / 1e9
         return {"bound": "alu", "kernel": "step_f64_kernel (FP64 residual applies)",
                 "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
@@ -498,6 +516,169 @@ class RefineRun:
 
 
 RUNNERS = {"apply": ApplyRun, "batched": BatchedRun, "refine": RefineRun}
+
+# --------------------------------------------------------------- serving
+def _build_pair(args):
+    d, rmax, seed, eps = args
+    K = inputs.scaled_operator(d, rmax, seed)
+    P = inputs.neumann_preconditioner(K, eps)
+    return d, K, P
+
+
+def _serve_operators(d_range, rmax, seed_base, eps, qtt, log):
+    """K_d and P_d = round(I - K_d + K_d^2, eps) for every d, built on the host
+    in a spawn-started process pool (TT rounding is QR-bound), then uploaded."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    ds = list(range(d_range[0], d_range[1] + 1))
+    t0 = time.perf_counter()
+    env_threads = os.environ.get("OPENBLAS_NUM_THREADS")
+    os.environ["OPENBLAS_NUM_THREADS"] = str(max(1, host_cores() // len(ds)))
+    try:
+        with cf.ProcessPoolExecutor(max_workers=len(ds),
+                                    mp_context=mp.get_context("spawn")) as ex:
+            built = list(ex.map(_build_pair, [(d, rmax, seed_base + d, eps) for d in ds]))
+    finally:
+        if env_threads is None:
+            os.environ.pop("OPENBLAS_NUM_THREADS", None)
+        else:
+            os.environ["OPENBLAS_NUM_THREADS"] = env_threads
+    log(f"built {len(ds)} operator pairs in {time.perf_counter() - t0:.1f} s")
+    ops = {}
+    for d, K, P in built:
+        ops[d] = {"K": qtt.Operator(K), "P64": qtt.Operator(P),
+                  "Pbf": qtt.Operator(P, packs=("bf16",)), "rP": max(P.ranks), "data": (K, P)}
+    return ops
+
+
+def _drive(server, ops, trace, pkey, rate_scale=1.0, closed=False):
+    """Submit the trace (Poisson arrival times, or all at once when closed),
+    wait for everything; returns per-request (latency, nrhs) and wall time."""
+    import threading as th
+    from collections import deque
+    ids = deque()
+    t0 = time.perf_counter()
+    done_ev = th.Event()
+
+    def feeder():
+        for r in trace:
+            if not closed:
+                delay = r["arrival"] * rate_scale - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+            o = ops[r["d"]]
+            ids.append((server.submit(o["K"], o[pkey], r["f"]), r))
+        done_ev.set()
+
+    th.Thread(target=feeder, daemon=True).start()
+    out = []
+    while not (done_ev.is_set() and not ids):
+        if not ids:
+            time.sleep(0.0005)
+            continue
+        rid, r = ids.popleft()
+        x, info, (ts, ta, tf) = server.wait(rid)
+        out.append({"lat": tf - ts, "queue": ta - ts, "nrhs": r["f"].shape[0], "d": r["d"],
+                    "rel": max(v for _, v, _ in info), "iters": info[0][0], "x": x, "req": r})
+    wall = time.perf_counter() - t0
+    return out, wall
+
+
+def run_serve(args, spec):
+    import torch
+    from paper_1511_06029_gb300 import build as qbuild, qtt
+    if not os.path.exists(qtt.LIB_PATH):
+        qbuild.build()
+    log = (lambda m: print(m, file=sys.stderr, flush=True))
+    ops = _serve_operators(spec["d_range"], spec["rmax"], spec["seed_base"], spec["eps"], qtt, log)
+    trace = inputs.serving_trace(spec["count"], rate=1.0, seed=spec["seed"],
+                                 d_range=spec["d_range"], rhs_range=spec["rhs_range"])
+    for r in trace:
+        r["f"] = inputs.gaussian_rhs(1 << r["d"], r["nrhs"], r["rhs_seed"])
+    tol = spec["tol"]
+    common = dict(kind="gmres", tol=tol, restart=30, max_iter=300)
+    # 1) mixed precision, saturation: every request submitted at t = 0
+    warm = qtt.Server(slots=spec["slots"], precond_compute="bf16", **common)
+    _drive(warm, ops, trace[:3], "Pbf", closed=True)
+    warm.close()
+    srv = qtt.Server(slots=spec["slots"], precond_compute="bf16", **common)
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    l0 = qtt.kernel_launches()
+    res_sat, wall_sat = _drive(srv, ops, trace, "Pbf", closed=True)
+    sat_rate = len(trace) / wall_sat
+    # 2) mixed precision under Poisson arrivals at 0.8 x the saturation rate
+    scale = 1.0 / (0.8 * sat_rate)  # trace arrivals are for rate 1/s
+    res_p, wall_p = _drive(srv, ops, trace, "Pbf", rate_scale=scale)
+    launches = qtt.kernel_launches() - l0
+    stats = srv.stats()
+    srv.close()
+    clocks = sampler.stop()
+    # 3) plain FP64: the same GMRES with an FP64 P apply, one request at a time,
+    # every request of the trace submitted at t = 0 (its saturation rate)
+    plain_n = min(len(trace), spec["plain_count"])
+    p64 = qtt.Server(slots=1, precond_compute="f64", **common)
+    res_64, wall_64 = _drive(p64, ops, trace[:plain_n], "P64", closed=True)
+    p64.close()
+    # accuracy: the smallest request of the trace against the oracle's GMRES
+    import oracle
+    small = min(res_p, key=lambda r: (r["d"], r["nrhs"]))
+    K, P = ops[small["d"]]["data"]
+    xo, _, _ = oracle.solve_gmres(K, P, small["req"]["f"], a=1.0, tol=1e-13, restart=30)
+    err = float(np.linalg.norm(small["x"] - xo) / np.linalg.norm(xo))
+    lat = sorted(r["lat"] for r in res_p)
+    pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+    rhs_total = sum(r["nrhs"] for r in res_p)
+    mixed_rate = len(res_p) / wall_p
+    line = {
+        "metric": "served solves/s", "value": mixed_rate, "unit": "solves/s",
+        "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": wall_p * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 residual + bf16 P", "data": "synthetic",
+        "config": {"workload": spec["name"], "requests": len(trace),
+                   "d_range": spec["d_range"], "nrhs_range": spec["rhs_range"],
+                   "K_rmax": spec["rmax"], "P": f"round(I - K + K^2, {spec['eps']})",
+                   "P_rmax_by_d": {d: o["rP"] for d, o in ops.items()},
+                   "solver": "right-preconditioned GMRES(30), FP64 Arnoldi and residual",
+                   "tol_rel_residual": tol, "slots": spec["slots"],
+                   "arrivals": f"Poisson at 0.8 x saturation = {0.8 * sat_rate:.3f} req/s"},
+        "serving": {"p50_latency_s": pct(0.5), "p99_latency_s": pct(0.99),
+                    "mean_queue_s": float(np.mean([r["queue"] for r in res_p])),
+                    "rhs_per_s": rhs_total / wall_p,
+                    "saturation_solves_per_s": sat_rate,
+                    "peak_concurrent_requests": stats["peak_running"],
+                    "peak_admitted_bytes": stats["peak_in_use"],
+                    "max_rel_residual": max(r["rel"] for r in res_p),
+                    "error_vs_oracle_smallest_request": err,
+                    "plain_fp64_solves_per_s": len(res_64) / wall_64,
+                    "plain_fp64_requests_timed": plain_n,
+                    "plain_fp64_max_rel_residual": max(r["rel"] for r in res_64),
+                    "mean_gmres_iters_mixed": float(np.mean([r["iters"] for r in res_p])),
+                    "mean_gmres_iters_plain_fp64": float(np.mean([r["iters"] for r in res_64])),
+                    "speedup_vs_plain_fp64_at_saturation":
+                        sat_rate / (len(res_64) / wall_64) if plain_n == len(trace) else None},
+        "roofline": {"bound": "alu", "kernel": "step_f64_kernel (FP64 residual/Arnoldi applies)",
+                     "achieved": None, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+                     "frac": None, "traffic": None},
+        "clocks": clocks,
+        "e2e": {"value": mixed_rate, "unit": "solves/s",
+                "h2d_bytes_per_step": int(sum(r["f"].nbytes for r in trace)),
+                "d2h_bytes_per_step": int(sum(r["f"].nbytes for r in trace)),
+                "note": "requests carry host arrays; uploads and downloads are inside "
+                        "every latency"},
+        "gpu_launches": int(launches),
+    }
+    # FP64 flops actually issued by the K applies of the timed Poisson pass
+    f64 = sum(4.0 * (1 << r["d"]) * r["nrhs"] * ops[r["d"]]["data"][0].sigma * (r["iters"] + 2)
+              for r in res_p)
+    line["roofline"]["achieved"] = f64 / wall_p / 1e9
+    line["roofline"]["frac"] = line["roofline"]["achieved"] / FP64_NOMINAL_GFLOPS
+    for o in ops.values():
+        for k in ("K", "P64", "Pbf"):
+            o[k].close()
+    print(json.dumps(line), flush=True)
+    return 0
+
 
 
 def run_ours(args, spec):
@@ -607,6 +788,8 @@ def main():
     spec = dict(WORKLOADS[args.workload], name=args.workload)
     if args.impl == "reference":
         return run_reference(args, spec)
+    if spec["kind"] == "serve":
+        return run_serve(args, spec)
     return run_ours(args, spec)
 
 

@@ -368,8 +368,11 @@ qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
   int max_rin = 1;
   for (auto &w : B->waves) max_rin = std::max(max_rin, w.max_rin);
   const size_t smem = sizeof(float) * (size_t)max_rin * 2 * 32 * TN;
-  QTT_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+  // raised once to the largest input chunk (rank 64), shared by all threads
+  static cudaError_t attr = cudaFuncSetAttribute(
+      batch_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)(sizeof(float) * (size_t)kMaxRank * 2 * 32 * TN));
+  QTT_CUDA_TRY(attr);
   int per_sm = 0, dev = 0, sms = 0;
   QTT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<TN>, kThreads, smem));
   cudaGetDevice(&dev);

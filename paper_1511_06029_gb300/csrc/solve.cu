@@ -5,7 +5,9 @@
 //   DIRECT : x = P f                     (Tables 1-2, "Solve" column)
 //   GMRES  : A P u = f, x = P u, x0 = 0  (Sec. 5.3: a QTT approximate inverse
 //            as preconditioner inside GMRES; right preconditioning so the
-//            true FP64 residual decides convergence)
+//            true FP64 residual decides convergence), in the flexible form:
+//            Z_j = P v_j is kept and x += Z y, which stays consistent when
+//            P is applied in reduced precision (not exactly linear)
 //   REFINE : x0 = P f; x <- x + P (f - A x)
 // The residual f - A x is always the FP64 apply of K with the subtraction
 // fused into its last step; P may be applied in FP64, FP32, TF32 or BF16.
@@ -165,9 +167,13 @@ qtt_status gmres(const Ctx &c, const double *f, double *x, int64_t ld, const qtt
   const int64_t N = c.N, nr = c.nrhs;
   const int m = prm.restart;
   Scratch S{c.st, {}};
-  double *V, *w, *z, *partial, *h1, *h2, *ss, *ydev;
+  double *V, *Z = nullptr, *w, *z, *partial, *h1, *h2, *ss, *ydev;
   const int64_t nrc = std::min<int64_t>(nr, 65535);
   QTT_TRY(S.get(&V, (size_t)(m + 1) * N * nr));
+  // Flexible GMRES: keep Z_j = P v_j, so that A Z = V H holds exactly for
+  // the preconditioner as applied (a reduced-precision P is not exactly
+  // linear), and update x with Z y.
+  if (c.P) QTT_TRY(S.get(&Z, (size_t)m * N * nr));
   QTT_TRY(S.get(&w, (size_t)N * nr));
   QTT_TRY(S.get(&z, (size_t)N * nr));
   QTT_TRY(S.get(&partial, (size_t)(m + 1) * nrc * blocks_for(N)));
@@ -214,8 +220,9 @@ qtt_status gmres(const Ctx &c, const double *f, double *x, int64_t ld, const qtt
     int jl = 0;
     for (int j = 0; j < m && iters < prm.max_iter; ++j) {
       double *Vj = V + (int64_t)j * vstride;
-      QTT_TRY(apply_P(c, Vj, N, z, N, false));
-      QTT_TRY(apply_A(c, z, w, N));
+      double *Zj = c.P ? Z + (int64_t)j * vstride : Vj;
+      if (c.P) QTT_TRY(apply_P(c, Vj, N, Zj, N, false));
+      QTT_TRY(apply_A(c, Zj, w, N));
       const int nv = j + 1;
       QTT_CUDA_OK(vec_dots(vecs(V, N, vstride), nv, vecs(w, N), N, nr, partial, h1, nullptr, c.st),
                   "dots");
@@ -276,13 +283,10 @@ qtt_status gmres(const Ctx &c, const double *f, double *x, int64_t ld, const qtt
     }
     QTT_CUDA_OK(cudaMemcpyAsync(ydev, y.data(), sizeof(double) * jl * nr, cudaMemcpyHostToDevice,
                                 c.st), "memcpy");
-    QTT_CUDA_OK(vec_combine(vecs(z, N), vecs(V, N, vstride), jl, ydev, N, nr, c.st), "combine");
-    if (ld == N) {
-      QTT_TRY(apply_P(c, z, N, x, N, true));
-    } else {
-      QTT_TRY(apply_P(c, z, N, w, N, false));
-      QTT_CUDA_OK(vec_axpy(vecs(x, ld), vecs(w, N), 1.0, N, nr, c.st), "axpy");
-    }
+    // x += Z y (Z = V without a preconditioner)
+    QTT_CUDA_OK(vec_combine(vecs(z, N), vecs(c.P ? Z : V, N, vstride), jl, ydev, N, nr, c.st),
+                "combine");
+    QTT_CUDA_OK(vec_axpy(vecs(x, ld), vecs(z, N), 1.0, N, nr, c.st), "axpy");
   }
   for (int64_t r = 0; r < nr; ++r) {
     info[r].iters = iters;

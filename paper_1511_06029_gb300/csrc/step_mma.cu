@@ -190,12 +190,22 @@ __global__ void __launch_bounds__(kThreads) step_mma_bf16_kernel(StepMMA s) {
 }
 
 template <int MT>
+size_t smem_bytes(int Kp) {
+  return sizeof(__nv_bfloat16) *
+         ((size_t)MT * 16 * (Kp + kPadB) + (size_t)kStages * Kp * (kBN + kPadB));
+}
+
+template <int MT>
 cudaError_t launch_mt(const StepMMA &s, cudaStream_t st) {
-  const size_t smem = sizeof(__nv_bfloat16) * ((size_t)MT * 16 * (s.Kp + kPadB) +
-                                               (size_t)kStages * s.Kp * (kBN + kPadB));
-  cudaError_t e = cudaFuncSetAttribute(step_mma_bf16_kernel<MT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  // The dynamic shared-memory limit is a property of the kernel shared by all
+  // host threads: raise it once to the largest this instantiation can use
+  // (Kp = 2 x 64), never per call, so concurrent launches cannot lower it
+  // under each other.
+  static cudaError_t attr = cudaFuncSetAttribute(
+      step_mma_bf16_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)smem_bytes<MT>(2 * kMmaMaxRank));
+  if (attr != cudaSuccess) return attr;
+  const size_t smem = smem_bytes<MT>(s.Kp);
   int per_sm = 1, dev = 0, sms = 148;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_mma_bf16_kernel<MT>, kThreads, smem);
   cudaGetDevice(&dev);

@@ -293,7 +293,8 @@ def tt_round(op: QTTData, eps: float) -> QTTData:
         Q, R = np.linalg.qr(M.T)  # M^T = Q R  =>  M = R^T Q^T
         rnew = Q.shape[1]
         cores[k] = Q.T.reshape(rnew, n, rb)
-        cores[k - 1] = np.einsum("anb,bc->anc", cores[k - 1], R.T)
+        pa, pn, _ = cores[k - 1].shape
+        cores[k - 1] = (cores[k - 1].reshape(pa * pn, -1) @ R.T).reshape(pa, pn, rnew)
         ranks[k] = rnew
     norm = np.linalg.norm(cores[0].ravel())
     delta = eps * norm / math.sqrt(max(d - 1, 1))
@@ -309,7 +310,8 @@ def tt_round(op: QTTData, eps: float) -> QTTData:
                 break
         cores[k] = U[:, :r].reshape(ra, n, r)
         SV = S[:r, None] * Vt[:r]
-        cores[k + 1] = np.einsum("ab,bnc->anc", SV, cores[k + 1])
+        _, nn, rc = cores[k + 1].shape
+        cores[k + 1] = (SV @ cores[k + 1].reshape(rb, nn * rc)).reshape(r, nn, rc)
         ranks[k + 1] = r
     out = [c.reshape(c.shape[0], 2, 2, c.shape[2]) for c in cores]
     return QTTData(ranks, out, dict(op.meta, rounded_eps=eps))

@@ -54,6 +54,14 @@ SIGNATURES = {
     "qtt_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                             ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_size_t)]),
     "qtt_batch_destroy": (_I, [_P]),
+    "qtt_server_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _P]),
+    "qtt_server_submit": (_I, [_P, _P, _P, _P, _P, _L, ctypes.POINTER(_L)]),
+    "qtt_server_poll": (_I, [_P, _L, _I, ctypes.POINTER(_I), _P, ctypes.POINTER(_D),
+                             ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "qtt_server_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                              ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                              ctypes.POINTER(_I)]),
+    "qtt_server_destroy": (_I, [_P]),
 }
 
 
@@ -300,6 +308,74 @@ class Batch:
     def close(self):
         if self._h is not None:
             load_library().qtt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-admission solve server (qtt_server_*).  submit() takes host
+    numpy arrays (nrhs, N) float64; the result lands in the returned x array
+    when poll()/wait() reports the request done."""
+
+    def __init__(self, slots=4, mem_budget=0, kind="gmres", a=1.0, tol=1e-10, restart=30,
+                 max_iter=300, precond_compute="bf16", inner_iters=0):
+        lib = load_library()
+        _torch()
+        self.prm = SolveParams(SOLVE_KINDS[kind], a, tol, restart, max_iter,
+                               DTYPES[precond_compute], inner_iters)
+        h = ctypes.c_void_p()
+        _check(lib.qtt_server_create(ctypes.byref(h), slots, mem_budget, ctypes.byref(self.prm)),
+               "qtt_server_create")
+        self._h = h
+        self._live = {}
+
+    def submit(self, K, P, f):
+        f = np.ascontiguousarray(np.atleast_2d(np.asarray(f, dtype=np.float64)))
+        x = np.empty_like(f)
+        rid = ctypes.c_int64()
+        _check(load_library().qtt_server_submit(
+            self._h, K.handle if K is not None else None, P.handle if P is not None else None,
+            f.ctypes.data_as(_P), x.ctypes.data_as(_P), f.shape[0], ctypes.byref(rid)),
+            "qtt_server_submit")
+        self._live[rid.value] = (f, x)
+        return rid.value
+
+    def poll(self, rid, wait=False):
+        """None while running; else (x, info, (t_submit, t_admit, t_finish))."""
+        f, x = self._live[rid]
+        done = ctypes.c_int()
+        info = (SolveInfo * f.shape[0])()
+        ts, ta, tf = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        st = load_library().qtt_server_poll(self._h, rid, 1 if wait else 0, ctypes.byref(done),
+                                            info, ctypes.byref(ts), ctypes.byref(ta),
+                                            ctypes.byref(tf))
+        if not done.value:
+            _check(st, "qtt_server_poll")
+            return None
+        del self._live[rid]
+        _check(st, "qtt_server_poll")
+        return x, [(i.iters, i.rel_residual, i.status) for i in info], (ts.value, ta.value, tf.value)
+
+    def wait(self, rid):
+        return self.poll(rid, wait=True)
+
+    def stats(self):
+        p, r, pi = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        iu, piu = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(load_library().qtt_server_stats(self._h, ctypes.byref(p), ctypes.byref(r),
+                                               ctypes.byref(iu), ctypes.byref(piu),
+                                               ctypes.byref(pi)), "qtt_server_stats")
+        return {"pending": p.value, "running": r.value, "in_use": iu.value,
+                "peak_in_use": piu.value, "peak_running": pi.value}
+
+    def close(self):
+        if self._h is not None:
+            load_library().qtt_server_destroy(self._h)
             self._h = None
 
     def __del__(self):
