@@ -94,6 +94,8 @@ WORKLOADS = {
                           compute="f64"),
     "batched_f32": dict(kind="batched", compute="f32", count=256, seed=4),
     "batched_tf32": dict(kind="batched", compute="tf32", count=256, seed=4),
+    "batched_f32_small": dict(kind="batched", compute="f32", count=24, seed=4,
+                              d_range=(14, 16)),
     "serve": dict(kind="serve", d_range=(14, 22), rhs_range=(1, 16), rmax=32, seed_base=5000,
                   eps=1e-4, seed=5, count=40, slots=6, tol=1e-10, plain_count=40),
     "serve_small": dict(kind="serve", d_range=(14, 18), rhs_range=(1, 16), rmax=32,
@@ -362,7 +364,8 @@ class BatchedRun:
         import torch
         from paper_1511_06029_gb300 import qtt
         self.spec = spec
-        self.items = inputs.batched_workload(count=spec["count"], seed=spec["seed"] + 97 * rank)
+        self.items = inputs.batched_workload(count=spec["count"], seed=spec["seed"] + 97 * rank,
+                                             d_range=spec.get("d_range", (12, 20)))
         self.compute = spec["compute"]
         self.ops, self.xs, self.ys = [], [], []
         self.flops = 0.0
@@ -420,7 +423,8 @@ class BatchedRun:
 
     def config(self):
         return {"workload": self.spec["name"], "operators": len(self.items),
-                "d_range": [12, 20], "rmax_range": [16, 40], "nrhs_range": [1, 32],
+                "d_range": list(self.spec.get("d_range", (12, 20))), "rmax_range": [16, 40],
+                "nrhs_range": [1, 32],
                 "total_rhs": sum(it["nrhs"] for it in self.items),
                 "flops_per_step_per_gpu": self.flops, "compute": self.compute,
                 "waves": self.info["waves"], "grid": self.info["grid"],

@@ -14,11 +14,17 @@
 // and every CTA leaves).
 //
 // Per item the CTA stages the input chunk (r_k ranks x 2 x 32*TN positions)
-// in shared memory (L2-coherent loads: the intermediate was written by other
-// CTAs of this launch), then each warp computes a block of TB output ranks
-// for the 32*TN pairs with FP32 multiply-adds (TF32 mode rounds operands to
-// TF32 as they are staged; cores are packed TF32-rounded).  TB = ceil(r_out/8)
-// so the eight warps cover all output ranks in one pass.
+// in shared memory with cp.async (L2 copies: the intermediate was written by
+// other CTAs of this launch); the next item is taken before the current one
+// is computed and, when its dependency is already complete, its copies are
+// issued at once so they overlap the current item's arithmetic (otherwise it
+// is waited for after the current item is published -- never before, which
+// keeps the no-deadlock argument above).  The core of the current (operator,
+// step) sits in shared memory while consecutive items share it.  Each warp
+// computes a block of TB output ranks for the 32*TN pairs with FP32
+// multiply-adds (TF32 mode rounds each staged operand to TF32; cores are
+// packed TF32-rounded).  TB = ceil(r_out/8), so the eight warps cover all
+// output ranks in one pass.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -61,6 +67,8 @@ struct BWave {
   int *status;
   int tf32;
   long long wait_budget;  // clock cycles
+  int max_k;              // 2 x max input rank of the wave (rows of a chunk)
+  int core_floats;        // shared floats reserved for one core (16-aligned)
 };
 
 __device__ __forceinline__ float tf32_rne_b(float x) {
@@ -72,8 +80,27 @@ __device__ __forceinline__ float tf32_rne_b(float x) {
   return __uint_as_float(u);
 }
 
+__device__ __forceinline__ unsigned smem_u32b(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async4(unsigned dst, const void *src, int n) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(n));
+}
+__device__ __forceinline__ void cp_async16b(unsigned dst, const void *src, int n) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+// One work item, decoded.
+struct Item {
+  long long idx;
+  int seg;
+};
+
 template <int TB, int TN>
-__device__ __forceinline__ void rank_block(const float *sm, const float *G, int rin, int rpad,
+__device__ __forceinline__ void rank_block(const float *sm, const float *sG, int rin, int rpad,
                                            int b0, int rout, int lane, int npair_chunk,
                                            float *out, int64_t N, int64_t q0, int k,
                                            int64_t npairs) {
@@ -91,12 +118,11 @@ __device__ __forceinline__ void rank_block(const float *sm, const float *G, int 
       float v[TN];
 #pragma unroll
       for (int m = 0; m < TN; ++m) v[m] = srow[lane + 32 * m];
-      const float2 *g2 = reinterpret_cast<const float2 *>(G + ((int64_t)(2 * a + j) * rpad + b0) * 2);
+      // core row (a, j) in shared memory; ranks past the padded row read 0
+      const float2 *g2 = reinterpret_cast<const float2 *>(sG + ((2 * a + j) * rpad + b0) * 2);
 #pragma unroll
       for (int t = 0; t < TB; ++t) {
-        // ranks past the padded row (last warp, r_out near a multiple of 8
-        // times TB) contribute nothing and must not be read
-        const float2 g = b0 + t < rpad ? __ldg(g2 + t) : make_float2(0.0f, 0.0f);
+        const float2 g = b0 + t < rpad ? g2[t] : make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int m = 0; m < TN; ++m) {
           acc[t][0][m] = fmaf(g.x, v[m], acc[t][0][m]);
@@ -121,95 +147,253 @@ __device__ __forceinline__ void rank_block(const float *sm, const float *G, int 
   }
 }
 
-template <int TN>
-__global__ void __launch_bounds__(kThreads) batch_kernel(BWave w) {
-  extern __shared__ float sm[];
-  __shared__ long long s_item;
-  __shared__ int s_seg;
-  __shared__ int s_abort;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int PC = 32 * TN;  // pairs per item
-  for (;;) {
-    if (tid == 0) {
-      const long long item = (long long)atomicAdd(w.next, 1ull);
-      s_item = item;
-      int abort = *(volatile int *)w.status != 0;
-      int seg = 0;
-      if (!abort && item < w.total) {
-        int lo = 0, hi = w.nseg - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (w.segs[mid].first <= item) lo = mid; else hi = mid - 1;
-        }
-        seg = lo;
-        const int dep = w.segs[seg].dep;
-        if (dep >= 0) {
-          const unsigned target = (unsigned)w.segs[dep].ntiles;
-          const long long t0 = clock64();
-          while (*(volatile unsigned *)(w.done + dep) < target) {
-            if (*(volatile int *)w.status != 0) { abort = 1; break; }
-            if (clock64() - t0 > w.wait_budget) {
-              atomicCAS(w.status, 0, (int)QTT_ERR_TIMEOUT);
-              abort = 1;
-              break;
-            }
-            __nanosleep(64);
-          }
-          __threadfence();
+// Segment holding `item` (all 32 lanes of warp 0): a 32-way search over the
+// segments' first items (increasing), one parallel load per round, so ~3
+// rounds for thousands of segments instead of a dozen dependent loads.
+__device__ __forceinline__ int find_seg(const BWave &w, long long item) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = w.nseg;  // segs[lo].first <= item < segs[hi].first
+  while (hi - lo > 1) {
+    const int step = (hi - lo + 31) / 32;
+    const int idx = lo + lane * step;
+    const bool pred = idx < hi && w.segs[idx].first <= item;
+    const unsigned m = __ballot_sync(0xffffffffu, pred);  // a prefix of lanes; lane 0 set
+    const int last = 31 - __clz(m);
+    lo += last * step;
+    hi = min(lo + step, hi);
+  }
+  return lo;
+}
+
+// Items are taken in blocks of kGrab consecutive indices (one atomic per
+// block) and processed in index order, so the smallest unprocessed item is
+// always at the head of some running CTA's block and every dependency wait
+// ends.  Within a block the segment advances incrementally and the
+// dependency is re-checked only when the segment changes (done counters only
+// grow, so a satisfied dependency stays satisfied).
+constexpr int kGrab = 8;
+
+struct Fetch {
+  long long cur, end;  // remaining block [cur, end)
+  int seg;             // segment of the last item handed out (-1: none)
+};
+
+// Take the next item (warp 0) and check, without waiting, whether its
+// operator's previous step is complete.  Broadcast through shared memory.
+__device__ __forceinline__ void fetch_item(const BWave &w, Fetch *f, Item *s_item, int *s_ready) {
+  if (threadIdx.x < 32) {
+    long long idx = 0;
+    int need_search = 0;
+    if (threadIdx.x == 0) {
+      if (f->cur >= f->end) {
+        const long long b = (long long)atomicAdd(w.next, (unsigned long long)kGrab);
+        f->cur = b;
+        f->end = b + kGrab < w.total ? b + kGrab : w.total;
+        need_search = 1;
+      }
+      if (f->seg < 0) need_search = 1;
+      idx = f->cur < f->end ? f->cur++ : w.total;
+    }
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    need_search = __shfl_sync(0xffffffffu, need_search, 0);
+    int seg = 0;
+    if (idx < w.total) {
+      if (need_search) {
+        seg = find_seg(w, idx);
+      } else if (threadIdx.x == 0) {
+        seg = f->seg;
+        while (seg + 1 < w.nseg && w.segs[seg + 1].first <= idx) ++seg;
+      }
+    }
+    if (threadIdx.x == 0) {
+      int ready = 0;
+      if (idx < w.total) {
+        if (seg == f->seg) {
+          ready = 1;
+        } else {
+          const int dep = w.segs[seg].dep;
+          ready = dep < 0 ||
+                  *(volatile unsigned *)(w.done + dep) >= (unsigned)w.segs[dep].ntiles;
+          if (ready) __threadfence();
         }
       }
-      s_seg = seg;
-      s_abort = abort;
+      f->seg = ready ? seg : -1;  // only a dependency seen complete is remembered
+      s_item->idx = idx;
+      s_item->seg = seg;
+      *s_ready = ready;
     }
+  }
+}
+
+// Wait (thread 0, bounded) until the item's dependency is complete; returns
+// through *s_abort whether the kernel must stop.
+__device__ __forceinline__ void wait_item(const BWave &w, const Item &it, int *s_abort) {
+  if (threadIdx.x == 0) {
+    int abort = *(volatile int *)w.status != 0;
+    const int dep = w.segs[it.seg].dep;
+    if (!abort && dep >= 0) {
+      const unsigned target = (unsigned)w.segs[dep].ntiles;
+      const long long t0 = clock64();
+      while (*(volatile unsigned *)(w.done + dep) < target) {
+        if (*(volatile int *)w.status != 0) { abort = 1; break; }
+        if (clock64() - t0 > w.wait_budget) {
+          atomicCAS(w.status, 0, (int)QTT_ERR_TIMEOUT);
+          abort = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+      __threadfence();
+    }
+    *s_abort = abort;
+  }
+}
+
+// Issue the asynchronous copies of an item's input chunk into `buf`
+// ([2a + j][pair], PC pairs per row).  16-byte copies when 4 consecutive
+// pairs are 4 consecutive positions (k >= 2), 4-byte copies otherwise;
+// pairs past the end are zero-filled.
+template <int PC>
+__device__ __forceinline__ void stage_item(const BWave &w, const Item &it, float *buf) {
+  const BSeg &sg = w.segs[it.seg];
+  const BOp &op = w.ops[sg.op];
+  const int k = sg.k, rin = op.ranks[k];
+  const int64_t N = op.N, npairs = N >> 1;
+  const int64_t tile = it.idx - sg.first;
+  const int64_t c = tile / sg.tiles_per_rhs;
+  const int64_t q0 = (tile % sg.tiles_per_rhs) * PC;
+  const int64_t bit = (int64_t)1 << k, low = bit - 1;
+  const float *in = k == 0 ? op.x + c * op.ld
+                           : ((k - 1) & 1 ? op.buf1 : op.buf0) + c * (int64_t)rin * N;
+  if (k >= 2) {
+    constexpr int PIECES = PC / 4;
+    for (int e = threadIdx.x; e < 2 * rin * PIECES; e += kThreads) {
+      const int kk = e / PIECES, pc = e % PIECES;
+      const int64_t q = q0 + 4 * pc;
+      const bool ok = q < npairs;
+      const float *src = in + (int64_t)(kk >> 1) * N + (((q & ~low) << 1) | (q & low)) +
+                         ((kk & 1) ? bit : 0);
+      cp_async16b(smem_u32b(buf + kk * PC + 4 * pc), ok ? src : op.x, ok ? 16 : 0);
+    }
+  } else {
+    for (int e = threadIdx.x; e < 2 * rin * PC; e += kThreads) {
+      const int kk = e / PC, qq = e % PC;
+      const int64_t q = q0 + qq;
+      const bool ok = q < npairs;
+      const float *src = in + (int64_t)(kk >> 1) * N + (((q & ~low) << 1) | (q & low)) +
+                         ((kk & 1) ? bit : 0);
+      cp_async4(smem_u32b(buf + kk * PC + qq), ok ? src : op.x, ok ? 4 : 0);
+    }
+  }
+}
+
+template <int TN, int TBMAX>
+__global__ void __launch_bounds__(kThreads) batch_kernel(BWave w) {
+  extern __shared__ __align__(16) float sm[];
+  constexpr int PC = 32 * TN;  // pairs per item
+  __shared__ Item s_item;
+  __shared__ Fetch s_fetch;
+  __shared__ int s_ready, s_abort, s_gseg;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float *sG = sm;                              // core of the current segment
+  float *sB0 = sm + w.core_floats;             // input chunk, two buffers
+  float *sB1 = sB0 + (size_t)w.max_k * PC;
+  if (tid == 0) {
+    s_gseg = -1;
+    s_fetch.cur = s_fetch.end = 0;
+    s_fetch.seg = -1;
+  }
+
+  // first item: fetch, wait for it, stage it
+  fetch_item(w, &s_fetch, &s_item, &s_ready);
+  __syncthreads();
+  Item cur = s_item;
+  if (cur.idx >= w.total) return;
+  if (!s_ready) {
+    wait_item(w, cur, &s_abort);
     __syncthreads();
-    const long long item = s_item;
-    if (item >= w.total || s_abort) return;
-    const BSeg sg = w.segs[s_seg];
+    if (s_abort) return;
+  }
+  stage_item<PC>(w, cur, sB0);
+  cp_commit();
+  int buf = 0;
+  for (;;) {
+    // take the next item now; prefetch its input only if it is already ready
+    // (the previous iteration ended with a barrier, so s_item is free)
+    fetch_item(w, &s_fetch, &s_item, &s_ready);
+    __syncthreads();
+    const Item nxt = s_item;
+    const bool has_next = nxt.idx < w.total;
+    const bool prefetched = has_next && s_ready;
+    if (prefetched) stage_item<PC>(w, nxt, buf ? sB0 : sB1);
+    cp_commit();
+    cp_wait_one();  // the current item's group is complete
+    __syncthreads();
+
+    const BSeg sg = w.segs[cur.seg];
     const BOp &op = w.ops[sg.op];
     const int k = sg.k;
     const int rin = op.ranks[k], rout = op.ranks[k + 1];
+    const int rpad = op.rpad[k + 1];
+    float *sb = buf ? sB1 : sB0;
+    // core of this (operator, step) into shared memory when it changes; TF32
+    // rounding of the staged operands (both uniform across the CTA)
+    const bool new_core = s_gseg != cur.seg;
+    if (new_core) {
+      const float *G = op.cores + op.coff[k];
+      for (int e = tid; e < 2 * rin * 2 * rpad; e += kThreads) sG[e] = __ldg(G + e);
+    }
+    if (w.tf32)
+      for (int e = tid; e < 2 * rin * PC; e += kThreads) sb[e] = tf32_rne_b(sb[e]);
+    if (new_core || w.tf32) __syncthreads();
+    if (tid == 0) s_gseg = cur.seg;
+
     const int64_t N = op.N, npairs = N >> 1;
-    const int64_t tile = item - sg.first;
+    const int64_t tile = cur.idx - sg.first;
     const int64_t c = tile / sg.tiles_per_rhs;
     const int64_t q0 = (tile % sg.tiles_per_rhs) * PC;
-    const int64_t bit = (int64_t)1 << k, low = bit - 1;
-    // ---- stage the input chunk: sm[(2a + j) * PC + qq]
-    const float *in = k == 0 ? op.x + c * op.ld
-                             : ((k - 1) & 1 ? op.buf1 : op.buf0) + c * (int64_t)rin * N;
-    for (int e = tid; e < rin * 2 * PC; e += kThreads) {
-      const int qq = e % PC, aj = e / PC;
-      const int a = aj >> 1, j = aj & 1;
-      const int64_t q = q0 + qq;
-      float v = 0.0f;
-      if (q < npairs) {
-        const int64_t p = (((q & ~low) << 1) | (q & low)) + (j ? bit : 0);
-        v = k == 0 ? __ldg(in + p) : __ldcg(in + (int64_t)a * N + p);
-      }
-      sm[e] = w.tf32 ? tf32_rne_b(v) : v;
-    }
-    __syncthreads();
     float *out = k == op.d - 1 ? op.y + c * op.ld
                                : (k & 1 ? op.buf1 : op.buf0) + c * (int64_t)rout * N;
-    const float *G = op.cores + op.coff[k];
-    const int rpad = op.rpad[k + 1];
     const int TB = (rout + 7) / 8;
     const int b0 = warp * TB;
     if (b0 < rout) {
-      switch (TB) {
-        case 1: rank_block<1, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-        case 2: rank_block<2, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-        case 3: rank_block<3, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-        case 4: rank_block<4, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-        case 5: rank_block<5, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-        case 6: rank_block<6, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-        case 7: rank_block<7, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-        default: rank_block<8, TN>(sm, G, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+      switch (TB > TBMAX ? TBMAX : TB) {
+        case 1: rank_block<1, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+        case 2: rank_block<2, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+        case 3: rank_block<3, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+        case 4: rank_block<4, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+        case 5: rank_block<5, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+        default:
+          if constexpr (TBMAX > 5) {
+            switch (TB) {
+              case 6: rank_block<6, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+              case 7: rank_block<7, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+              default: rank_block<8, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+            }
+          }
+          break;
       }
     }
-    __threadfence();
+    // publish this item: the barrier orders every thread's stores before
+    // thread 0's device-scope fence and counter update
     __syncthreads();
-    if (tid == 0) atomicAdd(w.done + s_seg, 1u);
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(w.done + cur.seg, 1u);
+    }
+    if (!has_next) break;
+    if (!prefetched) {
+      // its dependency was not complete when taken: wait (bounded), then copy
+      wait_item(w, nxt, &s_abort);
+      __syncthreads();
+      if (s_abort) break;
+      stage_item<PC>(w, nxt, buf ? sB0 : sB1);
+      cp_commit();
+    }
+    cur = nxt;
+    buf ^= 1;
   }
+  cp_wait_all();
 }
 
 }  // namespace
@@ -363,18 +547,23 @@ qtt_status build_plan(qtt_batch *B, cudaStream_t st) {
   return QTT_OK;
 }
 
-template <int TN>
+template <int TN, int TBMAX>
 qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
   int max_rin = 1;
   for (auto &w : B->waves) max_rin = std::max(max_rin, w.max_rin);
-  const size_t smem = sizeof(float) * (size_t)max_rin * 2 * 32 * TN;
-  // raised once to the largest input chunk (rank 64), shared by all threads
+  const int PC = 32 * TN;
+  const int max_k = 2 * max_rin;
+  const int rpad_max = (max_rin + 3) / 4 * 4;
+  const int core_floats = (max_k * 2 * rpad_max + 15) / 16 * 16;
+  const size_t smem = sizeof(float) * ((size_t)core_floats + 2 * (size_t)max_k * PC);
+  // raised once to the largest footprint (rank 64), shared by all threads
   static cudaError_t attr = cudaFuncSetAttribute(
-      batch_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)(sizeof(float) * (size_t)kMaxRank * 2 * 32 * TN));
+      batch_kernel<TN, TBMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)(sizeof(float) * ((size_t)(2 * kMaxRank * 2 * kMaxRank) +
+                             2 * (size_t)(2 * kMaxRank) * PC)));
   QTT_CUDA_TRY(attr);
   int per_sm = 0, dev = 0, sms = 0;
-  QTT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<TN>, kThreads, smem));
+  QTT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<TN, TBMAX>, kThreads, smem));
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int clk_khz = 2000000;
@@ -394,7 +583,9 @@ qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
     bw.status = B->d_status;
     bw.tf32 = B->compute == QTT_TF32;
     bw.wait_budget = (long long)clk_khz * 1000LL * 4;  // ~4 s of clock
-    batch_kernel<TN><<<B->grid, kThreads, smem, st>>>(bw);
+    bw.max_k = max_k;
+    bw.core_floats = core_floats;
+    batch_kernel<TN, TBMAX><<<B->grid, kThreads, smem, st>>>(bw);
     count_launches(1);
     QTT_CUDA_TRY(cudaGetLastError());
   }
@@ -402,9 +593,13 @@ qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
 }
 
 qtt_status launch_waves(qtt_batch *B, cudaStream_t st) {
+  // register footprint follows the largest rank block a wave needs
+  int max_r = 1;
+  for (auto &w : B->waves) max_r = std::max(max_r, w.max_rin);
+  const bool small = max_r <= 40;  // TB = ceil(r/8) <= 5
   switch (B->variant) {
-    case 2: return launch_waves_t<2>(B, st);
-    default: return launch_waves_t<4>(B, st);
+    case 2: return small ? launch_waves_t<2, 5>(B, st) : launch_waves_t<2, 8>(B, st);
+    default: return small ? launch_waves_t<4, 5>(B, st) : launch_waves_t<4, 8>(B, st);
   }
 }
 
