@@ -26,10 +26,12 @@ Workloads (a "step" is one pass of the hot path over one batch of input):
                   graph, tile variant chosen by the autotuner.
   serve           Poisson-arriving solve requests (d 14..22, 1..16 RHS) of
                   (I + K) x = f, ||K||_2 = 0.5, r_max 32, through the solve
-                  server: GMRES(30) to 1e-10 with the rounded preconditioner
-                  round(I - K + K^2, 1e-4) applied in BF16 and FP64 residuals;
-                  p50/p99 latency, solves/s, and the plain FP64 form (FP64 P
-                  apply, one request at a time) on the same GPU.
+                  server: flexible GMRES(30) to 1e-10 whose preconditioner is
+                  the rounded round(I - K + K^2, 1e-4) applied in BF16 plus one
+                  inner Richardson step (K, P in BF16), FP64 residuals and
+                  Arnoldi; p50/p99 latency, solves/s, and the plain FP64 form
+                  (FP64 P apply, one request at a time) on the same GPU.
+  serve_f32       the same with the preconditioner steps in FP32.
   serve_small     the same with d 14..18.
   refine_bf16_d21 / refine_f64_d21
                   solve (I + K) x = f, ||K||_2 = 0.5, d = 21, r_max = 48, 64
@@ -97,7 +99,15 @@ WORKLOADS = {
     "batched_f32_small": dict(kind="batched", compute="f32", count=24, seed=4,
                               d_range=(14, 16)),
     "serve": dict(kind="serve", d_range=(14, 22), rhs_range=(1, 16), rmax=32, seed_base=5000,
-                  eps=1e-4, seed=5, count=40, slots=6, tol=1e-10, plain_count=40),
+                  eps=1e-4, seed=5, count=40, slots=6, tol=1e-10, plain_count=40,
+                  pc="bf16", inner=1),
+    "serve_f32": dict(kind="serve", d_range=(14, 22), rhs_range=(1, 16), rmax=32,
+                      seed_base=5000, eps=1e-4, seed=5, count=40, slots=6, tol=1e-10,
+                      plain_count=40, pc="f32", inner=1),
+    "serve_probe": dict(kind="serve", d_range=(14, 22), rhs_range=(1, 16), rmax=32,
+                        seed_base=5000, eps=1e-4, seed=5, count=24, slots=6, tol=1e-10,
+                        plain_count=24,
+                        probe=[("bf16", 0), ("bf16", 1), ("f32", 0), ("f32", 1), ("tf32", 1)]),
     "serve_small": dict(kind="serve", d_range=(14, 18), rhs_range=(1, 16), rmax=32,
                         seed_base=5000, eps=1e-4, seed=5, count=40, slots=6, tol=1e-10,
                         plain_count=40),
@@ -550,8 +560,9 @@ def _serve_operators(d_range, rmax, seed_base, eps, qtt, log):
     log(f"built {len(ds)} operator pairs in {time.perf_counter() - t0:.1f} s")
     ops = {}
     for d, K, P in built:
-        ops[d] = {"K": qtt.Operator(K), "P64": qtt.Operator(P),
-                  "Pbf": qtt.Operator(P, packs=("bf16",)), "rP": max(P.ranks), "data": (K, P)}
+        ops[d] = {"K": qtt.Operator(K, packs=("bf16", "f32", "tf32")), "P64": qtt.Operator(P),
+                  "Pbf": qtt.Operator(P, packs=("bf16", "f32", "tf32")), "rP": max(P.ranks),
+                  "data": (K, P)}
     return ops
 
 
@@ -601,11 +612,30 @@ def run_serve(args, spec):
         r["f"] = inputs.gaussian_rhs(1 << r["d"], r["nrhs"], r["rhs_seed"])
     tol = spec["tol"]
     common = dict(kind="gmres", tol=tol, restart=30, max_iter=300)
+    mixed = dict(precond_compute=spec.get("pc", "bf16"), inner_iters=spec.get("inner", 0))
+    if spec.get("probe"):
+        # saturation rate of several (precision, inner steps) choices only
+        out = {}
+        for pc, inner in spec["probe"]:
+            srv = qtt.Server(slots=spec["slots"], precond_compute=pc, inner_iters=inner, **common)
+            _drive(srv, ops, trace[:3], "Pbf", closed=True)
+            res, wall = _drive(srv, ops, trace, "Pbf", closed=True)
+            srv.close()
+            out[f"{pc}_inner{inner}"] = {"solves_per_s": len(res) / wall,
+                                         "mean_iters": float(np.mean([r["iters"] for r in res])),
+                                         "max_rel": max(r["rel"] for r in res)}
+        srv = qtt.Server(slots=1, precond_compute="f64", **common)
+        res, wall = _drive(srv, ops, trace, "P64", closed=True)
+        srv.close()
+        out["plain_f64_1slot"] = {"solves_per_s": len(res) / wall,
+                                  "mean_iters": float(np.mean([r["iters"] for r in res]))}
+        print(json.dumps({"probe": out}), flush=True)
+        return 0
     # 1) mixed precision, saturation: every request submitted at t = 0
-    warm = qtt.Server(slots=spec["slots"], precond_compute="bf16", **common)
+    warm = qtt.Server(slots=spec["slots"], **mixed, **common)
     _drive(warm, ops, trace[:3], "Pbf", closed=True)
     warm.close()
-    srv = qtt.Server(slots=spec["slots"], precond_compute="bf16", **common)
+    srv = qtt.Server(slots=spec["slots"], **mixed, **common)
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     sampler.start()
     l0 = qtt.kernel_launches()
@@ -638,13 +668,15 @@ def run_serve(args, spec):
         "metric": "served solves/s", "value": mixed_rate, "unit": "solves/s",
         "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": wall_p * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 residual + bf16 P", "data": "synthetic",
+        "dtype": f"f64 residual + {mixed['precond_compute']} P", "data": "synthetic",
         "config": {"workload": spec["name"], "requests": len(trace),
                    "d_range": spec["d_range"], "nrhs_range": spec["rhs_range"],
                    "K_rmax": spec["rmax"], "P": f"round(I - K + K^2, {spec['eps']})",
                    "P_rmax_by_d": {d: o["rP"] for d, o in ops.items()},
                    "solver": "right-preconditioned GMRES(30), FP64 Arnoldi and residual",
                    "tol_rel_residual": tol, "slots": spec["slots"],
+                   "precond_compute": mixed["precond_compute"],
+                   "inner_iters": mixed["inner_iters"],
                    "arrivals": f"Poisson at 0.8 x saturation = {0.8 * sat_rate:.3f} req/s"},
         "serving": {"p50_latency_s": pct(0.5), "p99_latency_s": pct(0.99),
                     "mean_queue_s": float(np.mean([r["queue"] for r in res_p])),

@@ -173,12 +173,12 @@ typedef struct {
   int max_iter;          /* cap on outer corrections (REFINE) or Arnoldi steps */
   qtt_dtype precond_compute; /* arithmetic of the P applies (and of the inner
                                 K applies of REFINE) */
-  int inner_iters;       /* REFINE only: 0 = the correction is z = P r; s > 0 =
-                            z from s inner steps z <- z + P (r - (a z + K z))
-                            (P = identity if NULL) with K and P applied in
-                            precond_compute and vectors in FP64, starting
-                            from z = P r.  K then needs the matching
-                            QTT_PACK_* copy. */
+  int inner_iters;       /* REFINE and GMRES: the correction / flexible
+                            preconditioner is M r = P r when 0; when s > 0,
+                            s inner steps z <- z + P (r - (a z + K z)) from
+                            z = P r (P = identity if NULL) with K and P
+                            applied in precond_compute and vectors in FP64.
+                            K then needs the matching QTT_PACK_* copy. */
 } qtt_solve_params;
 
 typedef struct {

@@ -192,6 +192,16 @@ static bool use_tensor_cores() {
   return on;
 }
 
+// FP32/TF32 intermediate steps use the staged kernel unless
+// QTT_NO_STAGED_F32 is set (kept for A/B measurements).
+static bool use_staged_f32() {
+  static const bool on = [] {
+    const char *v = std::getenv("QTT_NO_STAGED_F32");
+    return !(v && *v && *v != '0');
+  }();
+  return on;
+}
+
 static size_t dtype_size(qtt_dtype t) {
   return t == QTT_F64 ? 8 : (t == QTT_BF16 ? 2 : 4);
 }
@@ -272,6 +282,7 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
         p.out = buf[k & 1];
         p.out_rhs_stride = (int64_t)p.rout * N;
         p.out_type = mid;
+        p.round_tf32_out = mode == LP_TF32;
       }
       cudaError_t e;
       if (compute == QTT_BF16 && use_tensor_cores() && A->mma_bf16 && A->mp[k] &&
@@ -291,6 +302,8 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
         m.N = N;
         m.nrhs = nc;
         e = launch_step_mma_bf16(m, st);
+      } else if (use_staged_f32() && f32s_step_eligible(p)) {
+        e = launch_step_f32s(p, st);
       } else {
         e = launch_step_lp(p, st);
       }

@@ -80,7 +80,9 @@ size_t request_bytes(const qtt_op *K, const qtt_op *P, int64_t nrhs, const qtt_s
   size_t b = 2 * N * R * 8;  // f, x
   if (p.kind == QTT_SOLVE_GMRES) b += (size_t)(p.restart + 3 + (P ? p.restart : 0)) * N * R * 8;
   else b += 4 * N * R * 8;
+  if (p.inner_iters > 0) b += 2 * N * R * 8;
   if (K) b += 2 * (size_t)K->rmax_inner * N * R * 8;
+  if (K && p.inner_iters > 0) b += 2 * (size_t)K->rmax_inner * N * R * 4;
   if (P) {
     const size_t e = p.precond_compute == QTT_F64 ? 8 : (p.precond_compute == QTT_BF16 ? 2 : 4);
     b += 2 * (size_t)P->rmax_inner * N * R * e;

@@ -132,6 +132,25 @@ qtt_status apply_K_lowp(const Ctx &c, const double *z, double *out, const double
   return apply_lp(c.K, c.pc, z, QTT_F64, out, QTT_F64, c.nrhs, c.N, c.st, e);
 }
 
+// z = M rhs, the correction operator: z0 = P rhs (P = I if absent), then
+// `inner` Richardson steps z <- z + P (rhs - (a z + K z)) with K and P in the
+// low precision c.pc and all vectors and updates in FP64.  tmp (and tmp2 when
+// there is no P) are N x nrhs work buffers; every buffer has leading dim N.
+qtt_status apply_M(const Ctx &c, int inner, const double *rhs, double *z, double *tmp,
+                   double *tmp2) {
+  QTT_TRY(apply_P(c, rhs, c.N, z, c.N, false));
+  for (int s = 0; s < inner; ++s) {
+    if (c.P) {
+      QTT_TRY(apply_K_lowp(c, z, tmp, rhs, -c.a));  // tmp = rhs - a z - K z
+      QTT_TRY(apply_P(c, tmp, c.N, z, c.N, true));  // z += P tmp
+    } else {
+      QTT_TRY(apply_K_lowp(c, z, tmp2, rhs, 1.0 - c.a));  // rhs + (1 - a) z - K z
+      QTT_CUDA_OK(vec_copy(vecs(z, c.N), vecs(tmp2, c.N), c.N, c.nrhs, c.st), "copy");
+    }
+  }
+  return QTT_OK;
+}
+
 // r = f - (a x + K x) (FP64, fused)
 qtt_status residual(const Ctx &c, const double *f, const double *x, int64_t ld, double *r) {
   Epilogue e;
@@ -173,7 +192,14 @@ qtt_status gmres(const Ctx &c, const double *f, double *x, int64_t ld, const qtt
   // Flexible GMRES: keep Z_j = P v_j, so that A Z = V H holds exactly for
   // the preconditioner as applied (a reduced-precision P is not exactly
   // linear), and update x with Z y.
-  if (c.P) QTT_TRY(S.get(&Z, (size_t)m * N * nr));
+  const int inner = prm.inner_iters;
+  const bool flex = c.P || inner > 0;  // z_j = M v_j differs from v_j
+  if (flex) QTT_TRY(S.get(&Z, (size_t)m * N * nr));
+  double *t1 = nullptr, *t2 = nullptr;
+  if (inner > 0) {
+    QTT_TRY(S.get(&t1, (size_t)N * nr));
+    QTT_TRY(S.get(&t2, (size_t)N * nr));
+  }
   QTT_TRY(S.get(&w, (size_t)N * nr));
   QTT_TRY(S.get(&z, (size_t)N * nr));
   QTT_TRY(S.get(&partial, (size_t)(m + 1) * nrc * blocks_for(N)));
@@ -220,8 +246,8 @@ qtt_status gmres(const Ctx &c, const double *f, double *x, int64_t ld, const qtt
     int jl = 0;
     for (int j = 0; j < m && iters < prm.max_iter; ++j) {
       double *Vj = V + (int64_t)j * vstride;
-      double *Zj = c.P ? Z + (int64_t)j * vstride : Vj;
-      if (c.P) QTT_TRY(apply_P(c, Vj, N, Zj, N, false));
+      double *Zj = flex ? Z + (int64_t)j * vstride : Vj;
+      if (flex) QTT_TRY(apply_M(c, inner, Vj, Zj, t1, t2));
       QTT_TRY(apply_A(c, Zj, w, N));
       const int nv = j + 1;
       QTT_CUDA_OK(vec_dots(vecs(V, N, vstride), nv, vecs(w, N), N, nr, partial, h1, nullptr, c.st),
@@ -284,7 +310,7 @@ qtt_status gmres(const Ctx &c, const double *f, double *x, int64_t ld, const qtt
     QTT_CUDA_OK(cudaMemcpyAsync(ydev, y.data(), sizeof(double) * jl * nr, cudaMemcpyHostToDevice,
                                 c.st), "memcpy");
     // x += Z y (Z = V without a preconditioner)
-    QTT_CUDA_OK(vec_combine(vecs(z, N), vecs(c.P ? Z : V, N, vstride), jl, ydev, N, nr, c.st),
+    QTT_CUDA_OK(vec_combine(vecs(z, N), vecs(flex ? Z : V, N, vstride), jl, ydev, N, nr, c.st),
                 "combine");
     QTT_CUDA_OK(vec_axpy(vecs(x, ld), vecs(z, N), 1.0, N, nr, c.st), "axpy");
   }
@@ -324,22 +350,8 @@ qtt_status refine(const Ctx &c, const double *f, double *x, int64_t ld,
     QTT_TRY(S.get(&zB, (size_t)N * nr));
     QTT_TRY(S.get(&w, (size_t)N * nr));
   }
-  // M(rhs) -> zA: `inner` Richardson steps on (a I + K) z = rhs, K (and P)
-  // in the low precision, vectors and updates in FP64, z0 = P rhs.
   auto correction = [&](const double *rhs) -> qtt_status {
-    QTT_TRY(apply_P(c, rhs, N, zA, N, false));
-    for (int s = 0; s < inner; ++s) {
-      if (c.P) {
-        // w = rhs - a zA - K zA ; zA += P w
-        QTT_TRY(apply_K_lowp(c, zA, w, rhs, -c.a));
-        QTT_TRY(apply_P(c, w, N, zA, N, true));
-      } else {
-        // zB = rhs + (1 - a) zA - K zA
-        QTT_TRY(apply_K_lowp(c, zA, zB, rhs, 1.0 - c.a));
-        std::swap(zA, zB);
-      }
-    }
-    return QTT_OK;
+    return apply_M(c, inner, rhs, zA, w, zB);
   };
   if (inner > 0) {
     QTT_TRY(correction(F));
@@ -442,7 +454,7 @@ extern "C" qtt_status qtt_solve(const qtt_op *K, const qtt_op *P, const double *
     return fail(QTT_ERR_INVALID_ARG, "qtt_solve: P lacks the packed copy for precond_compute");
   if (prm->inner_iters < 0 || prm->inner_iters > 1000)
     return fail(QTT_ERR_INVALID_ARG, "qtt_solve: inner_iters must be in [0, 1000]");
-  if (prm->kind == QTT_SOLVE_REFINE && prm->inner_iters > 0 && pc != QTT_F64 && !packed(K))
+  if (prm->kind != QTT_SOLVE_DIRECT && prm->inner_iters > 0 && pc != QTT_F64 && !packed(K))
     return fail(QTT_ERR_INVALID_ARG,
                 "qtt_solve: inner iterations need K packed for precond_compute");
   {

@@ -1,0 +1,195 @@
+// FP32 / TF32 core step on the FP32 pipe with staged inputs (intermediate to
+// intermediate steps with k >= 2).
+//
+// Same contraction as step_lp.cu, reorganised so that memory latency is
+// hidden: a persistent CTA keeps the packed core M_k in shared memory and
+// streams chunks of 128 position pairs through a three-deep cp.async ring
+// ([2a + j][pair] rows of 16-byte pieces; 4 consecutive pairs are 4
+// consecutive positions once k >= 2), while its eight warps multiply the
+// current chunk: warp w owns output ranks w*TB .. w*TB+TB-1 (TB = r_out/8
+// rounded up) for all 128 pairs (4 per lane), so each (a, j) costs 4 shared
+// loads of the input, TB broadcast loads of the core and 8 TB FMAs.
+// TF32 mode: the cores are packed TF32-rounded and the intermediates were
+// stored TF32-rounded by the previous step (rounding at the store instead of
+// at every use gives the same products), so no rounding happens here except
+// on the stored result.
+#include "qtt_internal.h"
+#include "step_lp.h"
+
+namespace qtt {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPC = 128;      // pairs per chunk
+constexpr int kStages = 3;
+constexpr int kMaxRankF32s = 48;
+
+__device__ __forceinline__ unsigned su32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cpa16(unsigned dst, const void *src, int n) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n));
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  unsigned u = __float_as_uint(x);
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0x0fffu + ((u >> 13) & 1u);
+    u &= 0xffffe000u;
+  }
+  return __uint_as_float(u);
+}
+
+__device__ __forceinline__ void load_chunk(const StepLP &s, float *sb, int64_t c, int64_t q0) {
+  const int rows = 2 * s.rin;
+  const int64_t bit = (int64_t)1 << s.k, low = bit - 1, npairs = s.N >> 1;
+  const float *in = static_cast<const float *>(s.in) + c * s.in_rhs_stride;
+  const int pc = threadIdx.x & 31;  // piece: pairs 4 pc .. 4 pc + 3
+  const int64_t q = q0 + 4 * pc;
+  const bool ok = q < npairs;
+  const float *base = in + (((q & ~low) << 1) | (q & low));
+  for (int kk = threadIdx.x >> 5; kk < rows; kk += kThreads / 32) {
+    const float *src = base + (int64_t)(kk >> 1) * s.N + ((kk & 1) ? bit : 0);
+    cpa16(su32(sb + kk * kPC + 4 * pc), ok ? src : s.in, ok ? 16 : 0);
+  }
+}
+
+template <int TB>
+__device__ __forceinline__ void chunk_block(const float *sb, const float *sG, const StepLP &s,
+                                            int b0, int lane, float *out, int64_t q0,
+                                            bool tf32) {
+  float acc[TB][2][4];
+#pragma unroll
+  for (int t = 0; t < TB; ++t)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc[t][i][m] = 0.0f;
+  const int rpad = s.rout_pad;
+  for (int kk = 0; kk < 2 * s.rin; ++kk) {
+    float v[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) v[m] = sb[kk * kPC + lane + 32 * m];
+    const float2 *g2 = reinterpret_cast<const float2 *>(sG + (kk * rpad + b0) * 2);
+#pragma unroll
+    for (int t = 0; t < TB; ++t) {
+      const float2 g = b0 + t < rpad ? g2[t] : make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        acc[t][0][m] = fmaf(g.x, v[m], acc[t][0][m]);
+        acc[t][1][m] = fmaf(g.y, v[m], acc[t][1][m]);
+      }
+    }
+  }
+  const int64_t bit = (int64_t)1 << s.k, low = bit - 1, npairs = s.N >> 1;
+#pragma unroll
+  for (int t = 0; t < TB; ++t) {
+    const int b = b0 + t;
+    if (b >= s.rout) break;
+    float *ob = out + (int64_t)b * s.N;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int64_t q = q0 + lane + 32 * m;
+      if (q >= npairs) continue;
+      const int64_t p0 = ((q & ~low) << 1) | (q & low);
+      ob[p0] = tf32 ? tf32_round(acc[t][0][m]) : acc[t][0][m];
+      ob[p0 + bit] = tf32 ? tf32_round(acc[t][1][m]) : acc[t][1][m];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) step_f32s_kernel(StepLP s) {
+  extern __shared__ __align__(16) float smf[];
+  const int rows = 2 * s.rin, rpad = s.rout_pad;
+  const int gfl = (rows * 2 * rpad + 3) / 4 * 4;  // core floats, 16-byte aligned end
+  float *sG = smf;
+  float *sB = smf + gfl;
+  const size_t stage = (size_t)rows * kPC;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool tf32 = s.mode == LP_TF32;
+  const float *G = static_cast<const float *>(s.M);
+  for (int e = tid; e < rows * 2 * rpad; e += kThreads) sG[e] = __ldg(G + e);
+
+  const int64_t npairs = s.N >> 1;
+  const int64_t cpr = (npairs + kPC - 1) / kPC;
+  const int64_t nchunks = cpr * s.nrhs;
+  const int64_t Gs = gridDim.x;
+#pragma unroll
+  for (int st = 0; st < kStages - 1; ++st) {
+    const int64_t t = blockIdx.x + st * Gs;
+    if (t < nchunks) load_chunk(s, sB + st * stage, t / cpr, (t % cpr) * kPC);
+    cpa_commit();
+  }
+  const int TB = (s.rout + 7) / 8;
+  const int b0 = warp * TB;
+  int cur = 0;
+  for (int64_t t = blockIdx.x; t < nchunks; t += Gs) {
+    {
+      const int64_t tn = t + (kStages - 1) * Gs;
+      if (tn < nchunks)
+        load_chunk(s, sB + ((cur + kStages - 1) % kStages) * stage, tn / cpr, (tn % cpr) * kPC);
+      cpa_commit();
+    }
+    cpa_wait<kStages - 1>();
+    __syncthreads();
+    const float *sb = sB + cur * stage;
+    const int64_t c = t / cpr, q0 = (t % cpr) * kPC;
+    float *out = static_cast<float *>(s.out) + c * s.out_rhs_stride;
+    if (b0 < s.rout) {
+      switch (TB) {
+        case 1: chunk_block<1>(sb, sG, s, b0, lane, out, q0, tf32); break;
+        case 2: chunk_block<2>(sb, sG, s, b0, lane, out, q0, tf32); break;
+        case 3: chunk_block<3>(sb, sG, s, b0, lane, out, q0, tf32); break;
+        case 4: chunk_block<4>(sb, sG, s, b0, lane, out, q0, tf32); break;
+        case 5: chunk_block<5>(sb, sG, s, b0, lane, out, q0, tf32); break;
+        case 6: chunk_block<6>(sb, sG, s, b0, lane, out, q0, tf32); break;
+        case 7: chunk_block<7>(sb, sG, s, b0, lane, out, q0, tf32); break;
+        default: chunk_block<8>(sb, sG, s, b0, lane, out, q0, tf32); break;
+      }
+    }
+    __syncthreads();  // the stage is refilled next iteration
+    cur = (cur + 1) % kStages;
+  }
+  cpa_wait<0>();
+}
+
+size_t f32s_smem(int rin, int rpad) {
+  const int rows = 2 * rin;
+  const size_t gfl = (size_t)(rows * 2 * rpad + 3) / 4 * 4;
+  return sizeof(float) * (gfl + (size_t)kStages * rows * kPC);
+}
+
+}  // namespace
+
+bool f32s_step_eligible(const StepLP &s) {
+  // ranks <= 48 keep the core plus three stages within one CTA's shared memory
+  return (s.mode == LP_F32 || s.mode == LP_TF32) && s.k >= 2 && s.in_type == QTT_F32 &&
+         s.out_type == QTT_F32 && !s.epi && s.rin <= kMaxRankF32s &&
+         s.rout <= kMaxRankF32s && s.rout >= 2 && (s.N >> 1) % 4 == 0;
+}
+
+cudaError_t launch_step_f32s(const StepLP &s, cudaStream_t st) {
+  // the kernel's shared-memory limit is raised once to the largest footprint
+  static cudaError_t attr = cudaFuncSetAttribute(
+      step_f32s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)f32s_smem(kMaxRankF32s, (kMaxRankF32s + 3) / 4 * 4));
+  if (attr != cudaSuccess) return attr;
+  const size_t smem = f32s_smem(s.rin, s.rout_pad);
+  int per_sm = 1, dev = 0, sms = 148;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_f32s_kernel, kThreads, smem);
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t nchunks = ((s.N >> 1) + kPC - 1) / kPC * s.nrhs;
+  int64_t grid = (int64_t)(per_sm < 1 ? 1 : per_sm) * sms;
+  if (grid > nchunks) grid = nchunks;
+  step_f32s_kernel<<<(unsigned)grid, kThreads, smem, st>>>(s);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace qtt

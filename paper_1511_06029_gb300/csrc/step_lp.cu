@@ -172,6 +172,8 @@ step_lp_kernel(StepLP s) {
         const int64_t p = p0[m] + (i ? bit : 0);
         if (s.epi)
           st_val(ob + p, epi_val(u, vv, p, s, acc[t][i][m]));
+        else if (MODE == LP_TF32 && s.round_tf32_out)
+          st_from_float(ob + p, tf32_rne(acc[t][i][m]));
         else
           st_from_float(ob + p, acc[t][i][m]);
       }

@@ -28,11 +28,19 @@ struct StepLP {
   const void *v;
   int64_t u_rhs_stride;  // also the stride of v
   double s_acc, s_u, s_v;
+  // TF32 mode: round the stored intermediate to TF32 (set for k < d-1), so
+  // that later steps may use it without rounding again.
+  int round_tf32_out;
 };
 
 // Rank padding of the packed reduced-precision cores (multiple of the
 // per-thread rank tile).
 int lp_rank_pad(int r);
 cudaError_t launch_step_lp(const StepLP &s, cudaStream_t st);
+
+// Staged (cp.async, persistent) FP32/TF32 step for intermediate-to-
+// intermediate steps with k >= 2 -- see step_f32s.cu.
+bool f32s_step_eligible(const StepLP &s);
+cudaError_t launch_step_f32s(const StepLP &s, cudaStream_t st);
 
 }  // namespace qtt

@@ -1,0 +1,94 @@
+"""Parity at the full workload sizes, in the configuration the benchmark
+times, on samples the oracle can afford:
+
+* mixed-precision refinement, d = 21, r_max = 48, ||K||_2 = 0.5: the true
+  residual of the GPU solution recomputed by the oracle's FP64 apply;
+  with cond(I + K) <= 3 a relative residual of 3e-11 bounds the error by 1e-10;
+* a d = 22 request through the solve server (GMRES(30), BF16 P, FP64
+  residual), its residual recomputed by the oracle;
+* the full batch of 256 uneven operators (FP32): whole outputs of the smallest
+  operators and one right-hand side of a d = 20 operator against the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_06029_gb300 import inputs
+from conftest import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qtt():
+    from paper_1511_06029_gb300 import build, qtt as q
+    build.build()
+    q.load_library()
+    return q
+
+
+def _true_residual(K, f, x):
+    return np.linalg.norm(f - (x + oracle.apply(K, x))) / np.linalg.norm(f)
+
+
+def test_refinement_full_size(qtt):
+    import torch
+    K = inputs.scaled_operator(21, 48, 3)
+    f = inputs.gaussian_rhs(K.N, 1, 4)
+    Kg = qtt.Operator(K, packs=("bf16",))
+    x, info = qtt.solve(Kg, None, torch.from_numpy(f).cuda(), kind="refine", tol=3e-11,
+                        max_iter=60, precond_compute="bf16", inner_iters=6)
+    Kg.close()
+    x = x.cpu().numpy()[0]
+    assert info[0][2] == qtt.QTT_OK
+    res = _true_residual(K, f[0], x)
+    assert res <= 3.1e-11, res
+    assert abs(res - info[0][1]) <= 1e-3 * res + 1e-14  # the GPU's own residual agrees
+
+
+def test_serving_request_full_size(qtt):
+    K = inputs.scaled_operator(22, 32, 5022)
+    P = inputs.neumann_preconditioner(K, 1e-4)
+    f = inputs.gaussian_rhs(K.N, 1, 6)
+    Kg, Pg = qtt.Operator(K), qtt.Operator(P, packs=("bf16",))
+    S = qtt.Server(slots=2, kind="gmres", tol=3e-11, precond_compute="bf16")
+    x, info, _ = S.wait(S.submit(Kg, Pg, f))
+    S.close()
+    Kg.close(), Pg.close()
+    assert info[0][2] == qtt.QTT_OK
+    assert _true_residual(K, f[0], x[0]) <= 3.1e-11
+
+
+def test_batched_full_size_samples(qtt):
+    import torch
+    items = inputs.batched_workload()
+    datas, ops, xs, ys = [], [], [], []
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4)
+    for it in items:
+        data = inputs.synthetic_operator(it["d"], it["rmax"], it["op_seed"])
+        datas.append(data)
+        ops.append(qtt.Operator(data, packs=("f32",)))
+        x = torch.randn(it["nrhs"], data.N, device="cuda", dtype=torch.float32, generator=gen)
+        xs.append(x)
+        ys.append(torch.full_like(x, float("nan")))
+    B = qtt.Batch(ops, xs, ys, compute="f32")
+    B.run()
+    B.status()
+    torch.cuda.synchronize()
+    order = sorted(range(len(items)), key=lambda i: items[i]["d"] * 64 + items[i]["nrhs"])
+    samples = [(i, None) for i in order[:4]]
+    big = max(range(len(items)), key=lambda i: (items[i]["d"], items[i]["rmax"]))
+    samples.append((big, 0))
+    for i, c in samples:
+        x = xs[i].double().cpu().numpy()
+        y = ys[i].double().cpu().numpy()
+        if c is not None:
+            x, y = x[c:c + 1], y[c:c + 1]
+        ref = oracle.apply(datas[i], x)
+        assert rel_l2(y, ref) <= 4 * math.sqrt(datas[i].d) * 2.0 ** -24, (i, items[i])
+    B.close()
+    for o in ops:
+        o.close()
