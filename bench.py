@@ -86,6 +86,8 @@ WORKLOADS = {
                           compute="f32"),
     "apply_tf32_d24": dict(kind="apply", d=24, rmax=32, seed=2, rhs_seed=3, nrhs=1,
                            compute="tf32"),
+    "apply_f32_d22": dict(kind="apply", d=22, rmax=32, seed=2, rhs_seed=3, nrhs=1,
+                          compute="f32"),
     "apply_bf16_d24": dict(kind="apply", d=24, rmax=32, seed=2, rhs_seed=3, nrhs=1,
                            compute="bf16"),
     "apply_bf16_d21": dict(kind="apply", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=64,
@@ -110,7 +112,7 @@ WORKLOADS = {
                         probe=[("bf16", 0), ("bf16", 1), ("f32", 0), ("f32", 1), ("tf32", 1)]),
     "serve_small": dict(kind="serve", d_range=(14, 18), rhs_range=(1, 16), rmax=32,
                         seed_base=5000, eps=1e-4, seed=5, count=40, slots=6, tol=1e-10,
-                        plain_count=40),
+                        plain_count=40, pc="bf16", inner=1),
     "refine_bf16_d21": dict(kind="refine", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=64,
                             pc="bf16", inner=6),
     "refine_f64_d21": dict(kind="refine", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=64,

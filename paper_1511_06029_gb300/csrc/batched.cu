@@ -21,10 +21,10 @@
 // is waited for after the current item is published -- never before, which
 // keeps the no-deadlock argument above).  The core of the current (operator,
 // step) sits in shared memory while consecutive items share it.  Each warp
-// computes a block of TB output ranks for the 32*TN pairs with FP32
-// multiply-adds (TF32 mode rounds each staged operand to TF32; cores are
-// packed TF32-rounded).  TB = ceil(r_out/8), so the eight warps cover all
-// output ranks in one pass.
+// computes a block of TB output ranks for the 32*TN pairs (TN consecutive
+// pairs per lane) with FP32 multiply-adds (TF32 mode rounds each staged
+// operand to TF32; cores are packed TF32-rounded).  TB = 2 ceil(r_out/16), so
+// the eight warps cover all output ranks in one pass.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -99,6 +99,21 @@ struct Item {
   int seg;
 };
 
+// Lane `lane` owns the TN consecutive pairs TN lane .. TN lane + TN - 1 of
+// the item (one vector shared load per (a, j)); the warp owns output ranks
+// b0 .. b0 + TB - 1 (TB even), read two at a time as one 16-byte broadcast
+// load ((b, i=0), (b, i=1), (b+1, i=0), (b+1, i=1)).
+template <int TN>
+__device__ __forceinline__ void load_v(const float *p, float (&v)[TN]) {
+  if constexpr (TN == 4) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    const float2 t = *reinterpret_cast<const float2 *>(p);
+    v[0] = t.x; v[1] = t.y;
+  }
+}
+
 template <int TB, int TN>
 __device__ __forceinline__ void rank_block(const float *sm, const float *sG, int rin, int rpad,
                                            int b0, int rout, int lane, int npair_chunk,
@@ -111,38 +126,58 @@ __device__ __forceinline__ void rank_block(const float *sm, const float *sG, int
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int m = 0; m < TN; ++m) acc[t][i][m] = 0.0f;
-  for (int a = 0; a < rin; ++a) {
+  for (int kk = 0; kk < 2 * rin; ++kk) {
+    float v[TN];
+    load_v<TN>(sm + (size_t)kk * npair_chunk + TN * lane, v);
+    const float4 *g4 = reinterpret_cast<const float4 *>(sG + (kk * rpad + b0) * 2);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const float *srow = sm + (size_t)(2 * a + j) * npair_chunk;
-      float v[TN];
+    for (int t2 = 0; t2 < TB / 2; ++t2) {
+      // ranks past the padded row contribute nothing (rpad is a multiple of 4)
+      const float4 g = b0 + 2 * t2 < rpad ? g4[t2] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float gg[4] = {g.x, g.y, g.z, g.w};
 #pragma unroll
-      for (int m = 0; m < TN; ++m) v[m] = srow[lane + 32 * m];
-      // core row (a, j) in shared memory; ranks past the padded row read 0
-      const float2 *g2 = reinterpret_cast<const float2 *>(sG + ((2 * a + j) * rpad + b0) * 2);
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int t = 0; t < TB; ++t) {
-        const float2 g = b0 + t < rpad ? g2[t] : make_float2(0.0f, 0.0f);
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int m = 0; m < TN; ++m) {
-          acc[t][0][m] = fmaf(g.x, v[m], acc[t][0][m]);
-          acc[t][1][m] = fmaf(g.y, v[m], acc[t][1][m]);
-        }
-      }
+          for (int m = 0; m < TN; ++m)
+            acc[2 * t2 + h][i][m] = fmaf(gg[2 * h + i], v[m], acc[2 * t2 + h][i][m]);
     }
   }
   const int64_t bit = (int64_t)1 << k, low = bit - 1;
+  const int64_t qb = q0 + TN * lane;
 #pragma unroll
   for (int t = 0; t < TB; ++t) {
     const int b = b0 + t;
     if (b >= rout) break;
+    float *ob = out + (int64_t)b * N;
+    // TN consecutive pairs are TN consecutive positions once 2^k >= 4; the
+    // vector store also needs an aligned row (the caller's y may have any ld)
+    const int64_t pv = ((qb & ~low) << 1) | (qb & low);
+    const bool vec = k >= 2 && qb < npairs &&
+                     ((reinterpret_cast<uintptr_t>(ob + pv) |
+                       reinterpret_cast<uintptr_t>(ob + pv + bit)) &
+                      (sizeof(float) * TN - 1)) == 0;
+    if (vec) {
+      const int64_t p0 = pv;
 #pragma unroll
-    for (int m = 0; m < TN; ++m) {
-      const int64_t q = q0 + lane + 32 * m;
-      if (q >= npairs) continue;
-      const int64_t p0 = ((q & ~low) << 1) | (q & low);
-      out[(int64_t)b * N + p0] = acc[t][0][m];
-      out[(int64_t)b * N + p0 + bit] = acc[t][1][m];
+      for (int i = 0; i < 2; ++i) {
+        float *o = ob + p0 + (i ? bit : 0);
+        if constexpr (TN == 4)
+          *reinterpret_cast<float4 *>(o) =
+              make_float4(acc[t][i][0], acc[t][i][1], acc[t][i][2], acc[t][i][3]);
+        else
+          *reinterpret_cast<float2 *>(o) = make_float2(acc[t][i][0], acc[t][i][1]);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < TN; ++m) {
+        const int64_t q = qb + m;
+        if (q >= npairs) continue;
+        const int64_t p0 = ((q & ~low) << 1) | (q & low);
+        ob[p0] = acc[t][0][m];
+        ob[p0 + bit] = acc[t][1][m];
+      }
     }
   }
 }
@@ -354,23 +389,16 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(BWave w) {
     const int64_t q0 = (tile % sg.tiles_per_rhs) * PC;
     float *out = k == op.d - 1 ? op.y + c * op.ld
                                : (k & 1 ? op.buf1 : op.buf0) + c * (int64_t)rout * N;
-    const int TB = (rout + 7) / 8;
+    const int TB = 2 * ((rout + 15) / 16);  // even; 8 warps x TB >= r_out
     const int b0 = warp * TB;
     if (b0 < rout) {
-      switch (TB > TBMAX ? TBMAX : TB) {
-        case 1: rank_block<1, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+      switch (TB) {
         case 2: rank_block<2, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-        case 3: rank_block<3, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
         case 4: rank_block<4, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-        case 5: rank_block<5, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
+        case 6: rank_block<6, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
         default:
-          if constexpr (TBMAX > 5) {
-            switch (TB) {
-              case 6: rank_block<6, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-              case 7: rank_block<7, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-              default: rank_block<8, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-            }
-          }
+          if constexpr (TBMAX > 6)
+            rank_block<8, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs);
           break;
       }
     }
@@ -596,10 +624,10 @@ qtt_status launch_waves(qtt_batch *B, cudaStream_t st) {
   // register footprint follows the largest rank block a wave needs
   int max_r = 1;
   for (auto &w : B->waves) max_r = std::max(max_r, w.max_rin);
-  const bool small = max_r <= 40;  // TB = ceil(r/8) <= 5
+  const bool small = max_r <= 48;  // TB = 2 ceil(r/16) <= 6
   switch (B->variant) {
-    case 2: return small ? launch_waves_t<2, 5>(B, st) : launch_waves_t<2, 8>(B, st);
-    default: return small ? launch_waves_t<4, 5>(B, st) : launch_waves_t<4, 8>(B, st);
+    case 2: return small ? launch_waves_t<2, 6>(B, st) : launch_waves_t<2, 8>(B, st);
+    default: return small ? launch_waves_t<4, 6>(B, st) : launch_waves_t<4, 8>(B, st);
   }
 }
 

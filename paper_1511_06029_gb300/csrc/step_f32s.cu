@@ -6,9 +6,10 @@
 // streams chunks of 128 position pairs through a three-deep cp.async ring
 // ([2a + j][pair] rows of 16-byte pieces; 4 consecutive pairs are 4
 // consecutive positions once k >= 2), while its eight warps multiply the
-// current chunk: warp w owns output ranks w*TB .. w*TB+TB-1 (TB = r_out/8
-// rounded up) for all 128 pairs (4 per lane), so each (a, j) costs 4 shared
-// loads of the input, TB broadcast loads of the core and 8 TB FMAs.
+// current chunk: warp w owns output ranks w*TB .. w*TB+TB-1 (TB = 2 ceil(r_out
+// / 16)) for all 128 pairs (4 consecutive per lane), so each (a, j) costs one
+// 16-byte shared load of the input, TB/2 16-byte broadcast loads of the core
+// and 8 TB FMAs.
 // TF32 mode: the cores are packed TF32-rounded and the intermediates were
 // stored TF32-rounded by the previous step (rounding at the store instead of
 // at every use gives the same products), so no rounding happens here except
@@ -59,6 +60,11 @@ __device__ __forceinline__ void load_chunk(const StepLP &s, float *sb, int64_t c
   }
 }
 
+// Lane `lane` owns the 4 consecutive pairs 4 lane .. 4 lane + 3 of the chunk
+// (one 16-byte shared load per (a, j)); the warp owns output ranks b0 ..
+// b0 + TB - 1 (TB even), read two at a time as one 16-byte broadcast load
+// ((b, i=0), (b, i=1), (b+1, i=0), (b+1, i=1)).  Per (a, j): 1 + TB/2 loads
+// for 8 TB FMAs.  Results leave as 16-byte stores (4 consecutive positions).
 template <int TB>
 __device__ __forceinline__ void chunk_block(const float *sb, const float *sG, const StepLP &s,
                                             int b0, int lane, float *out, int64_t q0,
@@ -72,33 +78,45 @@ __device__ __forceinline__ void chunk_block(const float *sb, const float *sG, co
       for (int m = 0; m < 4; ++m) acc[t][i][m] = 0.0f;
   const int rpad = s.rout_pad;
   for (int kk = 0; kk < 2 * s.rin; ++kk) {
-    float v[4];
+    const float4 v = *reinterpret_cast<const float4 *>(sb + kk * kPC + 4 * lane);
+    const float4 *g4 = reinterpret_cast<const float4 *>(sG + (kk * rpad + b0) * 2);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) v[m] = sb[kk * kPC + lane + 32 * m];
-    const float2 *g2 = reinterpret_cast<const float2 *>(sG + (kk * rpad + b0) * 2);
+    for (int t2 = 0; t2 < TB / 2; ++t2) {
+      // ranks past the padded row contribute nothing (rpad is a multiple of 4)
+      const float4 g = b0 + 2 * t2 < rpad ? g4[t2] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float gg[4] = {g.x, g.y, g.z, g.w};
 #pragma unroll
-    for (int t = 0; t < TB; ++t) {
-      const float2 g = b0 + t < rpad ? g2[t] : make_float2(0.0f, 0.0f);
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        acc[t][0][m] = fmaf(g.x, v[m], acc[t][0][m]);
-        acc[t][1][m] = fmaf(g.y, v[m], acc[t][1][m]);
-      }
+        for (int i = 0; i < 2; ++i) {
+          float *a = acc[2 * t2 + h][i];
+          const float c = gg[2 * h + i];
+          a[0] = fmaf(c, v.x, a[0]);
+          a[1] = fmaf(c, v.y, a[1]);
+          a[2] = fmaf(c, v.z, a[2]);
+          a[3] = fmaf(c, v.w, a[3]);
+        }
     }
   }
   const int64_t bit = (int64_t)1 << s.k, low = bit - 1, npairs = s.N >> 1;
+  const int64_t q = q0 + 4 * lane;
+  if (q >= npairs) return;
+  const int64_t p0 = ((q & ~low) << 1) | (q & low);
 #pragma unroll
   for (int t = 0; t < TB; ++t) {
     const int b = b0 + t;
     if (b >= s.rout) break;
-    float *ob = out + (int64_t)b * s.N;
+    float *ob = out + (int64_t)b * s.N + p0;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int64_t q = q0 + lane + 32 * m;
-      if (q >= npairs) continue;
-      const int64_t p0 = ((q & ~low) << 1) | (q & low);
-      ob[p0] = tf32 ? tf32_round(acc[t][0][m]) : acc[t][0][m];
-      ob[p0 + bit] = tf32 ? tf32_round(acc[t][1][m]) : acc[t][1][m];
+    for (int i = 0; i < 2; ++i) {
+      float4 o = make_float4(acc[t][i][0], acc[t][i][1], acc[t][i][2], acc[t][i][3]);
+      if (tf32) {
+        o.x = tf32_round(o.x);
+        o.y = tf32_round(o.y);
+        o.z = tf32_round(o.z);
+        o.w = tf32_round(o.w);
+      }
+      *reinterpret_cast<float4 *>(ob + (i ? bit : 0)) = o;
     }
   }
 }
@@ -125,7 +143,7 @@ __global__ void __launch_bounds__(kThreads) step_f32s_kernel(StepLP s) {
     if (t < nchunks) load_chunk(s, sB + st * stage, t / cpr, (t % cpr) * kPC);
     cpa_commit();
   }
-  const int TB = (s.rout + 7) / 8;
+  const int TB = 2 * ((s.rout + 15) / 16);  // even; 8 warps x TB >= r_out
   const int b0 = warp * TB;
   int cur = 0;
   for (int64_t t = blockIdx.x; t < nchunks; t += Gs) {
@@ -142,14 +160,9 @@ __global__ void __launch_bounds__(kThreads) step_f32s_kernel(StepLP s) {
     float *out = static_cast<float *>(s.out) + c * s.out_rhs_stride;
     if (b0 < s.rout) {
       switch (TB) {
-        case 1: chunk_block<1>(sb, sG, s, b0, lane, out, q0, tf32); break;
         case 2: chunk_block<2>(sb, sG, s, b0, lane, out, q0, tf32); break;
-        case 3: chunk_block<3>(sb, sG, s, b0, lane, out, q0, tf32); break;
         case 4: chunk_block<4>(sb, sG, s, b0, lane, out, q0, tf32); break;
-        case 5: chunk_block<5>(sb, sG, s, b0, lane, out, q0, tf32); break;
-        case 6: chunk_block<6>(sb, sG, s, b0, lane, out, q0, tf32); break;
-        case 7: chunk_block<7>(sb, sG, s, b0, lane, out, q0, tf32); break;
-        default: chunk_block<8>(sb, sG, s, b0, lane, out, q0, tf32); break;
+        default: chunk_block<6>(sb, sG, s, b0, lane, out, q0, tf32); break;
       }
     }
     __syncthreads();  // the stage is refilled next iteration

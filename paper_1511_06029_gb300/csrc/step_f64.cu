@@ -26,13 +26,16 @@ constexpr int kWarpsY = 8;   // output ranks per CTA (one per warp)
 template <int TN>
 __global__ void __launch_bounds__(32 * kWarpsY)
 step_f64_kernel(StepF64 s) {
-  const int b = blockIdx.y * blockDim.y + threadIdx.y;
+  // blockIdx.x = pair tile * rank blocks + rank block: the CTAs that share a
+  // pair tile (and so its input) run back to back and meet it in L2
+  const int nrb = (s.rout + blockDim.y - 1) / blockDim.y;
+  const int b = (int)(blockIdx.x % nrb) * blockDim.y + threadIdx.y;
   if (b >= s.rout) return;
   const int64_t c = blockIdx.z;
   const int64_t npairs = s.N >> 1;
   const int64_t bit = (int64_t)1 << s.k;
   const int64_t low = bit - 1;
-  const int64_t q0 = (int64_t)blockIdx.x * (32 * TN) + threadIdx.x;
+  const int64_t q0 = (int64_t)(blockIdx.x / nrb) * (32 * TN) + threadIdx.x;
 
   int64_t p0[TN];
   bool ok[TN];
@@ -104,7 +107,8 @@ cudaError_t launch_step_f64(const StepF64 &s, cudaStream_t stream) {
     t.out += c0 * s.out_rhs_stride;
     if (t.u) t.u += c0 * s.uv_rhs_stride;
     if (t.v) t.v += c0 * s.uv_rhs_stride;
-    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)nc);
+    if (gx * gy > 0x7fffffffLL) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)(gx * gy), 1, (unsigned)nc);
     step_f64_kernel<kTN><<<grid, block, 0, stream>>>(t);
     count_launches(1);
     cudaError_t e = cudaGetLastError();

@@ -108,14 +108,17 @@ __device__ __forceinline__ void ld_core8(const __nv_bfloat16 *g, float (&o)[8]) 
 template <int MODE, typename TIN, typename TOUT, typename TCORE>
 __global__ void __launch_bounds__(32 * kWarpsY)
 step_lp_kernel(StepLP s) {
-  const int bb = blockIdx.y * blockDim.y + threadIdx.y;  // rank block
+  // blockIdx.x = pair tile * rank-block groups + group (adjacent CTAs share
+  // the input tile through L2)
+  const int ngrp = ((s.rout + kTB - 1) / kTB + blockDim.y - 1) / blockDim.y;
+  const int bb = (int)(blockIdx.x % ngrp) * blockDim.y + threadIdx.y;  // rank block
   const int b0 = bb * kTB;
   if (b0 >= s.rout) return;
   const int64_t c = blockIdx.z;
   const int64_t npairs = s.N >> 1;
   const int64_t bit = (int64_t)1 << s.k;
   const int64_t low = bit - 1;
-  const int64_t q0 = (int64_t)blockIdx.x * (32 * kTN) + threadIdx.x;
+  const int64_t q0 = (int64_t)(blockIdx.x / ngrp) * (32 * kTN) + threadIdx.x;
   int64_t p0[kTN];
   bool ok[kTN];
 #pragma unroll
@@ -196,7 +199,7 @@ cudaError_t launch_t(const StepLP &s, cudaStream_t st) {
     if (t.u) t.u = static_cast<const TOUT *>(s.u) + c0 * s.u_rhs_stride;
     if (t.v) t.v = static_cast<const TOUT *>(s.v) + c0 * s.u_rhs_stride;
     step_lp_kernel<MODE, TIN, TOUT, TCORE>
-        <<<dim3((unsigned)gx, (unsigned)gy, (unsigned)nc), dim3(32, by), 0, st>>>(t);
+        <<<dim3((unsigned)(gx * gy), 1, (unsigned)nc), dim3(32, by), 0, st>>>(t);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -99,3 +99,32 @@ def test_batch_rejects_bad_input(qtt):
         qtt.Batch([op64], [x], [y], compute="bf16")
     assert e.value.status == qtt.QTT_ERR_UNSUPPORTED
     op64.close()
+
+
+def test_batch_odd_leading_dimension(qtt):
+    """Outputs with a leading dimension that is not a multiple of 4 (vector
+    stores must fall back to scalar ones)."""
+    import torch
+    items = _batch(4, 13, d_range=(6, 9), r_range=(8, 20), rhs_range=(2, 3))
+    datas, ops, xs, ys = [], [], [], []
+    for it in items:
+        data = inputs.synthetic_operator(it["d"], it["rmax"], it["op_seed"])
+        N = data.N
+        datas.append(data)
+        ops.append(qtt.Operator(data, packs=("f32",)))
+        x = torch.from_numpy(inputs.gaussian_rhs(N, it["nrhs"], it["rhs_seed"]).astype(np.float32))
+        xbig = torch.zeros((it["nrhs"], N + 3), dtype=torch.float32, device="cuda")
+        xbig[:, 1:N + 1] = x.cuda()
+        xs.append(xbig[:, 1:N + 1])  # ld = N + 3, rows start at odd offsets
+        big = torch.full((it["nrhs"], N + 3), float("nan"), dtype=torch.float32, device="cuda")
+        ys.append(big[:, 1:N + 1])
+    B = qtt.Batch(ops, xs, ys, compute="f32")
+    B.run()
+    B.status()
+    torch.cuda.synchronize()
+    for data, x, y in zip(datas, xs, ys):
+        err = rel_l2(y.double().cpu().numpy(), oracle.apply(data, x.double().cpu().numpy()))
+        assert err <= 4 * math.sqrt(data.d) * U["f32"]
+    B.close()
+    for o in ops:
+        o.close()
