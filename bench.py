@@ -424,7 +424,7 @@ class BatchedRun:
 
     def roofline(self, mean_s):
         achieved = self.flops / mean_s / 1e9
-        r = {"bound": "alu", "kernel": f"batch_kernel<{self.variant}>", "achieved": achieved,
+        r = {"bound": "alu", "kernel": f"batch_kernel<{self.variant % 100}>", "achieved": achieved,
              "peak": FP32_NOMINAL_GFLOPS, "unit": "GFLOP/s",
              "frac": achieved / FP32_NOMINAL_GFLOPS, "traffic": None,
              "peak_source": "FP32 pipe, 152 SMs x 128 FMA/clk x 2.07 GHz"}
@@ -440,7 +440,8 @@ class BatchedRun:
                 "total_rhs": sum(it["nrhs"] for it in self.items),
                 "flops_per_step_per_gpu": self.flops, "compute": self.compute,
                 "waves": self.info["waves"], "grid": self.info["grid"],
-                "autotuned_variant_pairs_per_lane": self.variant,
+                "autotuned_pairs_per_lane": self.variant % 100,
+                "autotuned_chunks_per_item": self.variant // 100,
                 "scratch_gb": self.info["scratch_bytes"] / 1e9,
                 "graph": "all waves captured in one CUDA graph",
                 "l2": "not flushed: each step streams tens of GB of intermediates"}

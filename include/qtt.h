@@ -219,7 +219,7 @@ qtt_status qtt_solve(const qtt_op *K, const qtt_op *P, const double *f,
  *   compute     : QTT_F32 or QTT_TF32 (operands rounded to TF32, FP32
  *                 accumulate); each operator needs the matching QTT_PACK_*.
  *   mem_budget  : bytes of intermediate per wave (0 = min(free/3, 64 GiB)).
- * Ranks above 64 return QTT_ERR_UNSUPPORTED. */
+ * Ranks above 48 return QTT_ERR_UNSUPPORTED. */
 typedef struct qtt_batch qtt_batch;
 qtt_status qtt_batch_create(qtt_batch **out, int nops, const qtt_op *const *ops,
                             const int64_t *nrhs, const void *const *x,
@@ -231,8 +231,9 @@ qtt_status qtt_batch_run(qtt_batch *B, void *stream);
 /* Synchronise `stream`; QTT_ERR_TIMEOUT if a dependency wait in the last
  * runs gave up (the status word is then cleared). */
 qtt_status qtt_batch_status(qtt_batch *B, void *stream);
-/* Tile variant: 2 or 4 position-pair columns per lane (64 or 128 pairs per
- * work item); re-plans and re-captures. */
+/* Tile variant = pairs per lane (2 or 4: chunks of 64 or 128 position pairs,
+ * wider for small ranks) + 100 x chunks per work item (1..64; a bare 2 or 4
+ * means 8); re-plans and re-captures. */
 qtt_status qtt_batch_set_variant(qtt_batch *B, int variant, void *stream);
 /* Time every variant (`reps` runs each, after one warm-up) and keep the
  * fastest; reports it and its seconds per run. */

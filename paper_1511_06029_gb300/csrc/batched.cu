@@ -37,7 +37,7 @@ namespace qtt {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kMaxRank = 64;
+constexpr int kMaxRank = 48;  // core + 3 chunk stages fit one CTA
 constexpr int kMaxD = 30;
 
 struct BOp {
@@ -52,9 +52,15 @@ struct BOp {
   int64_t coff[kMaxD + 1];
 };
 
+// One (operator, step) of a wave.  Its chunks (32*TN position pairs of one
+// right-hand side) are grouped into slices of `slice` chunks; slices are the
+// work items.  first = index of its first slice, ntiles = number of slices.
 struct BSeg {
   int op, k, dep;
-  int64_t first, ntiles, tiles_per_rhs;
+  int64_t first, ntiles;
+  int64_t chunks_per_rhs, nchunks;
+  int slice;
+  int pc;  // pairs per chunk: 32*TN times as many groups as the stage holds
 };
 
 struct BWave {
@@ -91,7 +97,11 @@ __device__ __forceinline__ void cp_async16b(unsigned dst, const void *src, int n
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
-__device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait_n() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+constexpr int kStagesB = 3;  // chunks in flight per CTA within a slice
 
 // One work item, decoded.
 struct Item {
@@ -118,7 +128,8 @@ template <int TB, int TN>
 __device__ __forceinline__ void rank_block(const float *sm, const float *sG, int rin, int rpad,
                                            int b0, int rout, int lane, int npair_chunk,
                                            float *out, int64_t N, int64_t q0, int k,
-                                           int64_t npairs) {
+                                           int64_t npairs, bool round_out) {
+
   float acc[TB][2][TN];
 #pragma unroll
   for (int t = 0; t < TB; ++t)
@@ -143,6 +154,14 @@ __device__ __forceinline__ void rank_block(const float *sm, const float *sG, int
           for (int m = 0; m < TN; ++m)
             acc[2 * t2 + h][i][m] = fmaf(gg[2 * h + i], v[m], acc[2 * t2 + h][i][m]);
     }
+  }
+  if (round_out) {
+#pragma unroll
+    for (int t = 0; t < TB; ++t)
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int m = 0; m < TN; ++m) acc[t][i][m] = tf32_rne_b(acc[t][i][m]);
   }
   const int64_t bit = (int64_t)1 << k, low = bit - 1;
   const int64_t qb = q0 + TN * lane;
@@ -200,62 +219,17 @@ __device__ __forceinline__ int find_seg(const BWave &w, long long item) {
   return lo;
 }
 
-// Items are taken in blocks of kGrab consecutive indices (one atomic per
-// block) and processed in index order, so the smallest unprocessed item is
-// always at the head of some running CTA's block and every dependency wait
-// ends.  Within a block the segment advances incrementally and the
-// dependency is re-checked only when the segment changes (done counters only
-// grow, so a satisfied dependency stays satisfied).
-constexpr int kGrab = 8;
-
-struct Fetch {
-  long long cur, end;  // remaining block [cur, end)
-  int seg;             // segment of the last item handed out (-1: none)
-};
-
-// Take the next item (warp 0) and check, without waiting, whether its
-// operator's previous step is complete.  Broadcast through shared memory.
-__device__ __forceinline__ void fetch_item(const BWave &w, Fetch *f, Item *s_item, int *s_ready) {
+// Take the next slice (warp 0); -> s_item (idx >= w.total: none left).
+__device__ __forceinline__ void fetch_slice(const BWave &w, Item *s_item) {
   if (threadIdx.x < 32) {
     long long idx = 0;
-    int need_search = 0;
-    if (threadIdx.x == 0) {
-      if (f->cur >= f->end) {
-        const long long b = (long long)atomicAdd(w.next, (unsigned long long)kGrab);
-        f->cur = b;
-        f->end = b + kGrab < w.total ? b + kGrab : w.total;
-        need_search = 1;
-      }
-      if (f->seg < 0) need_search = 1;
-      idx = f->cur < f->end ? f->cur++ : w.total;
-    }
+    if (threadIdx.x == 0) idx = (long long)atomicAdd(w.next, 1ull);
     idx = __shfl_sync(0xffffffffu, idx, 0);
-    need_search = __shfl_sync(0xffffffffu, need_search, 0);
     int seg = 0;
-    if (idx < w.total) {
-      if (need_search) {
-        seg = find_seg(w, idx);
-      } else if (threadIdx.x == 0) {
-        seg = f->seg;
-        while (seg + 1 < w.nseg && w.segs[seg + 1].first <= idx) ++seg;
-      }
-    }
+    if (idx < w.total) seg = find_seg(w, idx);
     if (threadIdx.x == 0) {
-      int ready = 0;
-      if (idx < w.total) {
-        if (seg == f->seg) {
-          ready = 1;
-        } else {
-          const int dep = w.segs[seg].dep;
-          ready = dep < 0 ||
-                  *(volatile unsigned *)(w.done + dep) >= (unsigned)w.segs[dep].ntiles;
-          if (ready) __threadfence();
-        }
-      }
-      f->seg = ready ? seg : -1;  // only a dependency seen complete is remembered
       s_item->idx = idx;
       s_item->seg = seg;
-      *s_ready = ready;
     }
   }
 }
@@ -284,24 +258,19 @@ __device__ __forceinline__ void wait_item(const BWave &w, const Item &it, int *s
   }
 }
 
-// Issue the asynchronous copies of an item's input chunk into `buf`
-// ([2a + j][pair], PC pairs per row).  16-byte copies when 4 consecutive
+// Issue the asynchronous copies of chunk (c, q0) of step k into `buf`
+// ([2a + j][pair], PC pairs per row): 16-byte copies when 4 consecutive
 // pairs are 4 consecutive positions (k >= 2), 4-byte copies otherwise;
 // pairs past the end are zero-filled.
-template <int PC>
-__device__ __forceinline__ void stage_item(const BWave &w, const Item &it, float *buf) {
-  const BSeg &sg = w.segs[it.seg];
-  const BOp &op = w.ops[sg.op];
-  const int k = sg.k, rin = op.ranks[k];
+__device__ __forceinline__ void stage_chunk(const BOp &op, int k, int64_t c, int64_t q0,
+                                            int PC, float *buf) {
+  const int rin = op.ranks[k];
   const int64_t N = op.N, npairs = N >> 1;
-  const int64_t tile = it.idx - sg.first;
-  const int64_t c = tile / sg.tiles_per_rhs;
-  const int64_t q0 = (tile % sg.tiles_per_rhs) * PC;
   const int64_t bit = (int64_t)1 << k, low = bit - 1;
   const float *in = k == 0 ? op.x + c * op.ld
                            : ((k - 1) & 1 ? op.buf1 : op.buf0) + c * (int64_t)rin * N;
   if (k >= 2) {
-    constexpr int PIECES = PC / 4;
+    const int PIECES = PC / 4;
     for (int e = threadIdx.x; e < 2 * rin * PIECES; e += kThreads) {
       const int kk = e / PIECES, pc = e % PIECES;
       const int64_t q = q0 + 4 * pc;
@@ -322,104 +291,103 @@ __device__ __forceinline__ void stage_item(const BWave &w, const Item &it, float
   }
 }
 
+// The chunk's work units are (rank block of TB ranks, group of 32*TN pairs);
+// warps take them round robin, so small output ranks (few rank blocks) still
+// keep every warp busy on a wider chunk.
+template <int TN, int TBMAX>
+__device__ __forceinline__ void compute_chunk(const float *sb, const float *sG, int rin,
+                                              int rpad, int rout, int warp, int lane, int PCe,
+                                              float *out, int64_t N, int64_t q0, int k,
+                                              int64_t npairs, bool round_out) {
+  constexpr int GP = 32 * TN;  // pairs per group
+  const int TB = rout <= 2 ? 2 : 2 * ((rout + 15) / 16);  // even, <= 6
+  const int nb = (rout + TB - 1) / TB;
+  const int units = nb * (PCe / GP);
+  for (int u = warp; u < units; u += kThreads / 32) {
+    const int b0 = (u % nb) * TB, g = u / nb;
+    const float *sg = sb + g * GP;
+    const int64_t qg = q0 + (int64_t)g * GP;
+    switch (TB) {
+      case 2: rank_block<2, TN>(sg, sG, rin, rpad, b0, rout, lane, PCe, out, N, qg, k, npairs, round_out); break;
+      case 4: rank_block<4, TN>(sg, sG, rin, rpad, b0, rout, lane, PCe, out, N, qg, k, npairs, round_out); break;
+      default: rank_block<6, TN>(sg, sG, rin, rpad, b0, rout, lane, PCe, out, N, qg, k, npairs, round_out); break;
+    }
+  }
+}
+
 template <int TN, int TBMAX>
 __global__ void __launch_bounds__(kThreads) batch_kernel(BWave w) {
   extern __shared__ __align__(16) float sm[];
-  constexpr int PC = 32 * TN;  // pairs per item
+  constexpr int PC = 32 * TN;  // pairs per chunk
   __shared__ Item s_item;
-  __shared__ Fetch s_fetch;
-  __shared__ int s_ready, s_abort, s_gseg;
+  __shared__ int s_abort;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float *sG = sm;                              // core of the current segment
-  float *sB0 = sm + w.core_floats;             // input chunk, two buffers
-  float *sB1 = sB0 + (size_t)w.max_k * PC;
-  if (tid == 0) {
-    s_gseg = -1;
-    s_fetch.cur = s_fetch.end = 0;
-    s_fetch.seg = -1;
-  }
-
-  // first item: fetch, wait for it, stage it
-  fetch_item(w, &s_fetch, &s_item, &s_ready);
-  __syncthreads();
-  Item cur = s_item;
-  if (cur.idx >= w.total) return;
-  if (!s_ready) {
-    wait_item(w, cur, &s_abort);
-    __syncthreads();
-    if (s_abort) return;
-  }
-  stage_item<PC>(w, cur, sB0);
-  cp_commit();
-  int buf = 0;
+  float *sB = sm + w.core_floats;              // kStagesB chunk buffers
+  const size_t stage = (size_t)w.max_k * PC;
+  int gseg = -1;                               // segment whose core is in sG
   for (;;) {
-    // take the next item now; prefetch its input only if it is already ready
-    // (the previous iteration ended with a barrier, so s_item is free)
-    fetch_item(w, &s_fetch, &s_item, &s_ready);
+    fetch_slice(w, &s_item);
     __syncthreads();
-    const Item nxt = s_item;
-    const bool has_next = nxt.idx < w.total;
-    const bool prefetched = has_next && s_ready;
-    if (prefetched) stage_item<PC>(w, nxt, buf ? sB0 : sB1);
-    cp_commit();
-    cp_wait_one();  // the current item's group is complete
+    const Item it = s_item;
+    if (it.idx >= w.total) break;
+    wait_item(w, it, &s_abort);
     __syncthreads();
-
-    const BSeg sg = w.segs[cur.seg];
+    if (s_abort) break;
+    const BSeg sg = w.segs[it.seg];
     const BOp &op = w.ops[sg.op];
     const int k = sg.k;
     const int rin = op.ranks[k], rout = op.ranks[k + 1];
     const int rpad = op.rpad[k + 1];
-    float *sb = buf ? sB1 : sB0;
-    // core of this (operator, step) into shared memory when it changes; TF32
-    // rounding of the staged operands (both uniform across the CTA)
-    const bool new_core = s_gseg != cur.seg;
-    if (new_core) {
+    const int64_t N = op.N, npairs = N >> 1;
+    if (gseg != it.seg) {
       const float *G = op.cores + op.coff[k];
       for (int e = tid; e < 2 * rin * 2 * rpad; e += kThreads) sG[e] = __ldg(G + e);
+      gseg = it.seg;
     }
-    if (w.tf32)
-      for (int e = tid; e < 2 * rin * PC; e += kThreads) sb[e] = tf32_rne_b(sb[e]);
-    if (new_core || w.tf32) __syncthreads();
-    if (tid == 0) s_gseg = cur.seg;
-
-    const int64_t N = op.N, npairs = N >> 1;
-    const int64_t tile = cur.idx - sg.first;
-    const int64_t c = tile / sg.tiles_per_rhs;
-    const int64_t q0 = (tile % sg.tiles_per_rhs) * PC;
-    float *out = k == op.d - 1 ? op.y + c * op.ld
-                               : (k & 1 ? op.buf1 : op.buf0) + c * (int64_t)rout * N;
-    const int TB = 2 * ((rout + 15) / 16);  // even; 8 warps x TB >= r_out
-    const int b0 = warp * TB;
-    if (b0 < rout) {
-      switch (TB) {
-        case 2: rank_block<2, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-        case 4: rank_block<4, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-        case 6: rank_block<6, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs); break;
-        default:
-          if constexpr (TBMAX > 6)
-            rank_block<8, TN>(sb, sG, rin, rpad, b0, rout, lane, PC, out, N, q0, k, npairs);
-          break;
-      }
-    }
-    // publish this item: the barrier orders every thread's stores before
-    // thread 0's device-scope fence and counter update
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      atomicAdd(w.done + cur.seg, 1u);
-    }
-    if (!has_next) break;
-    if (!prefetched) {
-      // its dependency was not complete when taken: wait (bounded), then copy
-      wait_item(w, nxt, &s_abort);
-      __syncthreads();
-      if (s_abort) break;
-      stage_item<PC>(w, nxt, buf ? sB0 : sB1);
+    const int64_t c_begin = (it.idx - sg.first) * sg.slice;
+    const int64_t c_end = c_begin + sg.slice < sg.nchunks ? c_begin + sg.slice : sg.nchunks;
+    const bool round_in = w.tf32 && k == 0;          // x itself is not TF32-rounded
+    const bool round_out = w.tf32 && k < op.d - 1;   // intermediates are stored rounded
+    float *out_base = k == op.d - 1 ? op.y : (k & 1 ? op.buf1 : op.buf0);
+    const int64_t out_stride = k == op.d - 1 ? op.ld : (int64_t)rout * N;
+    // prologue: the first kStagesB - 1 chunks of the slice
+#pragma unroll
+    for (int st = 0; st < kStagesB - 1; ++st) {
+      const int64_t t = c_begin + st;
+      if (t < c_end) stage_chunk(op, k, t / sg.chunks_per_rhs,
+                                 (t % sg.chunks_per_rhs) * sg.pc, sg.pc, sB + st * stage);
       cp_commit();
     }
-    cur = nxt;
-    buf ^= 1;
+    int cur = 0;
+    for (int64_t t = c_begin; t < c_end; ++t) {
+      {
+        const int64_t tn = t + kStagesB - 1;
+        if (tn < c_end)
+          stage_chunk(op, k, tn / sg.chunks_per_rhs, (tn % sg.chunks_per_rhs) * sg.pc, sg.pc,
+                      sB + ((cur + kStagesB - 1) % kStagesB) * stage);
+        cp_commit();
+      }
+      cp_wait_n<kStagesB - 1>();
+      __syncthreads();
+      float *sb = sB + cur * stage;
+      if (round_in) {
+        for (int e = tid; e < 2 * rin * sg.pc; e += kThreads) sb[e] = tf32_rne_b(sb[e]);
+        __syncthreads();
+      }
+      const int64_t c = t / sg.chunks_per_rhs, q0 = (t % sg.chunks_per_rhs) * sg.pc;
+      compute_chunk<TN, TBMAX>(sb, sG, rin, rpad, rout, warp, lane, sg.pc,
+                               out_base + c * out_stride, N, q0, k, npairs, round_out);
+      __syncthreads();  // the stage is refilled next iteration
+      cur = (cur + 1) % kStagesB;
+    }
+    cp_wait_all();
+    // publish the slice: the barrier above ordered every thread's stores
+    // before thread 0's device-scope fence and counter update
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(w.done + it.seg, 1u);
+    }
   }
   cp_wait_all();
 }
@@ -447,6 +415,7 @@ struct qtt_batch {
   qtt_dtype compute = QTT_F32;
   size_t budget = 0;
   int variant = 4;  // TN
+  int slice = 8;    // chunks per work item
   std::vector<qtt::WaveDev> waves;
   float *scratch = nullptr;
   size_t scratch_bytes = 0;
@@ -511,6 +480,11 @@ qtt_status build_plan(qtt_batch *B, cudaStream_t st) {
   if (B->d_next) cudaFree(B->d_next);
   B->d_next = nullptr;
   QTT_CUDA_TRY(cudaMalloc(&B->d_next, sizeof(unsigned long long) * std::max<size_t>(1, groups.size())));
+  // every wave's kernel is sized for the largest rank of the batch
+  int max_rank_all = 1;
+  for (const qtt_op *A : B->ops)
+    for (int k = 0; k <= A->d; ++k) max_rank_all = std::max(max_rank_all, A->ranks[k]);
+  const int max_k_wave = 2 * max_rank_all;
   for (auto &g : groups) {
     WaveDev wv;
     wv.ops = g;
@@ -553,8 +527,20 @@ qtt_status build_plan(qtt_batch *B, cudaStream_t st) {
         s.op = li;
         s.k = k;
         s.dep = k > 0 ? seg_of[li][k - 1] : -1;
-        s.tiles_per_rhs = ((o.N >> 1) + PC - 1) / PC;
-        s.ntiles = s.tiles_per_rhs * o.nrhs;
+        // widen the chunk while the stage (max_k rows of PC pairs) holds it,
+        // the pairs exist, and each warp would still get under 2 units
+        {
+          const int rows = 2 * o.ranks[k];
+          int f = 1;
+          while (rows * PC * (f * 2) <= max_k_wave * PC && (int64_t)PC * f * 2 <= (o.N >> 1) &&
+                 f * 2 <= 64)
+            f *= 2;
+          s.pc = PC * f;
+        }
+        s.chunks_per_rhs = ((o.N >> 1) + s.pc - 1) / s.pc;
+        s.nchunks = s.chunks_per_rhs * o.nrhs;
+        s.slice = B->slice;
+        s.ntiles = (s.nchunks + s.slice - 1) / s.slice;
         s.first = first;
         first += s.ntiles;
         seg_of[li][k] = (int)segs.size();
@@ -575,7 +561,7 @@ qtt_status build_plan(qtt_batch *B, cudaStream_t st) {
   return QTT_OK;
 }
 
-template <int TN, int TBMAX>
+template <int TN>
 qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
   int max_rin = 1;
   for (auto &w : B->waves) max_rin = std::max(max_rin, w.max_rin);
@@ -583,15 +569,15 @@ qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
   const int max_k = 2 * max_rin;
   const int rpad_max = (max_rin + 3) / 4 * 4;
   const int core_floats = (max_k * 2 * rpad_max + 15) / 16 * 16;
-  const size_t smem = sizeof(float) * ((size_t)core_floats + 2 * (size_t)max_k * PC);
-  // raised once to the largest footprint (rank 64), shared by all threads
+  const size_t smem = sizeof(float) * ((size_t)core_floats + (size_t)kStagesB * max_k * PC);
+  // raised once to the largest footprint (rank kMaxRank), shared by all threads
   static cudaError_t attr = cudaFuncSetAttribute(
-      batch_kernel<TN, TBMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      batch_kernel<TN, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
       (int)(sizeof(float) * ((size_t)(2 * kMaxRank * 2 * kMaxRank) +
-                             2 * (size_t)(2 * kMaxRank) * PC)));
+                             (size_t)kStagesB * (2 * kMaxRank) * PC)));
   QTT_CUDA_TRY(attr);
   int per_sm = 0, dev = 0, sms = 0;
-  QTT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<TN, TBMAX>, kThreads, smem));
+  QTT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<TN, 6>, kThreads, smem));
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int clk_khz = 2000000;
@@ -613,7 +599,7 @@ qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
     bw.wait_budget = (long long)clk_khz * 1000LL * 4;  // ~4 s of clock
     bw.max_k = max_k;
     bw.core_floats = core_floats;
-    batch_kernel<TN, TBMAX><<<B->grid, kThreads, smem, st>>>(bw);
+    batch_kernel<TN, 6><<<B->grid, kThreads, smem, st>>>(bw);
     count_launches(1);
     QTT_CUDA_TRY(cudaGetLastError());
   }
@@ -621,13 +607,9 @@ qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
 }
 
 qtt_status launch_waves(qtt_batch *B, cudaStream_t st) {
-  // register footprint follows the largest rank block a wave needs
-  int max_r = 1;
-  for (auto &w : B->waves) max_r = std::max(max_r, w.max_rin);
-  const bool small = max_r <= 48;  // TB = 2 ceil(r/16) <= 6
   switch (B->variant) {
-    case 2: return small ? launch_waves_t<2, 6>(B, st) : launch_waves_t<2, 8>(B, st);
-    default: return small ? launch_waves_t<4, 6>(B, st) : launch_waves_t<4, 8>(B, st);
+    case 2: return launch_waves_t<2>(B, st);
+    default: return launch_waves_t<4>(B, st);
   }
 }
 
@@ -687,7 +669,7 @@ qtt_status qtt_batch_create(qtt_batch **out, int nops, const qtt_op *const *ops,
       return fail(QTT_ERR_INVALID_ARG, "qtt_batch_create: operator lacks the packed copy");
     for (int k = 0; k <= A->d; ++k)
       if (A->ranks[k] > kMaxRank)
-        return fail(QTT_ERR_UNSUPPORTED, "qtt_batch_create: ranks above 64");
+        return fail(QTT_ERR_UNSUPPORTED, "qtt_batch_create: ranks above 48");
   }
   qtt_batch *B = new (std::nothrow) qtt_batch();
   if (!B) return fail(QTT_ERR_OOM, "qtt_batch_create: host allocation");
@@ -744,9 +726,13 @@ qtt_status qtt_batch_status(qtt_batch *B, void *stream) {
 
 qtt_status qtt_batch_set_variant(qtt_batch *B, int variant, void *stream) {
   if (!B) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_set_variant: no batch");
-  if (variant != 2 && variant != 4)
-    return fail(QTT_ERR_INVALID_ARG, "qtt_batch_set_variant: variant must be 2 or 4");
-  B->variant = variant;
+  // variant = pairs per lane (2 or 4) + 100 x chunks per work item (1..64);
+  // a bare 2 or 4 keeps 8 chunks per item
+  const int tn = variant % 100, sl = variant / 100 ? variant / 100 : 8;
+  if ((tn != 2 && tn != 4) || sl < 1 || sl > 64)
+    return fail(QTT_ERR_INVALID_ARG, "qtt_batch_set_variant: bad variant");
+  B->variant = tn;
+  B->slice = sl;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   QTT_CUDA_TRY(cudaStreamSynchronize(st));
   qtt_status s = build_plan(B, st);
@@ -759,12 +745,12 @@ qtt_status qtt_batch_autotune(qtt_batch *B, int reps, void *stream, int *chosen,
   if (!B) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_autotune: no batch");
   if (reps < 1) reps = 1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int best = B->variant;
+  int best = B->variant + 100 * B->slice;
   double best_t = 1e300;
   cudaEvent_t e0, e1;
   QTT_CUDA_TRY(cudaEventCreate(&e0));
   QTT_CUDA_TRY(cudaEventCreate(&e1));
-  for (int v : {2, 4}) {
+  for (int v : {802, 804, 3202, 3204}) {
     qtt_status s = qtt_batch_set_variant(B, v, stream);
     if (s != QTT_OK) continue;
     qtt_batch_run(B, stream);  // warm-up
@@ -793,7 +779,7 @@ qtt_status qtt_batch_info(const qtt_batch *B, int *waves, int *variant, int *gri
                           double *flops, size_t *scratch_bytes) {
   if (!B) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_info: no batch");
   if (waves) *waves = (int)B->waves.size();
-  if (variant) *variant = B->variant;
+  if (variant) *variant = B->variant + 100 * B->slice;
   if (grid) *grid = B->grid;
   if (flops) *flops = B->flops;
   if (scratch_bytes) *scratch_bytes = B->scratch_bytes;
