@@ -76,6 +76,13 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_GFLOPS = 1250.0
 FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.07
 METRIC = "QTT-apply GFLOP/s"
+# DRAM bytes (read + write) per launch of the workload's kernel from one ncu
+# capture of the same command, averaged over one apply's launches; valid for
+# the kernel source it was taken on (see the named profile).
+NCU_TRAFFIC = {
+    "apply_f64": {"bytes_per_launch": 144.43e9 / 24,
+                  "source": "profiles/step_f64_kernel_apply_f64_d24_launches.md"},
+}
 
 WORKLOADS = {
     "apply_f64": dict(kind="apply", d=24, rmax=32, seed=2, rhs_seed=3, nrhs=1, compute="f64"),
@@ -336,8 +343,24 @@ class ApplyRun:
     def work(self):
         return self.flops / 1e9
 
+    def algorithmic_bytes(self):
+        """Bytes one apply must move: every step reads r_k and writes r_{k+1}
+        values per position and right-hand side (Sec. 4.2's sweep)."""
+        d = self.data
+        es = {"f64": 8, "f32": 4, "tf32": 4, "bf16": 2}[self.compute]
+        return float(sum(d.ranks[k] + d.ranks[k + 1] for k in range(d.d)) * d.N * self.nrhs * es)
+
     def roofline(self, mean_s):
         achieved = self.flops / mean_s / 1e9
+        if self.compute == "bf16":
+            # BF16 steps run on the tensor cores and are bound by HBM: report
+            # the algorithmic bytes of the apply over its time
+            peak = measured_peaks().get("hbm_gbs") or 6800.0
+            gbs = self.algorithmic_bytes() / mean_s / 1e9
+            return {"bound": "hbm", "kernel": "step_mma_bf16_kernel (+ step_lp_kernel ends)",
+                    "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                    "traffic": None, "achieved_tflops": achieved / 1e3,
+                    "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json)"}
         if self.compute == "f64":
             peak, src = FP64_NOMINAL_GFLOPS, "FP64 pipe, 1.25 TFLOP/s nominal (2 FMA/clk/SM)"
         else:
@@ -345,6 +368,11 @@ class ApplyRun:
                                                "(the kernel multiplies on CUDA cores)")
         r = {"bound": "alu", "kernel": KERNEL[self.compute], "achieved": achieved, "peak": peak,
              "unit": "GFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": src}
+        t = NCU_TRAFFIC.get(self.spec["name"])
+        if t:
+            r["traffic"] = t["bytes_per_launch"]
+            r["traffic_source"] = t["source"]
+            r["algorithmic_bytes_per_launch"] = self.algorithmic_bytes() / self.launches
         if self.compute in ("bf16", "tf32"):
             pk = measured_peaks().get("bf16_tflops")
             if pk:
