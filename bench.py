@@ -469,7 +469,8 @@ class BatchedRun:
                 "flops_per_step_per_gpu": self.flops, "compute": self.compute,
                 "waves": self.info["waves"], "grid": self.info["grid"],
                 "autotuned_pairs_per_lane": self.variant % 100,
-                "autotuned_chunks_per_item": self.variant // 100,
+                "autotuned_chunks_per_item": (self.variant // 100) % 100,
+                "autotuned_ring_depth": self.variant // 10000,
                 "scratch_gb": self.info["scratch_bytes"] / 1e9,
                 "graph": "all waves captured in one CUDA graph",
                 "l2": "not flushed: each step streams tens of GB of intermediates"}

@@ -232,8 +232,9 @@ qtt_status qtt_batch_run(qtt_batch *B, void *stream);
  * runs gave up (the status word is then cleared). */
 qtt_status qtt_batch_status(qtt_batch *B, void *stream);
 /* Tile variant = pairs per lane (2 or 4: chunks of 64 or 128 position pairs,
- * wider for small ranks) + 100 x chunks per work item (1..64; a bare 2 or 4
- * means 8); re-plans and re-captures. */
+ * wider for small ranks) + 100 x chunks per work item (1..64, default 8)
+ * + 10000 x depth of the cp.async ring (2 or 3, default 3); re-plans and
+ * re-captures. */
 qtt_status qtt_batch_set_variant(qtt_batch *B, int variant, void *stream);
 /* Time every variant (`reps` runs each, after one warm-up) and keep the
  * fastest; reports it and its seconds per run. */

@@ -101,7 +101,7 @@ template <int N>
 __device__ __forceinline__ void cp_wait_n() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
-constexpr int kStagesB = 3;  // chunks in flight per CTA within a slice
+constexpr int kMaxStagesB = 3;  // chunk buffers per CTA (ring depth, 2 or 3)
 
 // One work item, decoded.
 struct Item {
@@ -315,7 +315,7 @@ __device__ __forceinline__ void compute_chunk(const float *sb, const float *sG, 
   }
 }
 
-template <int TN, int TBMAX>
+template <int TN, int TBMAX, int NS>
 __global__ void __launch_bounds__(kThreads) batch_kernel(BWave w) {
   extern __shared__ __align__(16) float sm[];
   constexpr int PC = 32 * TN;  // pairs per chunk
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(BWave w) {
   __shared__ int s_abort;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float *sG = sm;                              // core of the current segment
-  float *sB = sm + w.core_floats;              // kStagesB chunk buffers
+  float *sB = sm + w.core_floats;              // NS chunk buffers
   const size_t stage = (size_t)w.max_k * PC;
   int gseg = -1;                               // segment whose core is in sG
   for (;;) {
@@ -351,9 +351,9 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(BWave w) {
     const bool round_out = w.tf32 && k < op.d - 1;   // intermediates are stored rounded
     float *out_base = k == op.d - 1 ? op.y : (k & 1 ? op.buf1 : op.buf0);
     const int64_t out_stride = k == op.d - 1 ? op.ld : (int64_t)rout * N;
-    // prologue: the first kStagesB - 1 chunks of the slice
+    // prologue: the first NS - 1 chunks of the slice
 #pragma unroll
-    for (int st = 0; st < kStagesB - 1; ++st) {
+    for (int st = 0; st < NS - 1; ++st) {
       const int64_t t = c_begin + st;
       if (t < c_end) stage_chunk(op, k, t / sg.chunks_per_rhs,
                                  (t % sg.chunks_per_rhs) * sg.pc, sg.pc, sB + st * stage);
@@ -362,13 +362,13 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(BWave w) {
     int cur = 0;
     for (int64_t t = c_begin; t < c_end; ++t) {
       {
-        const int64_t tn = t + kStagesB - 1;
+        const int64_t tn = t + NS - 1;
         if (tn < c_end)
           stage_chunk(op, k, tn / sg.chunks_per_rhs, (tn % sg.chunks_per_rhs) * sg.pc, sg.pc,
-                      sB + ((cur + kStagesB - 1) % kStagesB) * stage);
+                      sB + ((cur + NS - 1) % NS) * stage);
         cp_commit();
       }
-      cp_wait_n<kStagesB - 1>();
+      cp_wait_n<NS - 1>();
       __syncthreads();
       float *sb = sB + cur * stage;
       if (round_in) {
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(BWave w) {
       compute_chunk<TN, TBMAX>(sb, sG, rin, rpad, rout, warp, lane, sg.pc,
                                out_base + c * out_stride, N, q0, k, npairs, round_out);
       __syncthreads();  // the stage is refilled next iteration
-      cur = (cur + 1) % kStagesB;
+      cur = (cur + 1) % NS;
     }
     cp_wait_all();
     // publish the slice: the barrier above ordered every thread's stores
@@ -416,6 +416,7 @@ struct qtt_batch {
   size_t budget = 0;
   int variant = 4;  // TN
   int slice = 8;    // chunks per work item
+  int stages = 3;   // cp.async ring depth
   std::vector<qtt::WaveDev> waves;
   float *scratch = nullptr;
   size_t scratch_bytes = 0;
@@ -561,7 +562,7 @@ qtt_status build_plan(qtt_batch *B, cudaStream_t st) {
   return QTT_OK;
 }
 
-template <int TN>
+template <int TN, int NS>
 qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
   int max_rin = 1;
   for (auto &w : B->waves) max_rin = std::max(max_rin, w.max_rin);
@@ -569,15 +570,15 @@ qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
   const int max_k = 2 * max_rin;
   const int rpad_max = (max_rin + 3) / 4 * 4;
   const int core_floats = (max_k * 2 * rpad_max + 15) / 16 * 16;
-  const size_t smem = sizeof(float) * ((size_t)core_floats + (size_t)kStagesB * max_k * PC);
+  const size_t smem = sizeof(float) * ((size_t)core_floats + (size_t)NS * max_k * PC);
   // raised once to the largest footprint (rank kMaxRank), shared by all threads
   static cudaError_t attr = cudaFuncSetAttribute(
-      batch_kernel<TN, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      batch_kernel<TN, 6, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
       (int)(sizeof(float) * ((size_t)(2 * kMaxRank * 2 * kMaxRank) +
-                             (size_t)kStagesB * (2 * kMaxRank) * PC)));
+                             (size_t)NS * (2 * kMaxRank) * PC)));
   QTT_CUDA_TRY(attr);
   int per_sm = 0, dev = 0, sms = 0;
-  QTT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<TN, 6>, kThreads, smem));
+  QTT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<TN, 6, NS>, kThreads, smem));
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int clk_khz = 2000000;
@@ -599,7 +600,7 @@ qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
     bw.wait_budget = (long long)clk_khz * 1000LL * 4;  // ~4 s of clock
     bw.max_k = max_k;
     bw.core_floats = core_floats;
-    batch_kernel<TN, 6><<<B->grid, kThreads, smem, st>>>(bw);
+    batch_kernel<TN, 6, NS><<<B->grid, kThreads, smem, st>>>(bw);
     count_launches(1);
     QTT_CUDA_TRY(cudaGetLastError());
   }
@@ -607,9 +608,10 @@ qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
 }
 
 qtt_status launch_waves(qtt_batch *B, cudaStream_t st) {
+  const bool deep = B->stages == 3;
   switch (B->variant) {
-    case 2: return launch_waves_t<2>(B, st);
-    default: return launch_waves_t<4>(B, st);
+    case 2: return deep ? launch_waves_t<2, 3>(B, st) : launch_waves_t<2, 2>(B, st);
+    default: return deep ? launch_waves_t<4, 3>(B, st) : launch_waves_t<4, 2>(B, st);
   }
 }
 
@@ -726,13 +728,15 @@ qtt_status qtt_batch_status(qtt_batch *B, void *stream) {
 
 qtt_status qtt_batch_set_variant(qtt_batch *B, int variant, void *stream) {
   if (!B) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_set_variant: no batch");
-  // variant = pairs per lane (2 or 4) + 100 x chunks per work item (1..64);
-  // a bare 2 or 4 keeps 8 chunks per item
-  const int tn = variant % 100, sl = variant / 100 ? variant / 100 : 8;
-  if ((tn != 2 && tn != 4) || sl < 1 || sl > 64)
+  // variant = pairs per lane (2 or 4) + 100 x chunks per work item (1..64)
+  // + 10000 x ring depth (2 or 3); missing parts mean 8 chunks and depth 3
+  const int tn = variant % 100, sl = (variant / 100) % 100 ? (variant / 100) % 100 : 8;
+  const int ns = variant / 10000 ? variant / 10000 : 3;
+  if ((tn != 2 && tn != 4) || sl < 1 || sl > 64 || (ns != 2 && ns != 3))
     return fail(QTT_ERR_INVALID_ARG, "qtt_batch_set_variant: bad variant");
   B->variant = tn;
   B->slice = sl;
+  B->stages = ns;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   QTT_CUDA_TRY(cudaStreamSynchronize(st));
   qtt_status s = build_plan(B, st);
@@ -745,12 +749,12 @@ qtt_status qtt_batch_autotune(qtt_batch *B, int reps, void *stream, int *chosen,
   if (!B) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_autotune: no batch");
   if (reps < 1) reps = 1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int best = B->variant + 100 * B->slice;
+  int best = B->variant + 100 * B->slice + 10000 * B->stages;
   double best_t = 1e300;
   cudaEvent_t e0, e1;
   QTT_CUDA_TRY(cudaEventCreate(&e0));
   QTT_CUDA_TRY(cudaEventCreate(&e1));
-  for (int v : {802, 804, 3202, 3204}) {
+  for (int v : {30802, 33202, 33204, 23202, 23204}) {
     qtt_status s = qtt_batch_set_variant(B, v, stream);
     if (s != QTT_OK) continue;
     qtt_batch_run(B, stream);  // warm-up
@@ -779,7 +783,7 @@ qtt_status qtt_batch_info(const qtt_batch *B, int *waves, int *variant, int *gri
                           double *flops, size_t *scratch_bytes) {
   if (!B) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_info: no batch");
   if (waves) *waves = (int)B->waves.size();
-  if (variant) *variant = B->variant + 100 * B->slice;
+  if (variant) *variant = B->variant + 100 * B->slice + 10000 * B->stages;
   if (grid) *grid = B->grid;
   if (flops) *flops = B->flops;
   if (scratch_bytes) *scratch_bytes = B->scratch_bytes;
