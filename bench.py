@@ -350,16 +350,40 @@ class ApplyRun:
         es = {"f64": 8, "f32": 4, "tf32": 4, "bf16": 2}[self.compute]
         return float(sum(d.ranks[k] + d.ranks[k + 1] for k in range(d.d)) * d.N * self.nrhs * es)
 
+    def fused_bytes(self):
+        """Bytes the BF16 launches must move: a fused pair of tensor-core
+        steps (k, k+1) reads r_k and writes r_{k+2} planes, the planes between
+        them stay on chip; every other step reads r_k and writes r_{k+1}.
+        The pairing rule is the library's: k >= 3, k + 2 < d, the three ranks
+        in [16, 48]."""
+        d, ks, b, k = self.data, [], 0.0, 0
+        r = d.ranks
+        while k < d.d:
+            if (k >= 3 and k + 2 < d.d and all(16 <= r[k + t] <= 48 for t in range(3))
+                    and (d.N >> 2) % 8 == 0):
+                b += r[k] + r[k + 2]
+                ks.append((k, k + 1))
+                k += 2
+            else:
+                b += r[k] + r[k + 1]
+                ks.append((k,))
+                k += 1
+        return b * d.N * self.nrhs * 2, ks
+
     def roofline(self, mean_s):
         achieved = self.flops / mean_s / 1e9
         if self.compute == "bf16":
             # BF16 steps run on the tensor cores and are bound by HBM: report
-            # the algorithmic bytes of the apply over its time
+            # the bytes the launches must move over the apply's time
             peak = measured_peaks().get("hbm_gbs") or 6800.0
-            gbs = self.algorithmic_bytes() / mean_s / 1e9
-            return {"bound": "hbm", "kernel": "step_mma_bf16_kernel (+ step_lp_kernel ends)",
+            fb, plan = self.fused_bytes()
+            gbs = fb / mean_s / 1e9
+            return {"bound": "hbm",
+                    "kernel": "step_mma2_kernel fused pairs (+ step_mma / step_lp single steps)",
                     "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                     "traffic": None, "achieved_tflops": achieved / 1e3,
+                    "bytes_per_apply": fb, "unfused_bytes_per_apply": self.algorithmic_bytes(),
+                    "launches_per_apply": len(plan),
                     "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json)"}
         if self.compute == "f64":
             peak, src = FP64_NOMINAL_GFLOPS, "FP64 pipe, 1.25 TFLOP/s nominal (2 FMA/clk/SM)"

@@ -202,6 +202,16 @@ static bool use_staged_f32() {
   return on;
 }
 
+// Pairs of tensor-core steps fused into one launch (QTT_NO_FUSED_MMA=1 keeps
+// one launch per step, for comparison).
+static bool use_fused_mma() {
+  static const bool on = [] {
+    const char *v = std::getenv("QTT_NO_FUSED_MMA");
+    return !(v && *v && *v != '0');
+  }();
+  return on;
+}
+
 static size_t dtype_size(qtt_dtype t) {
   return t == QTT_F64 ? 8 : (t == QTT_BF16 ? 2 : 4);
 }
@@ -243,9 +253,39 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
     buf[1] = buf[0] + (size_t)A->rmax_inner * (size_t)N * (size_t)chunk * esz;
   }
   const size_t xsz = dtype_size(xt), ysz = dtype_size(yt);
+  const bool tc = compute == QTT_BF16 && use_tensor_cores() && A->mma_bf16;
   for (int64_t c0 = 0; c0 < nrhs; c0 += chunk) {
     const int64_t nc = std::min<int64_t>(chunk, nrhs - c0);
+    int src = 0;  // scratch half holding the current intermediate (k >= 1)
     for (int k = 0; k < d; ++k) {
+      if (tc && use_fused_mma() && k + 2 < d && A->mp[k] && A->mp[k + 1] &&
+          mma2_steps_eligible(k, A->ranks[k], A->ranks[k + 1], A->ranks[k + 2], N)) {
+        // steps k and k+1 in one launch; y_{k+2} lands in the other half
+        StepMMA2 m;
+        m.in = reinterpret_cast<const __nv_bfloat16 *>(buf[src]);
+        m.in_rhs_stride = (int64_t)A->ranks[k] * N;
+        m.out = reinterpret_cast<__nv_bfloat16 *>(buf[src ^ 1]);
+        m.out_rhs_stride = (int64_t)A->ranks[k + 2] * N;
+        m.A1 = A->mma_bf16 + A->moff[k];
+        m.A2 = A->mma_bf16 + A->moff[k + 1];
+        m.k = k;
+        m.r0 = A->ranks[k];
+        m.r1 = A->ranks[k + 1];
+        m.r2 = A->ranks[k + 2];
+        m.Mp1 = A->mp[k];
+        m.Kp1 = A->kp[k];
+        m.Mp2 = A->mp[k + 1];
+        m.N = N;
+        m.nrhs = nc;
+        const cudaError_t e = launch_step_mma2_bf16(m, st);
+        if (e != cudaSuccess) {
+          scratch_free(scratch, st);
+          return cuda_fail(e, "fused tensor-core step launch");
+        }
+        src ^= 1;
+        ++k;
+        continue;
+      }
       StepLP p;
       std::memset(&p, 0, sizeof(p));
       p.k = k;
@@ -261,7 +301,7 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
         p.in_rhs_stride = ld;
         p.in_type = xt;
       } else {
-        p.in = buf[(k - 1) & 1];
+        p.in = buf[src];
         p.in_rhs_stride = (int64_t)p.rin * N;
         p.in_type = mid;
       }
@@ -279,13 +319,13 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
           p.s_v = epi.s_v;
         }
       } else {
-        p.out = buf[k & 1];
+        p.out = buf[k == 0 ? 0 : src ^ 1];
         p.out_rhs_stride = (int64_t)p.rout * N;
         p.out_type = mid;
         p.round_tf32_out = mode == LP_TF32;
       }
       cudaError_t e;
-      if (compute == QTT_BF16 && use_tensor_cores() && A->mma_bf16 && A->mp[k] &&
+      if (tc && A->mp[k] &&
           p.in_type == QTT_BF16 && p.out_type == QTT_BF16 && !p.epi &&
           mma_step_eligible(k, p.rin, p.rout, N)) {
         StepMMA m;
@@ -311,6 +351,7 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
         scratch_free(scratch, st);
         return cuda_fail(e, "step_lp launch");
       }
+      if (k > 0) src ^= 1;
     }
   }
   scratch_free(scratch, st);

@@ -24,4 +24,22 @@ struct StepMMA {
 bool mma_step_eligible(int k, int rin, int rout, int64_t N);
 cudaError_t launch_step_mma_bf16(const StepMMA &s, cudaStream_t st);
 
+// Two consecutive steps k, k+1 in one launch (step_mma2.cu): the r_{k+1}
+// planes between them stay in shared memory.
+constexpr int kMma2MaxRank = 48;
+
+struct StepMMA2 {
+  const __nv_bfloat16 *in;   // y_k, planar [rhs][a][position], BF16
+  int64_t in_rhs_stride;
+  __nv_bfloat16 *out;        // y_{k+2}
+  int64_t out_rhs_stride;
+  const __nv_bfloat16 *A1;   // M_k as [Mp1][Kp1]
+  const __nv_bfloat16 *A2;   // M_{k+1} as [Mp2][Mp1] (its K padding equals M_k's row padding)
+  int k, r0, r1, r2, Mp1, Kp1, Mp2;
+  int64_t N, nrhs;
+};
+
+bool mma2_steps_eligible(int k, int r0, int r1, int r2, int64_t N);
+cudaError_t launch_step_mma2_bf16(const StepMMA2 &s, cudaStream_t st);
+
 }  // namespace qtt

@@ -1,6 +1,8 @@
-"""The BF16 tensor-core step (mma.sync, FP32 accumulate) used for BF16 steps
-with k >= 3 and ranks in [4, 64]: exact on integer data and within the BF16
-error bound otherwise, including partial chunks and many right-hand sides."""
+"""The BF16 tensor-core steps (mma.sync, FP32 accumulate): the single step
+used for k >= 3 and ranks in [4, 64], and the fused pair of steps used for
+k >= 3, k + 2 < d and ranks in [16, 48].  Exact on integer data and within
+the BF16 error bound otherwise, including partial chunks, uneven rank
+profiles and many right-hand sides."""
 import math
 
 import numpy as np
@@ -26,12 +28,12 @@ def _signed_permutation(rng):
     return P * rng.choice([-1.0, 1.0], size=(2, 1))
 
 
-def _rank_diagonal_operator(d, r, seed):
+def _rank_diagonal_operator(d, r, seed, ranks=None):
     """A = sum over alpha of a Kronecker product of signed 2x2 permutations:
     every core is diagonal in the rank index, so every intermediate entry is
-    a signed copy of an x entry and the output a sum of r of them."""
+    a signed copy of an x entry and the output a sum of at most r of them."""
     rng = np.random.default_rng(seed)
-    ranks = [1] + [r] * (d - 1) + [1]
+    ranks = ranks or [1] + [r] * (d - 1) + [1]
     cores = []
     for k in range(d):
         ra, rb = ranks[k], ranks[k + 1]
@@ -60,6 +62,42 @@ def test_bf16_error_bound_tensor_cores(qtt, d, rmax, nrhs):
     import torch
     data = inputs.synthetic_operator(d, rmax, 9)
     x = inputs.gaussian_rhs(data.N, nrhs, 10)
+    op = qtt.Operator(data, packs=("bf16",))
+    y = op.apply(torch.from_numpy(x).to(torch.bfloat16).cuda(), compute="bf16")
+    err = rel_l2(y.double().cpu().numpy(), oracle.apply(data, x))
+    op.close()
+    assert err <= 4 * math.sqrt(d) * 2.0 ** -8, err
+
+
+@pytest.mark.parametrize("ranks,nrhs", [
+    ([1, 2, 4, 16, 16, 16, 1], 3),                           # d=6: one fused pair, 16 quads
+    ([1, 2, 4, 8, 17, 33, 20, 1], 2),                        # d=7: ragged ranks, 32 quads
+    ([1, 2, 4, 8, 48, 24, 48, 40, 19, 16, 9, 1], 4),         # d=11: pairs (3,4),(5,6),(7,8)
+    ([1, 2, 4, 8, 16, 48, 48, 48, 48, 48, 48, 48, 48, 1], 1),
+])
+def test_fused_pairs_integer_exact(qtt, ranks, nrhs):
+    """Uneven rank profiles through the fused pair kernel: every padded
+    shape (2 r rounded up to 16) from 32 to 96 on both sides of the pair."""
+    import torch
+    d = len(ranks) - 1
+    data = _rank_diagonal_operator(d, 0, sum(ranks), ranks=ranks)
+    x = np.random.default_rng(d).integers(-1, 2, size=(nrhs, 1 << d)).astype(np.float64)
+    op = qtt.Operator(data, packs=("bf16",))
+    y = op.apply(torch.from_numpy(x).float().cuda(), compute="bf16").double().cpu().numpy()
+    op.close()
+    assert np.array_equal(y, oracle.apply(data, x))
+
+
+@pytest.mark.parametrize("case,nrhs", [
+    ([1, 2, 4, 16, 16, 16, 1], 2), ([1, 3, 8, 24, 40, 31, 48, 17, 1], 3), (11, 3), (20, 2)])
+def test_fused_pairs_bf16_error_bound(qtt, case, nrhs):
+    import torch
+    if isinstance(case, list):
+        data = inputs.random_cores(len(case) - 1, case, 21)
+    else:
+        data = inputs.synthetic_operator(case, 48, 21)
+    d = data.d
+    x = inputs.gaussian_rhs(data.N, nrhs, 22)
     op = qtt.Operator(data, packs=("bf16",))
     y = op.apply(torch.from_numpy(x).to(torch.bfloat16).cuda(), compute="bf16")
     err = rel_l2(y.double().cpu().numpy(), oracle.apply(data, x))
