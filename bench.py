@@ -354,13 +354,17 @@ class ApplyRun:
         """Bytes the BF16 launches must move: a fused pair of tensor-core
         steps (k, k+1) reads r_k and writes r_{k+2} planes, the planes between
         them stay on chip; every other step reads r_k and writes r_{k+1}.
-        The pairing rule is the library's: k >= 3, k + 2 < d, the three ranks
-        in [16, 48]."""
+        The pairing rule is the library's: k + 2 < d and either the TMA +
+        tcgen05 pair (k >= 6, r_k % 8 == 0, ranks in [8, 56]) or the mma.sync
+        pair (k >= 3, ranks in [16, 48])."""
         d, ks, b, k = self.data, [], 0.0, 0
         r = d.ranks
         while k < d.d:
-            if (k >= 3 and k + 2 < d.d and all(16 <= r[k + t] <= 48 for t in range(3))
-                    and (d.N >> 2) % 8 == 0):
+            tc2 = k >= 6 and r[k] % 8 == 0 and all(8 <= r[k + t] <= 56 for t in range(3)) \
+                if k + 2 < d.d else False
+            mma2 = k >= 3 and all(16 <= r[k + t] <= 48 for t in range(3)) \
+                and (d.N >> 2) % 8 == 0 if k + 2 < d.d else False
+            if tc2 or mma2:
                 b += r[k] + r[k + 2]
                 ks.append((k, k + 1))
                 k += 2
@@ -379,7 +383,8 @@ class ApplyRun:
             fb, plan = self.fused_bytes()
             gbs = fb / mean_s / 1e9
             return {"bound": "hbm",
-                    "kernel": "step_mma2_kernel fused pairs (+ step_mma / step_lp single steps)",
+                    "kernel": "whole apply: step_tc2_kernel (TMA + tcgen05 fused pairs), "
+                              "step_mma2_kernel pairs, step_mma / step_lp single steps",
                     "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                     "traffic": None, "achieved_tflops": achieved / 1e3,
                     "bytes_per_apply": fb, "unfused_bytes_per_apply": self.algorithmic_bytes(),

@@ -212,6 +212,16 @@ static bool use_fused_mma() {
   return on;
 }
 
+// Fused pairs run on the tcgen05 tensor cores (QTT_NO_TCGEN05=1 selects the
+// mma.sync pair kernel instead, for comparison).
+static bool use_tcgen05() {
+  static const bool on = [] {
+    const char *v = std::getenv("QTT_NO_TCGEN05");
+    return !(v && *v && *v != '0');
+  }();
+  return on;
+}
+
 static size_t dtype_size(qtt_dtype t) {
   return t == QTT_F64 ? 8 : (t == QTT_BF16 ? 2 : 4);
 }
@@ -258,8 +268,12 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
     const int64_t nc = std::min<int64_t>(chunk, nrhs - c0);
     int src = 0;  // scratch half holding the current intermediate (k >= 1)
     for (int k = 0; k < d; ++k) {
-      if (tc && use_fused_mma() && k + 2 < d && A->mp[k] && A->mp[k + 1] &&
-          mma2_steps_eligible(k, A->ranks[k], A->ranks[k + 1], A->ranks[k + 2], N)) {
+      const bool pair = tc && use_fused_mma() && k + 2 < d && A->mp[k] && A->mp[k + 1];
+      const bool tc5 = pair && use_tcgen05() &&
+                       tc2_steps_eligible(k, A->ranks[k], A->ranks[k + 1], A->ranks[k + 2], N);
+      const bool mma2 =
+          pair && mma2_steps_eligible(k, A->ranks[k], A->ranks[k + 1], A->ranks[k + 2], N);
+      if (tc5 || mma2) {
         // steps k and k+1 in one launch; y_{k+2} lands in the other half
         StepMMA2 m;
         m.in = reinterpret_cast<const __nv_bfloat16 *>(buf[src]);
@@ -277,7 +291,13 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
         m.Mp2 = A->mp[k + 1];
         m.N = N;
         m.nrhs = nc;
-        const cudaError_t e = launch_step_mma2_bf16(m, st);
+        cudaError_t e = cudaErrorNotSupported;
+        if (tc5) e = launch_step_tc2_bf16(m, st);
+        if (e == cudaErrorNotSupported && mma2) e = launch_step_mma2_bf16(m, st);
+        if (e == cudaErrorNotSupported) {
+          cudaGetLastError();  // nothing was launched: run the two steps one by one
+          goto single_step;
+        }
         if (e != cudaSuccess) {
           scratch_free(scratch, st);
           return cuda_fail(e, "fused tensor-core step launch");
@@ -286,6 +306,7 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
         ++k;
         continue;
       }
+    single_step:
       StepLP p;
       std::memset(&p, 0, sizeof(p));
       p.k = k;
@@ -601,6 +622,11 @@ qtt_status qtt_residual(const qtt_op *K, double a, const double *f, const double
 qtt_status qtt_sync_status(void *stream) {
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "qtt_sync_status");
+  int h = 0;
+  e = tc_status_take(&h);
+  if (e != cudaSuccess) return cuda_fail(e, "qtt_sync_status: device status word");
+  if (h != 0)
+    return fail(QTT_ERR_TIMEOUT, "tensor-core kernel: an mbarrier wait ran out of its budget");
   return QTT_OK;
 }
 

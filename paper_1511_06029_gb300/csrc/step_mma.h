@@ -42,4 +42,15 @@ struct StepMMA2 {
 bool mma2_steps_eligible(int k, int r0, int r1, int r2, int64_t N);
 cudaError_t launch_step_mma2_bf16(const StepMMA2 &s, cudaStream_t st);
 
+// The same fused pair on the tcgen05 tensor cores (step_tc2.cu): TMA tile
+// loads and stores, MMAs from shared-memory descriptors into TMEM.  Returns
+// cudaErrorNotSupported (nothing launched) when the shapes do not fit its
+// tile views; the caller then runs the two steps another way.
+constexpr int kTc2MaxRank = 56;
+bool tc2_steps_eligible(int k, int r0, int r1, int r2, int64_t N);
+cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st);
+// Device status word of the tcgen05 kernels (QTT_ERR_TIMEOUT after a bounded
+// wait gave up); returns it and clears it.
+cudaError_t tc_status_take(int *status);
+
 }  // namespace qtt

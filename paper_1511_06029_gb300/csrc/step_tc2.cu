@@ -1,0 +1,523 @@
+// Two consecutive BF16 core steps (k, k+1) of Algorithm 2 on the fifth-
+// generation tensor cores: TMA tile loads and stores, tcgen05.mma with
+// operands in shared memory and FP32 accumulators in tensor memory (TMEM).
+//
+// The four positions of a quad (bits k and k+1 free, the others fixed) are
+// closed under both steps, so a chunk of 64 quads is read from HBM once and
+// only y_{k+2} goes back; the r_{k+1} planes in between stay on chip.
+//
+// Per chunk (a persistent CTA takes chunks blockIdx.x, + grid, ...):
+//   stage S   (B of step k, MN-major, 128-byte swizzle): K rows 2a + j_k,
+//             N columns 64 j_{k+1} + quad -- one TMA box of the input planes
+//   D1 = M_k S      in TMEM: lanes 2b + i_k, columns 64 j_{k+1} + quad
+//   T         (B of step k+1, MN-major, no swizzle): K rows 2b + j_{k+1},
+//             N columns 64 i_k + quad   (D1 rounded to BF16 -- the rounding
+//             the unfused path applies when it stores y_{k+1})
+//   D2 = M_{k+1} T  in TMEM: lanes 2c + i_{k+1}, columns 64 i_k + quad
+//   O         output tile, rows (i_k, c, i_{k+1}) of 64 quads (128-byte
+//             swizzle) -- one TMA box store into y_{k+2}
+// Both MMAs are M = 128 (rows 2b + i; rows past 2 r are padding whose
+// results are never read), N = 128, K = 16 per instruction.  M_k and M_{k+1}
+// stay in shared memory for the CTA's lifetime (K-major, no swizzle).
+//
+// TMA boxes.  With k >= 6 the 64 quads of a chunk are 64 consecutive
+// positions in each of the four (j_k, j_{k+1}) slices, and the planes of all
+// right-hand sides form one index P = rhs r + a (stride N), so one 5-D view
+// (x = position bits 0..k-1, j_k, P, j_{k+1}, position bits k+2..) covers the
+// input; its box (64, 2, r_k, 2, 1) lands in shared memory exactly as the
+// MMA's swizzled MN-major operand.  The output view orders (x, i_{k+1}, P,
+// i_k, hi) so that the rows one epilogue warp writes are consecutive in the
+// swizzle pattern.  r_k % 8 == 0 makes the box's K extent 2 r_k the padded
+// K of the MMA, so no plane of a neighbouring right-hand side is read.
+//
+// Warp roles, connected by mbarriers (a software pipeline over chunks):
+//   warp 0      one lane issues the TMA loads into a ring of S stages
+//   warp 1      allocates TMEM; one lane issues the MMAs: MMA1 of chunk n
+//               (frees its stage on completion) ahead of MMA2 of chunk n-1
+//   warps 2-9   epilogue: D1 -> T; D2 -> O (double buffered) -> TMA store
+// TMEM holds two accumulator buffers of 128 columns (chunk n uses n % 2;
+// D2 overwrites D1 of the same chunk once the epilogue has read it).
+//
+// Every wait is bounded: a clock budget after which the CTA raises a shared
+// abort flag, every role leaves its loop, the CTA drains its copies, frees
+// its TMEM, records QTT_ERR_TIMEOUT in a device status word (read by
+// qtt_sync_status) and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "qtt_internal.h"
+#include "step_mma.h"
+
+namespace qtt {
+
+__device__ int g_tc_status = 0;
+
+namespace {
+
+constexpr int kProducerWarp = 0;
+constexpr int kMmaWarp = 1;
+constexpr int kEpiWarp0 = 2;
+constexpr int kEpilogue = 256;             // warps 2-9
+constexpr int kThreads = 64 + kEpilogue;
+constexpr int kQ = 64;                     // quads per chunk
+constexpr int kCols = 2 * kQ;              // N of both MMAs
+constexpr int kMaxStages = 8;
+constexpr int kBarBytes = 256;             // mbarriers, TMEM address, abort flag
+constexpr int kTmemCols = 256;             // two accumulator buffers
+constexpr unsigned kLboT = 144;            // T: K-group stride (16-byte pad: no bank conflicts)
+constexpr long long kWaitBudget = 4000000000LL;  // clock64 ticks (about 2 s)
+
+__device__ __forceinline__ unsigned su32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cpa16(unsigned dst, const void *src, int n) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n));
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_init(unsigned a, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
+}
+// One test of phase `parity` of the mbarrier at `a`.
+__device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Shared-memory matrix descriptor: start address, leading and stride byte
+// offsets, version 1 (bits 46-47), layout (bits 61-63: 0 none, 2 128-byte
+// swizzle).  No swizzle: LBO = distance between core matrices adjacent in K,
+// SBO = adjacent in M/N.  128-byte swizzle, MN-major: LBO = distance between
+// 64-element MN blocks, SBO = between 8-row K groups (1024 bytes).
+__device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsigned sbo,
+                                              unsigned layout = 0) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) |
+         ((uint64_t)layout << 61);
+}
+
+// Instruction descriptor of kind::f16: D FP32, A and B BF16, A K-major,
+// B MN-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (0u << 15) | (1u << 16) |
+                            ((uint32_t)(kCols >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t da, uint64_t db, int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(unsigned mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          mbar)
+      : "memory");
+}
+
+// 32 lanes x 32 consecutive FP32 columns from TMEM into v[0..31].
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(r[e]);
+}
+
+// TMA tile copies (5-D tensor maps) and their completion mechanisms.
+__device__ __forceinline__ void tma_load5(unsigned dst, const CUtensorMap *m, int c0, int c1,
+                                          int c2, int c3, int c4, unsigned mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3, %4, %5, %6}], [%7];\n" ::"r"(dst),
+      "l"(m), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store5(const CUtensorMap *m, unsigned src, int c0, int c1,
+                                           int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5, %6}], "
+      "[%1];\n" ::"l"(m),
+      "r"(src), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+__device__ __forceinline__ void expect_tx(unsigned mbar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+}
+// Barrier of the epilogue warps that also ORs a flag over them: the abort
+// decision stays uniform, so no epilogue thread is left at a barrier.
+__device__ __forceinline__ bool epi_any(bool v) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((unsigned)v), "n"(kEpilogue)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void epi_sync() {
+  asm volatile("bar.sync 1, %0;\n" ::"n"(kEpilogue) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ uint4 pack8(const float *v) {
+  uint4 o;
+  __nv_bfloat162 h;
+  h = __floats2bfloat162_rn(v[0], v[1]);
+  o.x = *reinterpret_cast<unsigned *>(&h);
+  h = __floats2bfloat162_rn(v[2], v[3]);
+  o.y = *reinterpret_cast<unsigned *>(&h);
+  h = __floats2bfloat162_rn(v[4], v[5]);
+  o.z = *reinterpret_cast<unsigned *>(&h);
+  h = __floats2bfloat162_rn(v[6], v[7]);
+  o.w = *reinterpret_cast<unsigned *>(&h);
+  return o;
+}
+
+struct Bars {
+  unsigned long long full[kMaxStages], empty[kMaxStages];
+  unsigned long long d1full[2], d2full[2], dfree[2], tready;
+  uint32_t tmem;
+  int abort;
+};
+static_assert(sizeof(Bars) <= kBarBytes, "mbarrier block");
+
+__device__ __forceinline__ void mbar_arrive(unsigned a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(a) : "memory");
+}
+// Bounded wait that also gives up once another role raised the abort flag.
+__device__ __forceinline__ bool wait_bar(unsigned a, unsigned parity, volatile int *abort) {
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_try(a, parity)) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitBudget) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+// Shared-memory plan (byte offsets from a 1024-aligned base).
+struct Plan {
+  unsigned a1, a2, t, o0, o1, s0, stage, obytes, end;
+};
+__host__ __device__ inline unsigned up1k(unsigned v) { return (v + 1023u) & ~1023u; }
+__host__ __device__ inline Plan make_plan(const StepMMA2 &s, int S) {
+  Plan p;
+  const unsigned Kp2 = (unsigned)s.Mp1;
+  p.a1 = kBarBytes;
+  p.a2 = p.a1 + (unsigned)(s.Mp1 * s.Kp1 * 2);
+  p.t = p.a2 + (unsigned)(s.Mp2 * s.Mp1 * 2);
+  // O and the stages follow T: the M = 128 padding rows of M_{k+1} read past
+  // A2 into T (finite data; those rows are never used)
+  p.obytes = (unsigned)(2 * 2 * s.r2 * 128);
+  p.o0 = up1k(p.t + 16u * (Kp2 / 8u) * kLboT);
+  p.o1 = up1k(p.o0 + p.obytes);
+  p.stage = (unsigned)(s.Kp1 * kCols * 2);
+  p.s0 = up1k(p.o1 + p.obytes);
+  p.end = p.s0 + (unsigned)S * p.stage;
+  return p;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    step_tc2_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
+                    StepMMA2 s, int S) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  // 1024-aligned base for the swizzled tiles
+  unsigned char *base = smraw + ((1024u - (su32(smraw) & 1023u)) & 1023u);
+  const Plan P = make_plan(s, S);
+  Bars &B = *reinterpret_cast<Bars *>(base);
+  const int Kp2 = s.Mp1;
+  const unsigned sbo_t = (unsigned)(Kp2 / 8) * kLboT;
+  unsigned char *sA1 = base + P.a1, *sA2 = base + P.a2, *sT = base + P.t;
+  const unsigned base32 = su32(base);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == kMmaWarp) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+            su32(&B.tmem)),
+        "r"(kTmemCols)
+        : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < kMaxStages; ++i) {
+      mbar_init(su32(&B.full[i]), 1);
+      mbar_init(su32(&B.empty[i]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(su32(&B.d1full[i]), 1);
+      mbar_init(su32(&B.d2full[i]), 1);
+      mbar_init(su32(&B.dfree[i]), kEpilogue);
+    }
+    mbar_init(su32(&B.tready), kEpilogue);
+    B.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  // core matrices, K-major core-matrix layout: (row, k) at
+  // (row / 8) Kp 16 + (k / 8) 128 + (row % 8) 16 + (k % 8) 2 bytes
+  for (int e = tid; e < s.Mp1 * (s.Kp1 / 8); e += kThreads) {
+    const int r = e / (s.Kp1 / 8), kg = e % (s.Kp1 / 8);
+    cpa16(su32(sA1 + (size_t)(r >> 3) * s.Kp1 * 16 + kg * 128 + (r & 7) * 16),
+          s.A1 + (size_t)r * s.Kp1 + 8 * kg, 16);
+  }
+  for (int e = tid; e < s.Mp2 * (Kp2 / 8); e += kThreads) {
+    const int r = e / (Kp2 / 8), kg = e % (Kp2 / 8);
+    cpa16(su32(sA2 + (size_t)(r >> 3) * Kp2 * 16 + kg * 128 + (r & 7) * 16),
+          s.A2 + (size_t)r * Kp2 + 8 * kg, 16);
+  }
+  cpa_commit();
+  cpa_wait<0>();
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  const uint32_t tmem = B.tmem;
+  volatile int *abort = &B.abort;
+  const int64_t nq = s.N >> 2;
+  const int64_t cpr = nq / kQ;
+  const int64_t nchunks = cpr * s.nrhs;
+  const int64_t G = gridDim.x;
+  const int lowmask = (1 << s.k) - 1;
+
+  if (warp == kProducerWarp) {
+    // ---------------------------------------------------------------- TMA loads
+    if (lane == 0) {
+      int n = 0;
+      for (;; ++n) {
+        const int64_t t = blockIdx.x + (int64_t)n * G;
+        if (t >= nchunks) break;
+        const int st = n % S;
+        if (n >= S && !wait_bar(su32(&B.empty[st]), (unsigned)((n / S) - 1) & 1u, abort)) break;
+        const int64_t c = t / cpr, q0 = (t % cpr) * kQ;
+        const unsigned fb = su32(&B.full[st]);
+        expect_tx(fb, P.stage);
+        tma_load5(base32 + P.s0 + (unsigned)st * P.stage, &tin, (int)(q0 & lowmask), 0,
+                  (int)(c * s.r0), 0, (int)(q0 >> s.k), fb);
+      }
+      if (*abort) {
+        // loads still in flight land before the CTA's shared memory goes
+        volatile int never = 0;
+        for (int m = n - S < 0 ? 0 : n - S; m < n; ++m)
+          wait_bar(su32(&B.full[m % S]), (unsigned)(m / S) & 1u, &never);
+      }
+    }
+  } else if (warp == kMmaWarp) {
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      const unsigned a1 = base32 + P.a1, a2 = base32 + P.a2, t32 = base32 + P.t;
+      for (int n = 0;; ++n) {
+        const int64_t t = blockIdx.x + (int64_t)n * G;
+        const bool has = t < nchunks;
+        if (has) {
+          const int st = n % S, b = n & 1;
+          if (!wait_bar(su32(&B.full[st]), (unsigned)(n / S) & 1u, abort)) break;
+          if (n >= 2 && !wait_bar(su32(&B.dfree[b]), (unsigned)((n >> 1) - 1) & 1u, abort))
+            break;
+          tc_fence_after();
+          const unsigned sb = base32 + P.s0 + (unsigned)st * P.stage;
+          for (int ks = 0; ks < s.Kp1 / 16; ++ks)
+            mma_bf16(tmem + (uint32_t)(b * 128), smem_desc(a1 + ks * 256, 128, s.Kp1 * 16),
+                     smem_desc(sb + ks * 2048, (unsigned)s.Kp1 * 128, 1024, 2), ks > 0);
+          mma_commit(su32(&B.empty[st]));
+          mma_commit(su32(&B.d1full[b]));
+        }
+        if (n >= 1) {
+          const int m = n - 1, bm = m & 1;
+          if (!wait_bar(su32(&B.tready), (unsigned)m & 1u, abort)) break;
+          tc_fence_after();
+          for (int ks = 0; ks < Kp2 / 16; ++ks)
+            mma_bf16(tmem + (uint32_t)(bm * 128), smem_desc(a2 + ks * 256, 128, Kp2 * 16),
+                     smem_desc(t32 + ks * 2 * kLboT, kLboT, sbo_t), ks > 0);
+          mma_commit(su32(&B.d2full[bm]));
+        }
+        if (!has) break;
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int qr = warp & 3, half = (warp - kEpiWarp0) >> 2;
+    const int row = 32 * qr + lane;  // TMEM lane = D row
+    const bool leader = tid == kEpiWarp0 * 32;
+    const uint32_t tl = ((uint32_t)(32 * qr) << 16) + (uint32_t)(64 * half);
+    const int orows = 2 * s.r2;
+    const int R = half * orows + row;  // output tile row (i_k, c, i_{k+1})
+    for (int n = 0;; ++n) {
+      const int64_t t = blockIdx.x + (int64_t)n * G;
+      if (t >= nchunks) break;
+      const int b = n & 1;
+      const uint32_t tb = tmem + tl + (uint32_t)(b * 128);
+      if (epi_any(!wait_bar(su32(&B.d1full[b]), (unsigned)(n >> 1) & 1u, abort))) break;
+      tc_fence_after();
+      // D1 -> T: K2 = 2b + j', N2 = 64 i + quad
+      if (32 * qr < s.Mp1) {
+#pragma unroll
+        for (int xb = 0; xb < 2; ++xb) {
+          float v[32];
+          tmem_ld32(tb + 32 * xb, v);
+          if (row < Kp2) {
+            const int i = row & 1, k2 = 2 * (row >> 1) + half;
+            const unsigned kofs = (unsigned)(k2 >> 3) * kLboT + (unsigned)(k2 & 7) * 16u;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+              const int ng = 8 * i + 4 * xb + p;
+              *reinterpret_cast<uint4 *>(sT + (size_t)ng * sbo_t + kofs) = pack8(v + 8 * p);
+            }
+          }
+        }
+      }
+      fence_async_smem();
+      tc_fence_before();
+      mbar_arrive(su32(&B.tready));
+      if (epi_any(!wait_bar(su32(&B.d2full[b]), (unsigned)(n >> 1) & 1u, abort))) break;
+      tc_fence_after();
+      // D2 -> O[n % 2] (row R, 16-byte chunk ch at (ch ^ R % 8), the 128-byte
+      // swizzle) -> one TMA store
+      unsigned char *O = base + (b ? P.o1 : P.o0);
+      if (leader) bulk_wait_read1();  // the store from this buffer two chunks ago has read it
+      epi_sync();
+      if (32 * qr < s.Mp2) {
+#pragma unroll
+        for (int xb = 0; xb < 2; ++xb) {
+          float v[32];
+          tmem_ld32(tb + 32 * xb, v);
+          if (row < orows) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+              const int ch = 4 * xb + p;
+              *reinterpret_cast<uint4 *>(O + (size_t)R * 128 + ((ch ^ (R & 7)) << 4)) =
+                  pack8(v + 8 * p);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(su32(&B.dfree[b]));
+      fence_async_smem();
+      epi_sync();
+      if (leader) {
+        const int64_t c = t / cpr, q0 = (t % cpr) * kQ;
+        tma_store5(&tout, su32(O), (int)(q0 & lowmask), 0, (int)(c * s.r2), 0,
+                   (int)(q0 >> s.k));
+        bulk_commit();
+      }
+    }
+    if (leader) bulk_wait_all();  // output stores complete before the CTA exits
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kMmaWarp) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+  if (tid == 0 && *abort) atomicCAS(&g_tc_status, 0, (int)QTT_ERR_TIMEOUT);
+}
+
+constexpr size_t kSmemLimit = 227 * 1024;
+
+// 5-D view of a planar BF16 buffer [P][N] for the pair at bit k: dims (x:
+// bits 0..k-1, a: bit `b1`, P, b: bit `b3`, hi: bits k+2..), box (64, 2, box_p,
+// 2, 1), 128-byte swizzle.  Returns false if the driver rejects it.
+bool encode_view(CUtensorMap *m, const void *ptr, int k, int64_t N, int64_t planes, int b1,
+                 int b3, int box_p) {
+  const cuuint64_t dims[5] = {(cuuint64_t)1 << k, 2, (cuuint64_t)planes, 2,
+                              (cuuint64_t)(N >> (k + 2))};
+  const cuuint64_t strides[4] = {((cuuint64_t)1 << b1) * 2, (cuuint64_t)N * 2,
+                                 ((cuuint64_t)1 << b3) * 2, ((cuuint64_t)1 << (k + 2)) * 2};
+  const cuuint32_t box[5] = {64, 2, (cuuint32_t)box_p, 2, 1};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return cuTensorMapEncodeTiled(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(ptr),
+                                dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tc2_steps_eligible(int k, int r0, int r1, int r2, int64_t N) {
+  // k >= 6: 64 quads are 64 contiguous positions; r0 % 8 == 0: the input box
+  // is exactly the MMA's padded K; ranks <= 56: three ring stages fit
+  return k >= 6 && (int64_t)1 << (k + 2) < N && r0 % 8 == 0 && r0 >= 8 && r1 >= 8 && r2 >= 8 &&
+         r0 <= kTc2MaxRank && r1 <= kTc2MaxRank && r2 <= kTc2MaxRank;
+}
+
+cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st) {
+  // one CTA per SM with as many ring stages as its shared memory holds
+  static cudaError_t attr = cudaFuncSetAttribute(
+      step_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+  if (attr != cudaSuccess) return attr;
+  const Plan p0 = make_plan(s, 0);
+  if (p0.end + 3 * p0.stage + 1024 > kSmemLimit) return cudaErrorNotSupported;
+  int S = (int)((kSmemLimit - 1024 - p0.end) / p0.stage);
+  if (S > kMaxStages) S = kMaxStages;
+  const size_t smem = make_plan(s, S).end + 1024;
+  // the input view needs the buffer to hold exactly nrhs right-hand sides of r_k
+  // planes each, back to back (as the apply's scratch does)
+  if (s.in_rhs_stride != (int64_t)s.r0 * s.N || s.out_rhs_stride != (int64_t)s.r2 * s.N)
+    return cudaErrorNotSupported;
+  CUtensorMap tin, tout;
+  if (!encode_view(&tin, s.in, s.k, s.N, s.nrhs * s.r0, s.k, s.k + 1, s.r0) ||
+      !encode_view(&tout, s.out, s.k, s.N, s.nrhs * s.r2, s.k + 1, s.k, s.r2))
+    return cudaErrorNotSupported;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t nchunks = (s.N >> 2) / kQ * s.nrhs;
+  int64_t grid = sms;
+  if (grid > nchunks) grid = nchunks;
+  step_tc2_kernel<<<(unsigned)grid, kThreads, smem, st>>>(tin, tout, s, S);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_status_take(int *status) {
+  int zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(status, g_tc_status, sizeof(int));
+  if (e == cudaSuccess && *status != 0) e = cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int));
+  return e;
+}
+
+}  // namespace qtt

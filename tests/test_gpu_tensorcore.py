@@ -1,6 +1,7 @@
-"""The BF16 tensor-core steps (mma.sync, FP32 accumulate): the single step
-used for k >= 3 and ranks in [4, 64], and the fused pair of steps used for
-k >= 3, k + 2 < d and ranks in [16, 48].  Exact on integer data and within
+"""The BF16 tensor-core steps (FP32 accumulate): the single mma.sync step
+used for k >= 3 and ranks in [4, 64], and the fused pair of steps (TMA +
+tcgen05 with a TMEM accumulator for k >= 6, r_k % 8 == 0 and ranks in
+[8, 56], else mma.sync for k >= 3 and ranks in [16, 48]), k + 2 < d.  Exact on integer data and within
 the BF16 error bound otherwise, including partial chunks, uneven rank
 profiles and many right-hand sides."""
 import math
@@ -74,6 +75,9 @@ def test_bf16_error_bound_tensor_cores(qtt, d, rmax, nrhs):
     ([1, 2, 4, 8, 17, 33, 20, 1], 2),                        # d=7: ragged ranks, 32 quads
     ([1, 2, 4, 8, 48, 24, 48, 40, 19, 16, 9, 1], 4),         # d=11: pairs (3,4),(5,6),(7,8)
     ([1, 2, 4, 8, 16, 48, 48, 48, 48, 48, 48, 48, 48, 1], 1),
+    ([1, 2, 4, 8, 8, 8, 9, 64, 64, 64, 12, 1], 2),           # ranks 8 and 64 (M = 128 full)
+    ([1, 2, 4, 8, 16, 32, 56, 40, 56, 24, 8, 8, 1], 3),      # TMA pairs at k = 6, 8
+    ([1, 2, 4, 8, 8, 8, 8, 8, 8, 8, 8, 1], 2),               # TMA pairs of rank 8
 ])
 def test_fused_pairs_integer_exact(qtt, ranks, nrhs):
     """Uneven rank profiles through the fused pair kernel: every padded
@@ -84,6 +88,7 @@ def test_fused_pairs_integer_exact(qtt, ranks, nrhs):
     x = np.random.default_rng(d).integers(-1, 2, size=(nrhs, 1 << d)).astype(np.float64)
     op = qtt.Operator(data, packs=("bf16",))
     y = op.apply(torch.from_numpy(x).float().cuda(), compute="bf16").double().cpu().numpy()
+    qtt.sync_status()  # no bounded wait of a tensor-core kernel gave up
     op.close()
     assert np.array_equal(y, oracle.apply(data, x))
 
