@@ -77,7 +77,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcuda"])
+        run([nvcc(), "-shared", "-o", tmp] + objs + ARCH)
         os.replace(tmp, LIB)
     return LIB
 
