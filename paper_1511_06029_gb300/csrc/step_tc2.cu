@@ -10,15 +10,17 @@
 //   stage S   (B of step k, MN-major, 128-byte swizzle): K rows 2a + j_k,
 //             N columns 64 j_{k+1} + quad -- one TMA box of the input planes
 //   D1 = M_k S      in TMEM: lanes 2b + i_k, columns 64 j_{k+1} + quad
-//   T         (B of step k+1, MN-major, no swizzle): K rows 2b + j_{k+1},
-//             N columns 64 i_k + quad   (D1 rounded to BF16 -- the rounding
-//             the unfused path applies when it stores y_{k+1})
+//   T         (B of step k+1, MN-major, 128-byte swizzle): K rows
+//             2b + j_{k+1}, N columns 64 i_k + quad   (D1 rounded to BF16 --
+//             the rounding the unfused path applies when it stores y_{k+1})
 //   D2 = M_{k+1} T  in TMEM: lanes 2c + i_{k+1}, columns 64 i_k + quad
 //   O         output tile, rows (i_k, c, i_{k+1}) of 64 quads (128-byte
 //             swizzle) -- one TMA box store into y_{k+2}
 // Both MMAs are M = 128 (rows 2b + i; rows past 2 r are padding whose
 // results are never read), N = 128, K = 16 per instruction.  M_k and M_{k+1}
-// stay in shared memory for the CTA's lifetime (K-major, no swizzle).
+// stay in shared memory for the CTA's lifetime (K-major, 128-byte swizzle).
+// Every operand is swizzled: the unswizzled core-matrix layouts measured
+// about 10 % slower (bank conflicts in the tensor core's operand reads).
 //
 // TMA boxes.  With k >= 6 the 64 quads of a chunk are 64 consecutive
 // positions in each of the four (j_k, j_{k+1}) slices, and the planes of all
@@ -34,7 +36,9 @@
 //   warp 0      one lane issues the TMA loads into a ring of S stages
 //   warp 1      allocates TMEM; one lane issues the MMAs: MMA1 of chunk n
 //               (frees its stage on completion) ahead of MMA2 of chunk n-1
-//   warps 2-9   epilogue: D1 -> T; D2 -> O (double buffered) -> TMA store
+//   warps 2-17  two epilogue groups of eight warps; group g takes the chunks
+//               n = g (mod 2): D1 -> T[g]; D2 -> O[g] -> TMA store.  While
+//               one group waits for its MMA, the other works.
 // TMEM holds two accumulator buffers of 128 columns (chunk n uses n % 2;
 // D2 overwrites D1 of the same chunk once the epilogue has read it).
 //
@@ -58,14 +62,14 @@ namespace {
 constexpr int kProducerWarp = 0;
 constexpr int kMmaWarp = 1;
 constexpr int kEpiWarp0 = 2;
-constexpr int kEpilogue = 256;             // warps 2-9
-constexpr int kThreads = 64 + kEpilogue;
+constexpr int kEpilogue = 256;             // threads of one epilogue group
+constexpr int kGroups = 2;                 // warps 2-9 and 10-17
+constexpr int kThreads = 64 + kGroups * kEpilogue;
 constexpr int kQ = 64;                     // quads per chunk
 constexpr int kCols = 2 * kQ;              // N of both MMAs
 constexpr int kMaxStages = 8;
 constexpr int kBarBytes = 256;             // mbarriers, TMEM address, abort flag
 constexpr int kTmemCols = 256;             // two accumulator buffers
-constexpr unsigned kLboT = 144;            // T: K-group stride (16-byte pad: no bank conflicts)
 constexpr long long kWaitBudget = 4000000000LL;  // clock64 ticks (about 2 s)
 
 __device__ __forceinline__ unsigned su32(const void *p) {
@@ -176,23 +180,24 @@ __device__ __forceinline__ void expect_tx(unsigned mbar, unsigned bytes) {
 __device__ __forceinline__ void bulk_commit() {
   asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
 }
-__device__ __forceinline__ void bulk_wait_read1() {
-  asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+__device__ __forceinline__ void bulk_wait_read0() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
 }
 // Barrier of the epilogue warps that also ORs a flag over them: the abort
 // decision stays uniform, so no epilogue thread is left at a barrier.
-__device__ __forceinline__ bool epi_any(bool v) {
+// (Named barrier 1 + g belongs to epilogue group g.)
+__device__ __forceinline__ bool epi_any(bool v, int g) {
   unsigned r;
   asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n"
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n"
       " selp.u32 %0, 1, 0, q;\n}\n"
       : "=r"(r)
-      : "r"((unsigned)v), "n"(kEpilogue)
+      : "r"((unsigned)v), "r"(1 + g), "n"(kEpilogue)
       : "memory");
   return r != 0;
 }
-__device__ __forceinline__ void epi_sync() {
-  asm volatile("bar.sync 1, %0;\n" ::"n"(kEpilogue) : "memory");
+__device__ __forceinline__ void epi_sync(int g) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(1 + g), "n"(kEpilogue) : "memory");
 }
 __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
@@ -214,7 +219,7 @@ __device__ __forceinline__ uint4 pack8(const float *v) {
 
 struct Bars {
   unsigned long long full[kMaxStages], empty[kMaxStages];
-  unsigned long long d1full[2], d2full[2], dfree[2], tready;
+  unsigned long long d1full[2], d2full[2], dfree[2], tready[2];
   uint32_t tmem;
   int abort;
 };
@@ -237,20 +242,33 @@ __device__ __forceinline__ bool wait_bar(unsigned a, unsigned parity, volatile i
 }
 
 // Shared-memory plan (byte offsets from a 1024-aligned base).
+// Core matrix M (Mp x Kp) as the K-major operand, 128-byte swizzle: K in
+// atoms of 64 (Mp rows of 128 bytes each), row r of atom ka at
+// ka Mp 128 + r 128, its 16-byte chunk c at (c ^ r % 8).
+__host__ __device__ inline unsigned a_bytes(int Mp, int Kp) {
+  return (unsigned)((Kp + 63) / 64) * (unsigned)Mp * 128u;
+}
+__device__ __forceinline__ unsigned a_offset(int Mp, int r, int kc) {
+  return (unsigned)(kc >> 3) * (unsigned)Mp * 128u + (unsigned)r * 128u +
+         ((unsigned)((kc & 7) ^ (r & 7)) << 4);
+}
+
 struct Plan {
-  unsigned a1, a2, t, o0, o1, s0, stage, obytes, end;
+  unsigned a1, a2, t0, t1, o0, o1, s0, stage, obytes, end;
 };
 __host__ __device__ inline unsigned up1k(unsigned v) { return (v + 1023u) & ~1023u; }
 __host__ __device__ inline Plan make_plan(const StepMMA2 &s, int S) {
   Plan p;
   const unsigned Kp2 = (unsigned)s.Mp1;
-  p.a1 = kBarBytes;
-  p.a2 = p.a1 + (unsigned)(s.Mp1 * s.Kp1 * 2);
-  p.t = p.a2 + (unsigned)(s.Mp2 * s.Mp1 * 2);
-  // O and the stages follow T: the M = 128 padding rows of M_{k+1} read past
-  // A2 into T (finite data; those rows are never used)
+  // every tile 1024-aligned (the 128-byte swizzle repeats every 8 rows)
+  p.a1 = up1k(kBarBytes);
+  p.a2 = up1k(p.a1 + a_bytes(s.Mp1, s.Kp1));
+  // T[0] follows A2: the M = 128 padding rows of M_{k+1} read past A2 into
+  // it (finite data; those rows are never used)
+  p.t0 = up1k(p.a2 + a_bytes(s.Mp2, (int)Kp2));
+  p.t1 = p.t0 + 2u * Kp2 * 128u;
   p.obytes = (unsigned)(2 * 2 * s.r2 * 128);
-  p.o0 = up1k(p.t + 16u * (Kp2 / 8u) * kLboT);
+  p.o0 = up1k(p.t1 + 2u * Kp2 * 128u);
   p.o1 = up1k(p.o0 + p.obytes);
   p.stage = (unsigned)(s.Kp1 * kCols * 2);
   p.s0 = up1k(p.o1 + p.obytes);
@@ -267,8 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const Plan P = make_plan(s, S);
   Bars &B = *reinterpret_cast<Bars *>(base);
   const int Kp2 = s.Mp1;
-  const unsigned sbo_t = (unsigned)(Kp2 / 8) * kLboT;
-  unsigned char *sA1 = base + P.a1, *sA2 = base + P.a2, *sT = base + P.t;
+  unsigned char *sA1 = base + P.a1, *sA2 = base + P.a2;
   const unsigned base32 = su32(base);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -289,22 +306,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(su32(&B.d1full[i]), 1);
       mbar_init(su32(&B.d2full[i]), 1);
       mbar_init(su32(&B.dfree[i]), kEpilogue);
+      mbar_init(su32(&B.tready[i]), kEpilogue);
     }
-    mbar_init(su32(&B.tready), kEpilogue);
     B.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  // core matrices, K-major core-matrix layout: (row, k) at
-  // (row / 8) Kp 16 + (k / 8) 128 + (row % 8) 16 + (k % 8) 2 bytes
+  // core matrices as swizzled K-major operands (16-byte pieces of 8 columns)
   for (int e = tid; e < s.Mp1 * (s.Kp1 / 8); e += kThreads) {
-    const int r = e / (s.Kp1 / 8), kg = e % (s.Kp1 / 8);
-    cpa16(su32(sA1 + (size_t)(r >> 3) * s.Kp1 * 16 + kg * 128 + (r & 7) * 16),
-          s.A1 + (size_t)r * s.Kp1 + 8 * kg, 16);
+    const int r = e / (s.Kp1 / 8), kc = e % (s.Kp1 / 8);
+    cpa16(su32(sA1 + a_offset(s.Mp1, r, kc)), s.A1 + (size_t)r * s.Kp1 + 8 * kc, 16);
   }
   for (int e = tid; e < s.Mp2 * (Kp2 / 8); e += kThreads) {
-    const int r = e / (Kp2 / 8), kg = e % (Kp2 / 8);
-    cpa16(su32(sA2 + (size_t)(r >> 3) * Kp2 * 16 + kg * 128 + (r & 7) * 16),
-          s.A2 + (size_t)r * Kp2 + 8 * kg, 16);
+    const int r = e / (Kp2 / 8), kc = e % (Kp2 / 8);
+    cpa16(su32(sA2 + a_offset(s.Mp2, r, kc)), s.A2 + (size_t)r * Kp2 + 8 * kc, 16);
   }
   cpa_commit();
   cpa_wait<0>();
@@ -346,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------------- MMA issue
     if (lane == 0) {
-      const unsigned a1 = base32 + P.a1, a2 = base32 + P.a2, t32 = base32 + P.t;
+      const unsigned a1 = base32 + P.a1, a2 = base32 + P.a2;
       for (int n = 0;; ++n) {
         const int64_t t = blockIdx.x + (int64_t)n * G;
         const bool has = t < nchunks;
@@ -358,18 +372,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const unsigned sb = base32 + P.s0 + (unsigned)st * P.stage;
           for (int ks = 0; ks < s.Kp1 / 16; ++ks)
-            mma_bf16(tmem + (uint32_t)(b * 128), smem_desc(a1 + ks * 256, 128, s.Kp1 * 16),
+            mma_bf16(tmem + (uint32_t)(b * 128),
+                     smem_desc(a1 + (ks >> 2) * s.Mp1 * 128 + (ks & 3) * 32, 16, 1024, 2),
                      smem_desc(sb + ks * 2048, (unsigned)s.Kp1 * 128, 1024, 2), ks > 0);
           mma_commit(su32(&B.empty[st]));
           mma_commit(su32(&B.d1full[b]));
         }
         if (n >= 1) {
           const int m = n - 1, bm = m & 1;
-          if (!wait_bar(su32(&B.tready), (unsigned)m & 1u, abort)) break;
+          if (!wait_bar(su32(&B.tready[bm]), (unsigned)(m >> 1) & 1u, abort)) break;
           tc_fence_after();
+          const unsigned t32 = base32 + (bm ? P.t1 : P.t0);
           for (int ks = 0; ks < Kp2 / 16; ++ks)
-            mma_bf16(tmem + (uint32_t)(bm * 128), smem_desc(a2 + ks * 256, 128, Kp2 * 16),
-                     smem_desc(t32 + ks * 2 * kLboT, kLboT, sbo_t), ks > 0);
+            mma_bf16(tmem + (uint32_t)(bm * 128),
+                     smem_desc(a2 + (ks >> 2) * s.Mp2 * 128 + (ks & 3) * 32, 16, 1024, 2),
+                     smem_desc(t32 + ks * 2048, (unsigned)Kp2 * 128, 1024, 2), ks > 0);
           mma_commit(su32(&B.d2full[bm]));
         }
         if (!has) break;
@@ -377,18 +394,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------------------------------------------------------- epilogue
-    const int qr = warp & 3, half = (warp - kEpiWarp0) >> 2;
+    // group g takes the chunks n = g, g + 2, ... (TMEM buffer g, T[g], O[g]),
+    // so one group's epilogue overlaps the other's MMAs
+    const int g = (warp - kEpiWarp0) >> 3;
+    const int qr = warp & 3, half = ((warp - kEpiWarp0) >> 2) & 1;
     const int row = 32 * qr + lane;  // TMEM lane = D row
-    const bool leader = tid == kEpiWarp0 * 32;
+    const bool leader = tid == (kEpiWarp0 + 8 * g) * 32;
+    unsigned char *sT = base + (g ? P.t1 : P.t0);
+    unsigned char *O = base + (g ? P.o1 : P.o0);
     const uint32_t tl = ((uint32_t)(32 * qr) << 16) + (uint32_t)(64 * half);
     const int orows = 2 * s.r2;
     const int R = half * orows + row;  // output tile row (i_k, c, i_{k+1})
-    for (int n = 0;; ++n) {
+    for (int n = g;; n += kGroups) {
       const int64_t t = blockIdx.x + (int64_t)n * G;
       if (t >= nchunks) break;
-      const int b = n & 1;
+      const int b = g;
       const uint32_t tb = tmem + tl + (uint32_t)(b * 128);
-      if (epi_any(!wait_bar(su32(&B.d1full[b]), (unsigned)(n >> 1) & 1u, abort))) break;
+      if (epi_any(!wait_bar(su32(&B.d1full[b]), (unsigned)(n >> 1) & 1u, abort), g)) break;
       tc_fence_after();
       // D1 -> T: K2 = 2b + j', N2 = 64 i + quad
       if (32 * qr < s.Mp1) {
@@ -398,25 +420,23 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld32(tb + 32 * xb, v);
           if (row < Kp2) {
             const int i = row & 1, k2 = 2 * (row >> 1) + half;
-            const unsigned kofs = (unsigned)(k2 >> 3) * kLboT + (unsigned)(k2 & 7) * 16u;
+            unsigned char *trow = sT + (size_t)i * Kp2 * 128 + (size_t)k2 * 128;
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              const int ng = 8 * i + 4 * xb + p;
-              *reinterpret_cast<uint4 *>(sT + (size_t)ng * sbo_t + kofs) = pack8(v + 8 * p);
-            }
+            for (int p = 0; p < 4; ++p)
+              *reinterpret_cast<uint4 *>(trow + (((4 * xb + p) ^ (k2 & 7)) << 4)) =
+                  pack8(v + 8 * p);
           }
         }
       }
       fence_async_smem();
       tc_fence_before();
-      mbar_arrive(su32(&B.tready));
-      if (epi_any(!wait_bar(su32(&B.d2full[b]), (unsigned)(n >> 1) & 1u, abort))) break;
+      mbar_arrive(su32(&B.tready[b]));
+      if (epi_any(!wait_bar(su32(&B.d2full[b]), (unsigned)(n >> 1) & 1u, abort), g)) break;
       tc_fence_after();
       // D2 -> O[n % 2] (row R, 16-byte chunk ch at (ch ^ R % 8), the 128-byte
       // swizzle) -> one TMA store
-      unsigned char *O = base + (b ? P.o1 : P.o0);
-      if (leader) bulk_wait_read1();  // the store from this buffer two chunks ago has read it
-      epi_sync();
+      if (leader) bulk_wait_read0();  // the group's previous store has read O
+      epi_sync(g);
       if (32 * qr < s.Mp2) {
 #pragma unroll
         for (int xb = 0; xb < 2; ++xb) {
@@ -435,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       mbar_arrive(su32(&B.dfree[b]));
       fence_async_smem();
-      epi_sync();
+      epi_sync(g);
       if (leader) {
         const int64_t c = t / cpr, q0 = (t % cpr) * kQ;
         tma_store5(&tout, su32(O), (int)(q0 & lowmask), 0, (int)(c * s.r2), 0,
@@ -492,7 +512,7 @@ bool encode_view(CUtensorMap *m, const void *ptr, int k, int64_t N, int64_t plan
 
 bool tc2_steps_eligible(int k, int r0, int r1, int r2, int64_t N) {
   // k >= 6: 64 quads are 64 contiguous positions; r0 % 8 == 0: the input box
-  // is exactly the MMA's padded K; ranks <= 56: three ring stages fit
+  // is exactly the MMA's padded K; ranks <= 56: two ring stages fit
   return k >= 6 && (int64_t)1 << (k + 2) < N && r0 % 8 == 0 && r0 >= 8 && r1 >= 8 && r2 >= 8 &&
          r0 <= kTc2MaxRank && r1 <= kTc2MaxRank && r2 <= kTc2MaxRank;
 }
@@ -503,7 +523,7 @@ cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st) {
       step_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
   if (attr != cudaSuccess) return attr;
   const Plan p0 = make_plan(s, 0);
-  if (p0.end + 3 * p0.stage + 1024 > kSmemLimit) return cudaErrorNotSupported;
+  if (p0.end + 2 * p0.stage + 1024 > kSmemLimit) return cudaErrorNotSupported;
   int S = (int)((kSmemLimit - 1024 - p0.end) / p0.stage);
   if (S > kMaxStages) S = kMaxStages;
   const size_t smem = make_plan(s, S).end + 1024;
