@@ -351,14 +351,22 @@ class ApplyRun:
         return float(sum(d.ranks[k] + d.ranks[k + 1] for k in range(d.d)) * d.N * self.nrhs * es)
 
     def fused_bytes(self):
-        """Bytes the BF16 launches must move: a fused pair of tensor-core
-        steps (k, k+1) reads r_k and writes r_{k+2} planes, the planes between
-        them stay on chip; every other step reads r_k and writes r_{k+1}.
+        """Bytes the BF16 launches must move: the head kernel (first m steps)
+        reads r_0 and writes r_m planes; a fused pair of tensor-core steps
+        (k, k+1) reads r_k and writes r_{k+2} planes, the planes between them
+        stay on chip; every other step reads r_k and writes r_{k+1}.
         The pairing rule is the library's: k + 2 < d and either the TMA +
         tcgen05 pair (k >= 6, r_k % 8 == 0, ranks in [8, 56]) or the mma.sync
         pair (k >= 3, ranks in [16, 48])."""
         d, ks, b, k = self.data, [], 0.0, 0
         r = d.ranks
+        m = 0  # the head kernel: steps 0 .. m-1 (m = 2 or 3) with r_1 .. r_m <= 8
+        while m < 3 and m + 1 < d.d and r[m + 1] <= 8:
+            m += 1
+        if m >= 2:
+            b += r[0] + r[m]
+            ks.append(tuple(range(m)))
+            k = m
         while k < d.d:
             tc2 = k >= 6 and r[k] % 8 == 0 and all(8 <= r[k + t] <= 56 for t in range(3)) \
                 if k + 2 < d.d else False

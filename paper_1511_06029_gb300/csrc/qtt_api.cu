@@ -202,11 +202,12 @@ static bool use_staged_f32() {
   return on;
 }
 
-// Pairs of tensor-core steps fused into one launch (QTT_NO_FUSED_MMA=1 keeps
-// one launch per step, for comparison).
-static bool use_fused_mma() {
+// Several steps per launch -- the head kernel for the first steps, pairs of
+// tensor-core steps (QTT_NO_FUSION=1 keeps one launch per step, for
+// comparison).
+static bool use_fusion() {
   static const bool on = [] {
-    const char *v = std::getenv("QTT_NO_FUSED_MMA");
+    const char *v = std::getenv("QTT_NO_FUSION");
     return !(v && *v && *v != '0');
   }();
   return on;
@@ -267,8 +268,36 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
   for (int64_t c0 = 0; c0 < nrhs; c0 += chunk) {
     const int64_t nc = std::min<int64_t>(chunk, nrhs - c0);
     int src = 0;  // scratch half holding the current intermediate (k >= 1)
-    for (int k = 0; k < d; ++k) {
-      const bool pair = tc && use_fused_mma() && k + 2 < d && A->mp[k] && A->mp[k + 1];
+    int k0 = 0;
+    const int hm = use_fusion() ? head_steps(A->ranks.data(), d) : 0;
+    if (hm) {
+      // steps 0 .. hm-1 in one launch; y_hm lands in scratch half 0
+      StepHead h;
+      std::memset(&h, 0, sizeof(h));
+      h.in = static_cast<const char *>(x) + (size_t)c0 * ld * xsz;
+      h.in_rhs_stride = ld;
+      h.out = buf[0];
+      h.out_rhs_stride = (int64_t)A->ranks[hm] * N;
+      for (int k = 0; k < hm; ++k)
+        h.M[k] = static_cast<const char *>(cores) + (size_t)A->offlp[k] * core_esz;
+      for (int k = 0; k <= hm; ++k) {
+        h.r[k] = A->ranks[k];
+        h.rpad[k] = A->rpad[k];
+      }
+      h.N = N;
+      h.nrhs = nc;
+      h.m = hm;
+      h.mode = mode;
+      h.in_type = xt;
+      const cudaError_t e = launch_step_head(h, st);
+      if (e != cudaSuccess) {
+        scratch_free(scratch, st);
+        return cuda_fail(e, "head step launch");
+      }
+      k0 = hm;
+    }
+    for (int k = k0; k < d; ++k) {
+      const bool pair = tc && use_fusion() && k + 2 < d && A->mp[k] && A->mp[k + 1];
       const bool tc5 = pair && use_tcgen05() &&
                        tc2_steps_eligible(k, A->ranks[k], A->ranks[k + 1], A->ranks[k + 2], N);
       const bool mma2 =

@@ -1,0 +1,208 @@
+// The first m core steps (m = 2 or 3, every rank r_1 .. r_m <= 8) of a
+// reduced-precision apply in one launch.
+//
+// Steps 0 .. m-1 of Algorithm 2 mix only position bits 0 .. m-1, so the 2^m
+// consecutive positions 2^m g .. 2^m g + 2^m - 1 are closed under them.  Two
+// lanes share a group (2^(m-1) positions each): steps 0 .. m-2 run in each
+// lane's registers, step m-1 (bit m-1 = the lane parity) exchanges the
+// partner's half with one shuffle per value.  Each lane writes r_m planes of
+// 2^(m-1) values (one vector store each).  The apply reads x once and writes
+// y_m once instead of moving y_1 .. y_{m-1} through HBM, and a warp's
+// accesses are contiguous.
+//
+// Numerics are those of the one-step kernel (step_lp.cu) step by step: the
+// input rounded to the mode's precision when read, each intermediate rounded
+// to it (BF16 or TF32) as the one-step kernel stores it, FP32 sums over
+// (a, j) in the same order -- so the result is bitwise that of m separate
+// launches.
+#include <cuda_bf16.h>
+
+#include "qtt_internal.h"
+#include "step_lp.h"
+
+namespace qtt {
+namespace {
+
+constexpr int kR = kHeadMaxRank;  // register tile bound on every rank
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float tf32_rne(float x) {
+  unsigned u = __float_as_uint(x);
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0x0fffu + ((u >> 13) & 1u);
+    u &= 0xffffe000u;
+  }
+  return __uint_as_float(u);
+}
+template <int MODE>
+__device__ __forceinline__ float round_mode(float v) {
+  if (MODE == LP_TF32) return tf32_rne(v);
+  if (MODE == LP_BF16) return __bfloat162float(__float2bfloat16_rn(v));
+  return v;
+}
+__device__ __forceinline__ float to_f(double v) { return (float)v; }
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+// T consecutive values as one vector store (T = 2 or 4; the scratch planes
+// are 16-byte aligned and T divides every plane offset used).
+template <int T>
+__device__ __forceinline__ void store_vec(float *o, const float *v) {
+  if (T == 4)
+    *reinterpret_cast<float4 *>(o) = make_float4(v[0], v[1], v[2], v[3]);
+  else
+    *reinterpret_cast<float2 *>(o) = make_float2(v[0], v[1]);
+}
+template <int T>
+__device__ __forceinline__ void store_vec(__nv_bfloat16 *o, const float *v) {
+  __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]);
+  if (T == 4) {
+    __nv_bfloat162 h1 = __floats2bfloat162_rn(v[2], v[3]);
+    *reinterpret_cast<uint2 *>(o) =
+        make_uint2(*reinterpret_cast<unsigned *>(&h0), *reinterpret_cast<unsigned *>(&h1));
+  } else {
+    *reinterpret_cast<__nv_bfloat162 *>(o) = h0;
+  }
+}
+
+template <int MODE, typename TIN, typename TMID, typename TCORE, int M>
+__global__ void __launch_bounds__(kThreads, 2) step_head_kernel(StepHead s) {
+  constexpr int P = 1 << M;   // positions of a group
+  constexpr int T = P / 2;    // positions per thread: two lanes share a group
+  __shared__ float sG[3][4 * kR * kR];
+  // cores of steps 0 .. M-1 from the packed [a][j][b padded][i] layout
+  for (int k = 0; k < M; ++k) {
+    const TCORE *G = static_cast<const TCORE *>(s.M[k]);
+    const int n = 2 * s.r[k] * 2 * s.rpad[k + 1];
+    for (int e = threadIdx.x; e < n; e += blockDim.x) sG[k][e] = to_f(G[e]);
+  }
+  __syncthreads();
+  // lane pair (2 g, 2 g + 1) holds group g: the lane with h = 1 the positions
+  // with bit M-1 set.  Inactive lanes (past the end) still take part in the
+  // shuffles of the last step.
+  const int64_t groups = s.N >> M;
+  const int64_t tidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = tidx < 2 * groups;
+  const int h = (int)(tidx & 1);
+  const int64_t c = blockIdx.y;
+  const int64_t pbase = (tidx >> 1) * P + h * T;  // first position of this thread
+  float y[kR][T], z[kR][T];
+  {
+    const TIN *in = static_cast<const TIN *>(s.in) + c * s.in_rhs_stride + pbase;
+#pragma unroll
+    for (int q = 0; q < T; ++q) y[0][q] = active ? round_mode<MODE>(to_f(in[q])) : 0.0f;
+  }
+  int rin = 1;
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    const int rout = s.r[k + 1], rpad = s.rpad[k + 1];
+    const float *G = sG[k];
+#pragma unroll
+    for (int b = 0; b < kR; ++b)
+#pragma unroll
+      for (int q = 0; q < T; ++q) z[b][q] = 0.0f;
+    if (k < M - 1) {
+      // bit k lies inside the thread's T positions
+#pragma unroll
+      for (int a = 0; a < kR; ++a) {
+        if (a >= rin) break;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+#pragma unroll
+          for (int b = 0; b < kR; ++b) {
+            if (b >= rout) break;
+            const float g0 = G[((2 * a + j) * rpad + b) * 2];
+            const float g1 = G[((2 * a + j) * rpad + b) * 2 + 1];
+#pragma unroll
+            for (int q = 0; q < T; ++q) {
+              if (((q >> k) & 1) != 0) continue;  // q = pair base (bit k clear)
+              const float v = y[a][q | (j << k)];
+              z[b][q] = fmaf(g0, v, z[b][q]);
+              z[b][q | (1 << k)] = fmaf(g1, v, z[b][q | (1 << k)]);
+            }
+          }
+        }
+      }
+    } else {
+      // bit M-1 is the lane parity: the partner lane holds the other half;
+      // every output of this lane has i = h
+#pragma unroll
+      for (int a = 0; a < kR; ++a) {
+        if (a >= rin) break;  // uniform over the warp: rin is the same everywhere
+        float other[T];
+#pragma unroll
+        for (int q = 0; q < T; ++q) other[q] = __shfl_xor_sync(0xffffffffu, y[a][q], 1);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+#pragma unroll
+          for (int b = 0; b < kR; ++b) {
+            if (b >= rout) break;
+            const float g = G[((2 * a + j) * rpad + b) * 2 + h];
+#pragma unroll
+            for (int q = 0; q < T; ++q) z[b][q] = fmaf(g, j == h ? y[a][q] : other[q], z[b][q]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < kR; ++b)
+#pragma unroll
+      for (int q = 0; q < T; ++q) y[b][q] = round_mode<MODE>(z[b][q]);
+    rin = rout;
+  }
+  if (!active) return;
+  TMID *out = static_cast<TMID *>(s.out) + c * s.out_rhs_stride + pbase;
+#pragma unroll
+  for (int b = 0; b < kR; ++b) {
+    if (b >= rin) break;
+    store_vec<T>(out + (int64_t)b * s.N, y[b]);
+  }
+}
+
+template <int MODE, typename TIN, typename TMID, typename TCORE>
+cudaError_t launch_m(const StepHead &s, cudaStream_t st) {
+  const int64_t groups = s.N >> s.m;
+  const unsigned gx = (unsigned)((2 * groups + kThreads - 1) / kThreads);
+  for (int64_t c0 = 0; c0 < s.nrhs; c0 += 65535) {
+    StepHead t = s;
+    const int64_t nc = (s.nrhs - c0) < 65535 ? (s.nrhs - c0) : 65535;
+    t.in = static_cast<const TIN *>(s.in) + c0 * s.in_rhs_stride;
+    t.out = static_cast<TMID *>(s.out) + c0 * s.out_rhs_stride;
+    if (s.m == 2)
+      step_head_kernel<MODE, TIN, TMID, TCORE, 2><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
+    else
+      step_head_kernel<MODE, TIN, TMID, TCORE, 3><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
+    count_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <int MODE, typename TMID, typename TCORE>
+cudaError_t by_input(const StepHead &s, cudaStream_t st) {
+  switch (s.in_type) {
+    case QTT_F64: return launch_m<MODE, double, TMID, TCORE>(s, st);
+    case QTT_BF16: return launch_m<MODE, __nv_bfloat16, TMID, TCORE>(s, st);
+    default: return launch_m<MODE, float, TMID, TCORE>(s, st);
+  }
+}
+
+}  // namespace
+
+int head_steps(const int *ranks, int d) {
+  int m = 0;
+  while (m < 3 && m + 1 < d && ranks[m + 1] <= kHeadMaxRank) ++m;
+  return m >= 2 ? m : 0;
+}
+
+cudaError_t launch_step_head(const StepHead &s, cudaStream_t st) {
+  if (s.m < 2 || s.m > 3) return cudaErrorInvalidValue;
+  switch (s.mode) {
+    case LP_F32: return by_input<LP_F32, float, float>(s, st);
+    case LP_TF32: return by_input<LP_TF32, float, float>(s, st);
+    case LP_BF16: return by_input<LP_BF16, __nv_bfloat16, __nv_bfloat16>(s, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace qtt

@@ -38,6 +38,24 @@ struct StepLP {
 int lp_rank_pad(int r);
 cudaError_t launch_step_lp(const StepLP &s, cudaStream_t st);
 
+// The first m = 2 or 3 steps in one launch (step_head.cu), when r_1 .. r_m
+// are all <= kHeadMaxRank: reads x once, writes y_m.
+constexpr int kHeadMaxRank = 8;
+struct StepHead {
+  const void *in;          // x, element type in_type, rhs stride in elements
+  int64_t in_rhs_stride;
+  void *out;               // y_m (intermediate type of the mode), planar
+  int64_t out_rhs_stride;
+  const void *M[3];        // packed cores 0 .. m-1 (as for StepLP)
+  int r[4], rpad[4];       // ranks r_0 .. r_m and their padded widths
+  int64_t N, nrhs;
+  int m, mode;
+  qtt_dtype in_type;
+};
+// Steps the head kernel takes for this rank profile (0: none).
+int head_steps(const int *ranks, int d);
+cudaError_t launch_step_head(const StepHead &s, cudaStream_t st);
+
 // Staged (cp.async, persistent) FP32/TF32 step for intermediate-to-
 // intermediate steps with k >= 2 -- see step_f32s.cu.
 bool f32s_step_eligible(const StepLP &s);

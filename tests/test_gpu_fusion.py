@@ -1,0 +1,86 @@
+"""Multi-step launches against one launch per step.
+
+The head kernel (steps 0 .. m-1 in registers, ranks <= 8) follows the
+one-step kernel's numerics step by step, so its result must be bitwise the
+unfused one in every reduced precision and for every input type.  The
+unfused reference runs in a child process with QTT_NO_FUSION=1 (the switch
+is read once per process); one child computes every case."""
+import itertools
+import os
+import pickle
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from paper_1511_06029_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TORCH = {"f64": "float64", "f32": "float32", "bf16": "bfloat16"}
+
+CASES = [
+    ([1, 2, 4, 8, 6, 1], 3),        # head of 3 steps, then 2 single steps
+    ([1, 3, 5, 7, 2, 1], 2),        # uneven ranks, padded core widths
+    ([1, 2, 4, 1], 4),              # head of 2 steps (d = 3)
+    ([1, 8, 8, 8, 8, 8, 1], 1),     # rank 8 everywhere
+    ([1, 2, 16, 4, 1], 2),          # r_2 > 8: no head (m would be 1)
+]
+GRID = list(itertools.product(range(len(CASES)), ["f32", "tf32", "bf16"], ["f64", "f32", "bf16"]))
+
+CHILD = r"""
+import pickle, sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1511_06029_gb300 import inputs, qtt
+specs = pickle.load(open(sys.argv[2], "rb"))
+outs = []
+for sp in specs:
+    data = inputs.QTTData(sp["ranks"], sp["cores"])
+    op = qtt.Operator(data, packs=(sp["compute"],))
+    x = torch.from_numpy(sp["x"]).cuda().to(getattr(torch, sp["io"]))
+    outs.append(op.apply(x, compute=sp["compute"]).double().cpu().numpy())
+    op.close()
+pickle.dump(outs, open(sys.argv[3], "wb"))
+"""
+
+
+def _spec(case, compute, io):
+    ranks, nrhs = CASES[case]
+    d = len(ranks) - 1
+    data = inputs.random_cores(d, ranks, sum(ranks) + nrhs)
+    x = inputs.gaussian_rhs(data.N, nrhs, d)
+    return {"ranks": ranks, "cores": data.cores, "x": x, "compute": compute, "io": TORCH[io]}
+
+
+@pytest.fixture(scope="module")
+def qtt():
+    from paper_1511_06029_gb300 import build, qtt as q
+    build.build()
+    q.load_library()
+    return q
+
+
+@pytest.fixture(scope="module")
+def unfused(tmp_path_factory):
+    d = tmp_path_factory.mktemp("fusion")
+    spec, out = d / "specs.pkl", d / "unfused.pkl"
+    pickle.dump([_spec(*g) for g in GRID], open(spec, "wb"))
+    env = dict(os.environ, QTT_NO_FUSION="1")
+    r = subprocess.run([sys.executable, "-c", CHILD, ROOT, str(spec), str(out)], env=env,
+                       capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return pickle.load(open(out, "rb"))
+
+
+@pytest.mark.parametrize("idx", range(len(GRID)))
+def test_head_is_bitwise_the_unfused_sweep(qtt, unfused, idx):
+    import torch
+    sp = _spec(*GRID[idx])
+    data = inputs.QTTData(sp["ranks"], sp["cores"])
+    op = qtt.Operator(data, packs=(sp["compute"],))
+    x = torch.from_numpy(sp["x"]).cuda().to(getattr(torch, sp["io"]))
+    fused = op.apply(x, compute=sp["compute"]).double().cpu().numpy()
+    op.close()
+    assert np.array_equal(fused.view(np.uint64), unfused[idx].view(np.uint64))
