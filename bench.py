@@ -356,8 +356,8 @@ class ApplyRun:
         (k, k+1) reads r_k and writes r_{k+2} planes, the planes between them
         stay on chip; every other step reads r_k and writes r_{k+1}.
         The pairing rule is the library's: k + 2 < d and either the TMA +
-        tcgen05 pair (k >= 6, r_k % 8 == 0, ranks in [8, 56]) or the mma.sync
-        pair (k >= 3, ranks in [16, 48])."""
+        tcgen05 pair (k >= 4, N >= 256, r_k % 8 == 0, ranks in [8, 56]) or
+        the mma.sync pair (k >= 3, ranks in [16, 48])."""
         d, ks, b, k = self.data, [], 0.0, 0
         r = d.ranks
         m = 0  # the head kernel: steps 0 .. m-1 (m = 2 or 3) with r_1 .. r_m <= 8
@@ -368,8 +368,8 @@ class ApplyRun:
             ks.append(tuple(range(m)))
             k = m
         while k < d.d:
-            tc2 = k >= 6 and r[k] % 8 == 0 and all(8 <= r[k + t] <= 56 for t in range(3)) \
-                if k + 2 < d.d else False
+            tc2 = k >= 4 and d.N >= 256 and r[k] % 8 == 0 and \
+                all(8 <= r[k + t] <= 56 for t in range(3)) if k + 2 < d.d else False
             mma2 = k >= 3 and all(16 <= r[k + t] <= 48 for t in range(3)) \
                 and (d.N >> 2) % 8 == 0 if k + 2 < d.d else False
             if tc2 or mma2:

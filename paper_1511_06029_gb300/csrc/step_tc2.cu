@@ -22,15 +22,19 @@
 // Every operand is swizzled: the unswizzled core-matrix layouts measured
 // about 10 % slower (bank conflicts in the tensor core's operand reads).
 //
-// TMA boxes.  With k >= 6 the 64 quads of a chunk are 64 consecutive
-// positions in each of the four (j_k, j_{k+1}) slices, and the planes of all
-// right-hand sides form one index P = rhs r + a (stride N), so one 5-D view
-// (x = position bits 0..k-1, j_k, P, j_{k+1}, position bits k+2..) covers the
-// input; its box (64, 2, r_k, 2, 1) lands in shared memory exactly as the
-// MMA's swizzled MN-major operand.  The output view orders (x, i_{k+1}, P,
-// i_k, hi) so that the rows one epilogue warp writes are consecutive in the
-// swizzle pattern.  r_k % 8 == 0 makes the box's K extent 2 r_k the padded
-// K of the MMA, so no plane of a neighbouring right-hand side is read.
+// TMA boxes.  Within a chunk, runs of X = 2^min(k, 6) quads are X
+// consecutive positions in each of the four (j_k, j_{k+1}) slices, and the
+// planes of all right-hand sides form one index P = rhs r + a (stride N), so
+// one 5-D view (x = position bits 0..k-1, j_k, P, j_{k+1}, position bits
+// k+2..) covers the input; its box (X, 2, r_k, 2, 64 / X) lands in shared
+// memory exactly as the MMA's MN-major operand, rows of X values with the
+// swizzle that spans one row (none, 32, 64 or 128 bytes for X = 8 .. 64).
+// The MN order of the stage is then (position bits k+2.., j_{k+1}, x); T and
+// the output tile use (bits k+2.., i_k, x).  The output view orders (x,
+// i_{k+1}, P, i_k, hi) so that the rows one epilogue warp writes are
+// consecutive in the swizzle pattern.  r_k % 8 == 0 makes the box's K extent
+// 2 r_k the padded K of the MMA, so no plane of a neighbouring right-hand
+// side is read.
 //
 // Warp roles, connected by mbarriers (a software pipeline over chunks):
 //   warp 0      one lane issues the TMA loads into a ring of S stages
@@ -276,9 +280,33 @@ __host__ __device__ inline Plan make_plan(const StepMMA2 &s, int S) {
   return p;
 }
 
+// Position runs: X = 2^XLOG quads (XLOG = min(k, 6)) are contiguous, so the
+// tile rows are X values (2 X bytes) wide and the swizzle spans one row:
+// B = XLOG - 3 bits of 16-byte chunk index (none, 32, 64 or 128 bytes).
+template <int XLOG>
+struct Rows {
+  static constexpr int X = 1 << XLOG;
+  static constexpr unsigned bytes = 2u * X;
+  static constexpr int B = XLOG - 3;
+  // descriptor layout code: none 0, 32-byte 6, 64-byte 4, 128-byte 2
+  static constexpr unsigned code = B == 3 ? 2u : B == 2 ? 4u : B == 1 ? 6u : 0u;
+  // physical offset of a logical byte offset from a 1024-aligned tile base
+  __device__ static unsigned swz(unsigned off) {
+    return off ^ (((off >> 7) & ((1u << B) - 1u)) << 4);
+  }
+  // MN-major operand of Kp rows: descriptor for K rows 16 ks .. 16 ks + 15
+  __device__ static uint64_t desc(unsigned tile, int Kp, int ks) {
+    if (B == 0)  // core matrices: K groups 128 bytes apart, MN blocks Kp 16
+      return smem_desc(tile + ks * 256, 128, (unsigned)Kp * 16, 0);
+    return smem_desc(tile + ks * 16 * bytes, (unsigned)Kp * bytes, 8 * bytes, code);
+  }
+};
+
+template <int XLOG>
 __global__ void __launch_bounds__(kThreads, 1)
     step_tc2_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
                     StepMMA2 s, int S) {
+  using Rw = Rows<XLOG>;
   extern __shared__ __align__(1024) unsigned char smraw[];
   // 1024-aligned base for the swizzled tiles
   unsigned char *base = smraw + ((1024u - (su32(smraw) & 1023u)) & 1023u);
@@ -374,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int ks = 0; ks < s.Kp1 / 16; ++ks)
             mma_bf16(tmem + (uint32_t)(b * 128),
                      smem_desc(a1 + (ks >> 2) * s.Mp1 * 128 + (ks & 3) * 32, 16, 1024, 2),
-                     smem_desc(sb + ks * 2048, (unsigned)s.Kp1 * 128, 1024, 2), ks > 0);
+                     Rw::desc(sb, s.Kp1, ks), ks > 0);
           mma_commit(su32(&B.empty[st]));
           mma_commit(su32(&B.d1full[b]));
         }
@@ -386,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int ks = 0; ks < Kp2 / 16; ++ks)
             mma_bf16(tmem + (uint32_t)(bm * 128),
                      smem_desc(a2 + (ks >> 2) * s.Mp2 * 128 + (ks & 3) * 32, 16, 1024, 2),
-                     smem_desc(t32 + ks * 2048, (unsigned)Kp2 * 128, 1024, 2), ks > 0);
+                     Rw::desc(t32, Kp2, ks), ks > 0);
           mma_commit(su32(&B.d2full[bm]));
         }
         if (!has) break;
@@ -404,7 +432,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char *O = base + (g ? P.o1 : P.o0);
     const uint32_t tl = ((uint32_t)(32 * qr) << 16) + (uint32_t)(64 * half);
     const int orows = 2 * s.r2;
-    const int R = half * orows + row;  // output tile row (i_k, c, i_{k+1})
     for (int n = g;; n += kGroups) {
       const int64_t t = blockIdx.x + (int64_t)n * G;
       if (t >= nchunks) break;
@@ -412,19 +439,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t tb = tmem + tl + (uint32_t)(b * 128);
       if (epi_any(!wait_bar(su32(&B.d1full[b]), (unsigned)(n >> 1) & 1u, abort), g)) break;
       tc_fence_after();
-      // D1 -> T: K2 = 2b + j', N2 = 64 i + quad
+      // D1 -> T.  D1 column n = (2 hi + j') X + x (the stage's MN order);
+      // T row K2 = 2b + j', its MN order (2 hi + i) X + x
       if (32 * qr < s.Mp1) {
 #pragma unroll
         for (int xb = 0; xb < 2; ++xb) {
           float v[32];
           tmem_ld32(tb + 32 * xb, v);
           if (row < Kp2) {
-            const int i = row & 1, k2 = 2 * (row >> 1) + half;
-            unsigned char *trow = sT + (size_t)i * Kp2 * 128 + (size_t)k2 * 128;
+            const int i = row & 1, bb = row >> 1;
 #pragma unroll
-            for (int p = 0; p < 4; ++p)
-              *reinterpret_cast<uint4 *>(trow + (((4 * xb + p) ^ (k2 & 7)) << 4)) =
-                  pack8(v + 8 * p);
+            for (int p = 0; p < 4; ++p) {
+              const int n = 64 * half + 32 * xb + 8 * p;
+              const int beta = n >> XLOG, x = n & (Rw::X - 1);
+              const int k2 = 2 * bb + (beta & 1), beta2 = (beta & ~1) | i;
+              const unsigned off = (unsigned)(beta2 * Kp2 + k2) * Rw::bytes + 2u * x;
+              *reinterpret_cast<uint4 *>(sT + Rw::swz(off)) = pack8(v + 8 * p);
+            }
           }
         }
       }
@@ -433,8 +464,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_arrive(su32(&B.tready[b]));
       if (epi_any(!wait_bar(su32(&B.d2full[b]), (unsigned)(n >> 1) & 1u, abort), g)) break;
       tc_fence_after();
-      // D2 -> O[n % 2] (row R, 16-byte chunk ch at (ch ^ R % 8), the 128-byte
-      // swizzle) -> one TMA store
+      // D2 -> O[g] -> one TMA store.  D2 column n = (2 hi + i) X + x; the
+      // store box's rows are (2 hi + i, c, i_{k+1}), X values each
       if (leader) bulk_wait_read0();  // the group's previous store has read O
       epi_sync(g);
       if (32 * qr < s.Mp2) {
@@ -445,9 +476,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (row < orows) {
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
-              const int ch = 4 * xb + p;
-              *reinterpret_cast<uint4 *>(O + (size_t)R * 128 + ((ch ^ (R & 7)) << 4)) =
-                  pack8(v + 8 * p);
+              const int n = 64 * half + 32 * xb + 8 * p;
+              const int beta2 = n >> XLOG, x = n & (Rw::X - 1);
+              const unsigned off = (unsigned)(beta2 * orows + row) * Rw::bytes + 2u * x;
+              *reinterpret_cast<uint4 *>(O + Rw::swz(off)) = pack8(v + 8 * p);
             }
           }
         }
@@ -480,15 +512,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 constexpr size_t kSmemLimit = 227 * 1024;
 
 // 5-D view of a planar BF16 buffer [P][N] for the pair at bit k: dims (x:
-// bits 0..k-1, a: bit `b1`, P, b: bit `b3`, hi: bits k+2..), box (64, 2, box_p,
-// 2, 1), 128-byte swizzle.  Returns false if the driver rejects it.
+// bits 0..k-1, a: bit `b1`, P, b: bit `b3`, hi: bits k+2..), box (X, 2, box_p,
+// 2, 64 / X) with X = 2^min(k, 6), swizzle spanning one X-value row.
+// Returns false if the driver rejects it.
 bool encode_view(CUtensorMap *m, const void *ptr, int k, int64_t N, int64_t planes, int b1,
                  int b3, int box_p) {
+  const int xl = k < 6 ? k : 6;
   const cuuint64_t dims[5] = {(cuuint64_t)1 << k, 2, (cuuint64_t)planes, 2,
                               (cuuint64_t)(N >> (k + 2))};
   const cuuint64_t strides[4] = {((cuuint64_t)1 << b1) * 2, (cuuint64_t)N * 2,
                                  ((cuuint64_t)1 << b3) * 2, ((cuuint64_t)1 << (k + 2)) * 2};
-  const cuuint32_t box[5] = {64, 2, (cuuint32_t)box_p, 2, 1};
+  const cuuint32_t box[5] = {1u << xl, 2, (cuuint32_t)box_p, 2, 64u >> xl};
+  const CUtensorMapSwizzle swz = xl == 6   ? CU_TENSOR_MAP_SWIZZLE_128B
+                                 : xl == 5 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                 : xl == 4 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                           : CU_TENSOR_MAP_SWIZZLE_NONE;
   const cuuint32_t es[5] = {1, 1, 1, 1, 1};
   // the driver's encoder, looked up through the runtime (the library does not
   // link libcuda, so it loads on machines without a driver)
@@ -503,25 +541,41 @@ bool encode_view(CUtensorMap *m, const void *ptr, int k, int64_t N, int64_t plan
   }();
   if (!encode) return false;
   return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(ptr), dims, strides,
-                box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
+namespace {
+
+template <int XLOG>
+cudaError_t launch_x(const CUtensorMap &tin, const CUtensorMap &tout, const StepMMA2 &s, int S,
+                     size_t smem, unsigned grid, cudaStream_t st) {
+  // one CTA per SM: the shared-memory limit is raised once per instantiation
+  static cudaError_t attr = cudaFuncSetAttribute(
+      step_tc2_kernel<XLOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+  if (attr != cudaSuccess) return attr;
+  step_tc2_kernel<XLOG><<<grid, kThreads, smem, st>>>(tin, tout, s, S);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 bool tc2_steps_eligible(int k, int r0, int r1, int r2, int64_t N) {
-  // k >= 6: 64 quads are 64 contiguous positions; r0 % 8 == 0: the input box
-  // is exactly the MMA's padded K; ranks <= 56: two ring stages fit
-  return k >= 6 && (int64_t)1 << (k + 2) < N && r0 % 8 == 0 && r0 >= 8 && r1 >= 8 && r2 >= 8 &&
-         r0 <= kTc2MaxRank && r1 <= kTc2MaxRank && r2 <= kTc2MaxRank;
+  // k >= 4: runs of 16 quads are contiguous (the TMA engine moves about one
+  // box row per 4 cycles, so 16-byte rows (k = 3) ran at 1.2 TB/s, slower
+  // than two single steps; 32-, 64- and 128-byte rows at 2.4, 4.7 and
+  // 5.9 TB/s); N >= 256: whole 64-quad chunks; r0 % 8 == 0: the input box is
+  // exactly the MMA's padded K; ranks <= 56: two ring stages fit
+  return k >= 4 && N >= 256 && (int64_t)1 << (k + 2) < N && r0 % 8 == 0 && r0 >= 8 &&
+         r1 >= 8 && r2 >= 8 && r0 <= kTc2MaxRank && r1 <= kTc2MaxRank && r2 <= kTc2MaxRank;
 }
 
 cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st) {
-  // one CTA per SM with as many ring stages as its shared memory holds
-  static cudaError_t attr = cudaFuncSetAttribute(
-      step_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
-  if (attr != cudaSuccess) return attr;
+  // as many ring stages as the shared memory holds
   const Plan p0 = make_plan(s, 0);
   if (p0.end + 2 * p0.stage + 1024 > kSmemLimit) return cudaErrorNotSupported;
   int S = (int)((kSmemLimit - 1024 - p0.end) / p0.stage);
@@ -539,11 +593,13 @@ cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t nchunks = (s.N >> 2) / kQ * s.nrhs;
-  int64_t grid = sms;
-  if (grid > nchunks) grid = nchunks;
-  step_tc2_kernel<<<(unsigned)grid, kThreads, smem, st>>>(tin, tout, s, S);
-  count_launches(1);
-  return cudaGetLastError();
+  const unsigned grid = (unsigned)(nchunks < sms ? nchunks : sms);
+  switch (s.k < 6 ? s.k : 6) {
+    case 4: return launch_x<4>(tin, tout, s, S, smem, grid, st);
+    case 5: return launch_x<5>(tin, tout, s, S, smem, grid, st);
+    case 6: return launch_x<6>(tin, tout, s, S, smem, grid, st);
+  }
+  return cudaErrorNotSupported;
 }
 
 cudaError_t tc_status_take(int *status) {

@@ -1,7 +1,8 @@
 """The BF16 tensor-core steps (FP32 accumulate): the single mma.sync step
 used for k >= 3 and ranks in [4, 64], and the fused pair of steps (TMA +
-tcgen05 with a TMEM accumulator for k >= 6, r_k % 8 == 0 and ranks in
-[8, 56], else mma.sync for k >= 3 and ranks in [16, 48]), k + 2 < d.  Exact on integer data and within
+tcgen05 with a TMEM accumulator for k >= 4, N >= 256, r_k % 8 == 0 and ranks
+in [8, 56] -- position runs of 16, 32 or 64 with the matching swizzle --
+else mma.sync for ranks in [16, 48]), k + 2 < d.  Exact on integer data and within
 the BF16 error bound otherwise, including partial chunks, uneven rank
 profiles and many right-hand sides."""
 import math
@@ -78,6 +79,7 @@ def test_bf16_error_bound_tensor_cores(qtt, d, rmax, nrhs):
     ([1, 2, 4, 8, 8, 8, 9, 64, 64, 64, 12, 1], 2),           # ranks 8 and 64 (M = 128 full)
     ([1, 2, 4, 8, 16, 32, 56, 40, 56, 24, 8, 8, 1], 3),      # TMA pairs at k = 6, 8
     ([1, 2, 4, 8, 8, 8, 8, 8, 8, 8, 8, 1], 2),               # TMA pairs of rank 8
+    ([1, 2, 4, 6, 16, 24, 16, 32, 8, 1], 3),                 # TMA pairs at k = 4 and 6
 ])
 def test_fused_pairs_integer_exact(qtt, ranks, nrhs):
     """Uneven rank profiles through the fused pair kernel: every padded
