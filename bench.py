@@ -80,7 +80,7 @@ METRIC = "QTT-apply GFLOP/s"
 # capture of the same command, averaged over one apply's launches; valid for
 # the kernel source it was taken on (see the named profile).
 NCU_TRAFFIC = {
-    "apply_f64": {"bytes_per_launch": 144.43e9 / 24,
+    "apply_f64": {"bytes_per_launch": 144.41e9 / 24,
                   "source": "profiles/step_f64_kernel_apply_f64_d24_launches.md"},
 }
 
