@@ -269,7 +269,8 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
     const int64_t nc = std::min<int64_t>(chunk, nrhs - c0);
     int src = 0;  // scratch half holding the current intermediate (k >= 1)
     int k0 = 0;
-    const int hm = use_fusion() ? head_steps(A->ranks.data(), d) : 0;
+    const std::vector<float> &hcores = A->head[mode == LP_F32 ? 0 : mode == LP_TF32 ? 1 : 2];
+    const int hm = use_fusion() && !hcores.empty() ? head_steps(A->ranks.data(), d) : 0;
     if (hm) {
       // steps 0 .. hm-1 in one launch; y_hm lands in scratch half 0
       StepHead h;
@@ -278,12 +279,8 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
       h.in_rhs_stride = ld;
       h.out = buf[0];
       h.out_rhs_stride = (int64_t)A->ranks[hm] * N;
-      for (int k = 0; k < hm; ++k)
-        h.M[k] = static_cast<const char *>(cores) + (size_t)A->offlp[k] * core_esz;
-      for (int k = 0; k <= hm; ++k) {
-        h.r[k] = A->ranks[k];
-        h.rpad[k] = A->rpad[k];
-      }
+      std::memcpy(h.G, hcores.data(), sizeof(h.G));
+      for (int k = 0; k <= hm; ++k) h.r[k] = A->ranks[k];
       h.N = N;
       h.nrhs = nc;
       h.m = hm;
@@ -515,6 +512,26 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores
               L[(((size_t)a * 2 + j) * rp + b) * 2 + i] = G[(((size_t)a * 2 + i) * 2 + j) * rb + b];
     }
     std::vector<float> lp(lpd.begin(), lpd.end());
+    // head-kernel copies of cores 0..2 (the same values as the packed copies)
+    auto head_copy = [&](auto value_of) {
+      std::vector<float> hc(3 * 16 * 8 * 2, 0.0f);
+      for (int k = 0; k < 3 && k < d; ++k) {
+        if (ranks[k] > kHeadMaxRank || ranks[k + 1] > kHeadMaxRank) break;
+        const int rp = A->rpad[k + 1];
+        for (int a = 0; a < ranks[k]; ++a)
+          for (int j = 0; j < 2; ++j)
+            for (int b = 0; b < ranks[k + 1]; ++b)
+              for (int i = 0; i < 2; ++i)
+                hc[(((size_t)k * 16 + 2 * a + j) * 8 + b) * 2 + i] =
+                    value_of(A->offlp[k] + (((int64_t)a * 2 + j) * rp + b) * 2 + i);
+      }
+      return hc;
+    };
+    if (precision_mask & QTT_PACK_F32) A->head[0] = head_copy([&](int64_t q) { return lp[q]; });
+    if (precision_mask & QTT_PACK_TF32)
+      A->head[1] = head_copy([&](int64_t q) { return host_tf32_rne(lp[q]); });
+    if (precision_mask & QTT_PACK_BF16)
+      A->head[2] = head_copy([&](int64_t q) { return __bfloat162float(__double2bfloat16(lpd[q])); });
     auto upload = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
       cudaError_t e2 = cudaMalloc(dst, bytes);
       if (e2 != cudaSuccess) return e2;

@@ -62,6 +62,10 @@ struct qtt_op {
   std::vector<int> rpad;        // padded output rank per core (index k+1)
   std::vector<int64_t> offlp;   // element offset of core k
   int64_t nlp = 0;              // total packed elements
+  // Host copies of cores 0..2 for the head kernel, per reduced precision
+  // (F32, TF32, BF16), [k][2a + j][b][i] with 16 x 8 x 2 floats per core;
+  // empty when the first ranks are too large.
+  std::vector<float> head[3];
 };
 
 namespace qtt {

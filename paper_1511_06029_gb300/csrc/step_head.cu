@@ -10,6 +10,9 @@
 // y_m once instead of moving y_1 .. y_{m-1} through HBM, and a warp's
 // accesses are contiguous.
 //
+// The cores travel by value in the launch parameters, so every multiply
+// takes its core value as a constant-bank operand (no load instruction).
+//
 // Numerics are those of the one-step kernel (step_lp.cu) step by step: the
 // input rounded to the mode's precision when read, each intermediate rounded
 // to it (BF16 or TF32) as the one-step kernel stores it, FP32 sums over
@@ -43,6 +46,36 @@ __device__ __forceinline__ float round_mode(float v) {
 __device__ __forceinline__ float to_f(double v) { return (float)v; }
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+// T consecutive input values: one vector load when the address allows it
+// (the caller's x may have any leading dimension), else scalar loads.
+template <int T, typename TIN>
+__device__ __forceinline__ void load_vec(const TIN *p, TIN (&v)[T]) {
+  constexpr int bytes = T * (int)sizeof(TIN);
+  if (bytes >= 4 && (reinterpret_cast<uintptr_t>(p) & (bytes > 16 ? 15 : bytes - 1)) == 0) {
+    if (bytes <= 16) {
+      if (bytes == 16) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(p));
+        memcpy(v, &w, 16);
+      } else if (bytes == 8) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
+        memcpy(v, &w, 8);
+      } else {
+        const unsigned w = __ldg(reinterpret_cast<const unsigned *>(p));
+        memcpy(v, &w, 4);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < bytes / 16; ++q) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+        memcpy(reinterpret_cast<char *>(v) + 16 * q, &w, 16);
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < T; ++q) v[q] = p[q];
+}
+
 // T consecutive values as one vector store (T = 2 or 4; the scratch planes
 // are 16-byte aligned and T divides every plane offset used).
 template <int T>
@@ -64,18 +97,10 @@ __device__ __forceinline__ void store_vec(__nv_bfloat16 *o, const float *v) {
   }
 }
 
-template <int MODE, typename TIN, typename TMID, typename TCORE, int M>
-__global__ void __launch_bounds__(kThreads, 2) step_head_kernel(StepHead s) {
+template <int MODE, typename TIN, typename TMID, int M>
+__global__ void __launch_bounds__(kThreads, 2) step_head_kernel(const __grid_constant__ StepHead s) {
   constexpr int P = 1 << M;   // positions of a group
   constexpr int T = P / 2;    // positions per thread: two lanes share a group
-  __shared__ float sG[3][4 * kR * kR];
-  // cores of steps 0 .. M-1 from the packed [a][j][b padded][i] layout
-  for (int k = 0; k < M; ++k) {
-    const TCORE *G = static_cast<const TCORE *>(s.M[k]);
-    const int n = 2 * s.r[k] * 2 * s.rpad[k + 1];
-    for (int e = threadIdx.x; e < n; e += blockDim.x) sG[k][e] = to_f(G[e]);
-  }
-  __syncthreads();
   // lane pair (2 g, 2 g + 1) holds group g: the lane with h = 1 the positions
   // with bit M-1 set.  Inactive lanes (past the end) still take part in the
   // shuffles of the last step.
@@ -88,14 +113,15 @@ __global__ void __launch_bounds__(kThreads, 2) step_head_kernel(StepHead s) {
   float y[kR][T], z[kR][T];
   {
     const TIN *in = static_cast<const TIN *>(s.in) + c * s.in_rhs_stride + pbase;
+    TIN xv[T];
+    if (active) load_vec<T>(in, xv);
 #pragma unroll
-    for (int q = 0; q < T; ++q) y[0][q] = active ? round_mode<MODE>(to_f(in[q])) : 0.0f;
+    for (int q = 0; q < T; ++q) y[0][q] = active ? round_mode<MODE>(to_f(xv[q])) : 0.0f;
   }
   int rin = 1;
 #pragma unroll
   for (int k = 0; k < M; ++k) {
-    const int rout = s.r[k + 1], rpad = s.rpad[k + 1];
-    const float *G = sG[k];
+    const int rout = s.r[k + 1];
 #pragma unroll
     for (int b = 0; b < kR; ++b)
 #pragma unroll
@@ -110,8 +136,7 @@ __global__ void __launch_bounds__(kThreads, 2) step_head_kernel(StepHead s) {
 #pragma unroll
           for (int b = 0; b < kR; ++b) {
             if (b >= rout) break;
-            const float g0 = G[((2 * a + j) * rpad + b) * 2];
-            const float g1 = G[((2 * a + j) * rpad + b) * 2 + 1];
+            const float g0 = s.G[k][2 * a + j][b][0], g1 = s.G[k][2 * a + j][b][1];
 #pragma unroll
             for (int q = 0; q < T; ++q) {
               if (((q >> k) & 1) != 0) continue;  // q = pair base (bit k clear)
@@ -136,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 2) step_head_kernel(StepHead s) {
 #pragma unroll
           for (int b = 0; b < kR; ++b) {
             if (b >= rout) break;
-            const float g = G[((2 * a + j) * rpad + b) * 2 + h];
+            const float g = h ? s.G[k][2 * a + j][b][1] : s.G[k][2 * a + j][b][0];
 #pragma unroll
             for (int q = 0; q < T; ++q) z[b][q] = fmaf(g, j == h ? y[a][q] : other[q], z[b][q]);
           }
@@ -158,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 2) step_head_kernel(StepHead s) {
   }
 }
 
-template <int MODE, typename TIN, typename TMID, typename TCORE>
+template <int MODE, typename TIN, typename TMID>
 cudaError_t launch_m(const StepHead &s, cudaStream_t st) {
   const int64_t groups = s.N >> s.m;
   const unsigned gx = (unsigned)((2 * groups + kThreads - 1) / kThreads);
@@ -168,9 +193,9 @@ cudaError_t launch_m(const StepHead &s, cudaStream_t st) {
     t.in = static_cast<const TIN *>(s.in) + c0 * s.in_rhs_stride;
     t.out = static_cast<TMID *>(s.out) + c0 * s.out_rhs_stride;
     if (s.m == 2)
-      step_head_kernel<MODE, TIN, TMID, TCORE, 2><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
+      step_head_kernel<MODE, TIN, TMID, 2><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
     else
-      step_head_kernel<MODE, TIN, TMID, TCORE, 3><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
+      step_head_kernel<MODE, TIN, TMID, 3><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
     count_launches(1);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -178,12 +203,12 @@ cudaError_t launch_m(const StepHead &s, cudaStream_t st) {
   return cudaSuccess;
 }
 
-template <int MODE, typename TMID, typename TCORE>
+template <int MODE, typename TMID>
 cudaError_t by_input(const StepHead &s, cudaStream_t st) {
   switch (s.in_type) {
-    case QTT_F64: return launch_m<MODE, double, TMID, TCORE>(s, st);
-    case QTT_BF16: return launch_m<MODE, __nv_bfloat16, TMID, TCORE>(s, st);
-    default: return launch_m<MODE, float, TMID, TCORE>(s, st);
+    case QTT_F64: return launch_m<MODE, double, TMID>(s, st);
+    case QTT_BF16: return launch_m<MODE, __nv_bfloat16, TMID>(s, st);
+    default: return launch_m<MODE, float, TMID>(s, st);
   }
 }
 
@@ -198,9 +223,9 @@ int head_steps(const int *ranks, int d) {
 cudaError_t launch_step_head(const StepHead &s, cudaStream_t st) {
   if (s.m < 2 || s.m > 3) return cudaErrorInvalidValue;
   switch (s.mode) {
-    case LP_F32: return by_input<LP_F32, float, float>(s, st);
-    case LP_TF32: return by_input<LP_TF32, float, float>(s, st);
-    case LP_BF16: return by_input<LP_BF16, __nv_bfloat16, __nv_bfloat16>(s, st);
+    case LP_F32: return by_input<LP_F32, float>(s, st);
+    case LP_TF32: return by_input<LP_TF32, float>(s, st);
+    case LP_BF16: return by_input<LP_BF16, __nv_bfloat16>(s, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -46,11 +46,13 @@ struct StepHead {
   int64_t in_rhs_stride;
   void *out;               // y_m (intermediate type of the mode), planar
   int64_t out_rhs_stride;
-  const void *M[3];        // packed cores 0 .. m-1 (as for StepLP)
-  int r[4], rpad[4];       // ranks r_0 .. r_m and their padded widths
+  int r[4];                // ranks r_0 .. r_m
   int64_t N, nrhs;
   int m, mode;
   qtt_dtype in_type;
+  // cores 0 .. m-1 by value (the kernel reads them as constant-bank operands):
+  // G[k][2a + j][b][i], zero beyond the ranks, values of the mode's packed copy
+  float G[3][2 * kHeadMaxRank][kHeadMaxRank][2];
 };
 // Steps the head kernel takes for this rank profile (0: none).
 int head_steps(const int *ranks, int d);
