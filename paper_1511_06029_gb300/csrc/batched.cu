@@ -137,6 +137,7 @@ __device__ __forceinline__ void rank_block(const float *sm, const float *sG, int
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int m = 0; m < TN; ++m) acc[t][i][m] = 0.0f;
+#pragma unroll 4
   for (int kk = 0; kk < 2 * rin; ++kk) {
     float v[TN];
     load_v<TN>(sm + (size_t)kk * npair_chunk + TN * lane, v);

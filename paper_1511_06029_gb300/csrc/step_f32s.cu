@@ -77,6 +77,7 @@ __device__ __forceinline__ void chunk_block(const float *sb, const float *sG, co
 #pragma unroll
       for (int m = 0; m < 4; ++m) acc[t][i][m] = 0.0f;
   const int rpad = s.rout_pad;
+#pragma unroll 4
   for (int kk = 0; kk < 2 * s.rin; ++kk) {
     const float4 v = *reinterpret_cast<const float4 *>(sb + kk * kPC + 4 * lane);
     const float4 *g4 = reinterpret_cast<const float4 *>(sG + (kk * rpad + b0) * 2);
