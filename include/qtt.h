@@ -159,8 +159,8 @@ typedef enum {
   QTT_SOLVE_GMRES = 1,  /* right-preconditioned GMRES(restart) with P
                            (Sec. 5.3: QTT preconditioner inside GMRES). */
   QTT_SOLVE_REFINE = 2  /* iterative refinement x <- x + M (f - (a I + K) x)
-                           with the residual in FP64 (the spec mixed-
-                           precision scheme): M = P, or inner_iters steps of
+                           with the residual in FP64 (mixed-precision
+                           refinement): M = P, or inner_iters steps of
                            a low-precision Richardson iteration on
                            (a I + K) z = r preconditioned by P. */
 } qtt_solve_kind;

@@ -61,18 +61,29 @@ cudaMemPool_t pool_for_current_device() {
 }
 }  // namespace
 
-size_t scratch_available() {
-  size_t free_b = 0, total_b = 0;
-  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
+// Bytes the pool holds already reserved but unused (no driver query of free
+// memory: cheap enough for every small apply).
+static size_t scratch_cached() {
   cudaMemPool_t p = pool_for_current_device();
-  if (!p) return free_b;
+  if (!p) return 0;
   uint64_t reserved = 0, used = 0;
   cudaMemPoolGetAttribute(p, cudaMemPoolAttrReservedMemCurrent, &reserved);
   cudaMemPoolGetAttribute(p, cudaMemPoolAttrUsedMemCurrent, &used);
-  const size_t cached = reserved > used ? (size_t)(reserved - used) : 0;
+  return reserved > used ? (size_t)(reserved - used) : 0;
+}
+
+size_t scratch_available() {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
+  const size_t cached = scratch_cached();
   // Leave a margin for the driver and other allocators in the process.
   const size_t margin = (size_t)512 << 20;
   return free_b > margin ? free_b - margin + cached : cached;
+}
+
+size_t scratch_available_at_least(size_t bytes) {
+  const size_t cached = scratch_cached();
+  return cached >= bytes ? cached : scratch_available();
 }
 
 qtt_status scratch_alloc(void **ptr, size_t bytes, cudaStream_t stream) {
@@ -80,7 +91,7 @@ qtt_status scratch_alloc(void **ptr, size_t bytes, cudaStream_t stream) {
   if (bytes == 0) return QTT_OK;
   cudaMemPool_t p = pool_for_current_device();
   if (!p) return fail(QTT_ERR_CUDA, "cannot create the scratch memory pool");
-  if (bytes > scratch_available())
+  if (bytes > scratch_available_at_least(bytes))
     return fail(QTT_ERR_OOM, "scratch of " + std::to_string(bytes) +
                                  " bytes exceeds free device memory");
   cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes, p, stream);
@@ -122,7 +133,7 @@ qtt_status apply_f64(const qtt_op *A, const double *x, double *y, int64_t nrhs,
   const size_t per_rhs = d > 1 ? (size_t)2 * A->rmax_inner * (size_t)N * sizeof(double) : 0;
   int64_t chunk = nrhs;
   if (per_rhs) {
-    const size_t avail = scratch_available();
+    const size_t avail = scratch_available_at_least(per_rhs * (size_t)nrhs);
     const int64_t fit = (int64_t)(avail / per_rhs);
     if (fit < 1)
       return fail(QTT_ERR_OOM, "apply scratch for one right-hand side (" +
@@ -250,7 +261,7 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
   const size_t per_rhs = d > 1 ? (size_t)2 * A->rmax_inner * (size_t)N * esz : 0;
   int64_t chunk = nrhs;
   if (per_rhs) {
-    const int64_t fit = (int64_t)(scratch_available() / per_rhs);
+    const int64_t fit = (int64_t)(scratch_available_at_least(per_rhs * (size_t)nrhs) / per_rhs);
     if (fit < 1)
       return fail(QTT_ERR_OOM, "apply scratch for one right-hand side does not fit");
     chunk = std::min<int64_t>(nrhs, fit);

@@ -31,6 +31,9 @@ qtt_status scratch_alloc(void **ptr, size_t bytes, cudaStream_t stream);
 void scratch_free(void *ptr, cudaStream_t stream);
 // Bytes the pool could hand out right now without growing past free memory.
 size_t scratch_available();
+// The same, but answered from the pool's own cached bytes (no query of the
+// device's free memory) when those already cover `bytes`.
+size_t scratch_available_at_least(size_t bytes);
 
 }  // namespace qtt
 

@@ -94,10 +94,13 @@ step_f64_kernel(StepF64 s) {
 
 }  // namespace
 
-cudaError_t launch_step_f64(const StepF64 &s, cudaStream_t stream) {
+namespace {
+
+template <int TN>
+cudaError_t launch_tn(const StepF64 &s, cudaStream_t stream) {
   const int64_t npairs = s.N >> 1;
   const int by = s.rout < kWarpsY ? s.rout : kWarpsY;
-  const int64_t gx = (npairs + 32 * kTN - 1) / (32 * kTN);
+  const int64_t gx = (npairs + 32 * TN - 1) / (32 * TN);
   const int64_t gy = (s.rout + by - 1) / by;
   dim3 block(32, by, 1);
   for (int64_t c0 = 0; c0 < s.nrhs; c0 += 65535) {
@@ -109,12 +112,29 @@ cudaError_t launch_step_f64(const StepF64 &s, cudaStream_t stream) {
     if (t.v) t.v += c0 * s.uv_rhs_stride;
     if (gx * gy > 0x7fffffffLL) return cudaErrorInvalidValue;
     dim3 grid((unsigned)(gx * gy), 1, (unsigned)nc);
-    step_f64_kernel<kTN><<<grid, block, 0, stream>>>(t);
+    step_f64_kernel<TN><<<grid, block, 0, stream>>>(t);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_step_f64(const StepF64 &s, cudaStream_t stream) {
+  // Small steps (the 8^3 volume operator has N = 512) would give a few CTAs
+  // with 4 pairs per lane and leave most SMs idle: one pair per lane then
+  // gives 4x the CTAs (the same work, shorter FMA chains per warp).
+  static const int sms = [] {
+    int dev = 0, n = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+  }();
+  const int64_t ctas = ((s.N >> 1) + 127) / 128 * ((s.rout + kWarpsY - 1) / kWarpsY) * s.nrhs;
+  if (ctas < 2 * sms) return launch_tn<1>(s, stream);
+  return launch_tn<kTN>(s, stream);
 }
 
 }  // namespace qtt

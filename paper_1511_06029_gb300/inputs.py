@@ -196,7 +196,8 @@ def tt_svd(T: np.ndarray, eps: float):
 
 
 def laplace_volume(n: int = 8, eps: float = 1e-8):
-    """Config 1 operator.  Returns (QTTData, dense A)."""
+    """The n^3 Laplace volume operator A = I + h^3 K (Sec. 5.2) compressed by
+    TT-SVD at eps.  Returns (QTTData, dense A)."""
     A = laplace_volume_dense(n)
     ranks, cores = tt_svd(matrix_to_qtt_tensor(A), eps)
     cores = [c.reshape(c.shape[0], 2, 2, c.shape[2]) for c in cores]

@@ -71,7 +71,7 @@ def test_synthetic_recipe():
     assert all(np.array_equal(a, b) for a, b in zip(op.cores, op2.cores))
 
 
-def test_config2_rank_profile_sigma():
+def test_d24_rank_profile_sigma():
     r = inputs.rank_profile(24, 32)
     assert r[:6] == [1, 2, 4, 8, 16, 32] and r[-6:] == [32, 16, 8, 4, 2, 1]
     sigma = sum(r[k] * r[k + 1] for k in range(24))
