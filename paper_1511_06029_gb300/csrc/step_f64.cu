@@ -92,9 +92,93 @@ step_f64_kernel(StepF64 s) {
   }
 }
 
+// Small steps (few pair tiles, e.g. the 8^3 volume operator with N = 512):
+// the same contraction with the sum over (a, j) split among KS warps, so a
+// CTA of 8 warps covers 8 / KS output ranks of 32 pairs and the grid has
+// KS times more CTAs with KS times shorter FMA chains.  The KS partial sums
+// meet in shared memory and are added in a fixed order (deterministic).
+template <int KS>
+__global__ void __launch_bounds__(32 * kWarpsY)
+step_f64_small_kernel(StepF64 s) {
+  constexpr int RPC = kWarpsY / KS;  // output ranks per CTA
+  __shared__ double part[kWarpsY][2][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nrg = (s.rout + RPC - 1) / RPC;
+  const int b = (int)(blockIdx.x % nrg) * RPC + warp / KS;
+  const int split = warp % KS;
+  const int64_t c = blockIdx.z;
+  const int64_t npairs = s.N >> 1;
+  const int64_t bit = (int64_t)1 << s.k;
+  const int64_t low = bit - 1;
+  const int64_t q = (int64_t)(blockIdx.x / nrg) * 32 + lane;
+  const bool ok = q < npairs && b < s.rout;
+  const int64_t p0 = ((q & ~low) << 1) | (q & low);
+  double acc0 = 0.0, acc1 = 0.0;
+  if (ok) {
+    const double *in = s.in + c * s.in_rhs_stride;
+    const double2 *Mb = reinterpret_cast<const double2 *>(s.M) + (int64_t)b * 2 * s.rin;
+    const int per = (s.rin + KS - 1) / KS;
+    const int a0 = split * per, a1 = min(s.rin, a0 + per);
+    for (int a = a0; a < a1; ++a) {
+      const double *ina = in + (int64_t)a * s.N + p0;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const double2 g = __ldg(Mb + 2 * a + j);
+        const double v = __ldg(ina + (j ? bit : 0));
+        acc0 = fma(g.x, v, acc0);
+        acc1 = fma(g.y, v, acc1);
+      }
+    }
+  }
+  part[warp][0][lane] = acc0;
+  part[warp][1][lane] = acc1;
+  __syncthreads();
+  if (split != 0 || !ok) return;
+  acc0 = acc1 = 0.0;
+#pragma unroll
+  for (int t = 0; t < KS; ++t) {
+    acc0 += part[warp + t][0][lane];
+    acc1 += part[warp + t][1][lane];
+  }
+  double *out = s.out + c * s.out_rhs_stride + (int64_t)b * s.N;
+  if (s.epi) {
+    const double *u = s.u ? s.u + c * s.uv_rhs_stride : nullptr;
+    const double *v = s.v ? s.v + c * s.uv_rhs_stride : nullptr;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int64_t p = p0 + (i ? bit : 0);
+      double t = v ? s.s_v * v[p] : 0.0;
+      if (u) t += s.s_u * u[p];
+      out[p] = t + s.s_acc * (i ? acc1 : acc0);
+    }
+  } else {
+    out[p0] = acc0;
+    out[p0 + bit] = acc1;
+  }
+}
+
 }  // namespace
 
 namespace {
+
+cudaError_t launch_small(const StepF64 &s, cudaStream_t stream) {
+  constexpr int KS = 4, RPC = kWarpsY / KS;
+  const int64_t gx = ((s.N >> 1) + 31) / 32 * ((s.rout + RPC - 1) / RPC);
+  for (int64_t c0 = 0; c0 < s.nrhs; c0 += 65535) {
+    StepF64 t = s;
+    const int64_t nc = (s.nrhs - c0) < 65535 ? (s.nrhs - c0) : 65535;
+    t.in += c0 * s.in_rhs_stride;
+    t.out += c0 * s.out_rhs_stride;
+    if (t.u) t.u += c0 * s.uv_rhs_stride;
+    if (t.v) t.v += c0 * s.uv_rhs_stride;
+    if (gx > 0x7fffffffLL) return cudaErrorInvalidValue;
+    step_f64_small_kernel<KS><<<dim3((unsigned)gx, 1, (unsigned)nc), 32 * kWarpsY, 0, stream>>>(t);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 template <int TN>
 cudaError_t launch_tn(const StepF64 &s, cudaStream_t stream) {
@@ -124,8 +208,8 @@ cudaError_t launch_tn(const StepF64 &s, cudaStream_t stream) {
 
 cudaError_t launch_step_f64(const StepF64 &s, cudaStream_t stream) {
   // Small steps (the 8^3 volume operator has N = 512) would give a few CTAs
-  // with 4 pairs per lane and leave most SMs idle: one pair per lane then
-  // gives 4x the CTAs (the same work, shorter FMA chains per warp).
+  // with 4 pairs per lane and leave most SMs idle: the split-sum kernel then
+  // gives 16x the CTAs (one pair per lane, the (a, j) sum over 4 warps).
   static const int sms = [] {
     int dev = 0, n = 148;
     cudaGetDevice(&dev);
@@ -133,7 +217,7 @@ cudaError_t launch_step_f64(const StepF64 &s, cudaStream_t stream) {
     return n;
   }();
   const int64_t ctas = ((s.N >> 1) + 127) / 128 * ((s.rout + kWarpsY - 1) / kWarpsY) * s.nrhs;
-  if (ctas < 2 * sms) return launch_tn<1>(s, stream);
+  if (ctas < 2 * sms) return launch_small(s, stream);
   return launch_tn<kTN>(s, stream);
 }
 
