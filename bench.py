@@ -11,6 +11,8 @@ Workloads (a "step" is one pass of the hot path over one batch of input):
                   arithmetic: one qtt_apply per step.
   apply_f64_d22   the same family at d = 22 (profiler captures).
   laplace_f64     the 8^3 Laplace volume operator (TT-SVD, eps 1e-8), 1 RHS.
+  laplace_f64_plan  the same, each apply a replay of the recorded sweep
+                  (qtt_plan_*, one CUDA graph launch).
   apply_f32_d24 / apply_tf32_d24 / apply_bf16_d24
                   the default operator and RHS with FP32 / TF32 / BF16 operands
                   and FP32 accumulation (FP32 pipe).
@@ -89,6 +91,8 @@ WORKLOADS = {
     "apply_f64_d22": dict(kind="apply", d=22, rmax=32, seed=2, rhs_seed=3, nrhs=1,
                           compute="f64"),
     "laplace_f64": dict(kind="apply", laplace=True, rhs_seed=1, nrhs=1, compute="f64"),
+    "laplace_f64_plan": dict(kind="apply", laplace=True, rhs_seed=1, nrhs=1, compute="f64",
+                             plan=True),
     "apply_f32_d24": dict(kind="apply", d=24, rmax=32, seed=2, rhs_seed=3, nrhs=1,
                           compute="f32"),
     "apply_tf32_d24": dict(kind="apply", d=24, rmax=32, seed=2, rhs_seed=3, nrhs=1,
@@ -325,11 +329,22 @@ class ApplyRun:
         self.unit = "GFLOP/s"
 
     def step(self):
+        if self.spec.get("plan"):
+            # the sweep recorded once as a CUDA graph (qtt_plan_*), replayed
+            if getattr(self, "_plan", None) is None:
+                self._plan = self.op.plan(self.x, self.y, compute=self.compute)
+            self._plan.run(stream=self.stream)
+            return
         self.op.apply(self.x, out=self.y, compute=self.compute, stream=self.stream)
 
     def e2e_step(self):
         self.xd.copy_(self.xh, non_blocking=True)
-        self.op.apply(self.xd, out=self.yd, compute=self.compute)
+        if self.spec.get("plan"):
+            if getattr(self, "_plan_e2e", None) is None:
+                self._plan_e2e = self.op.plan(self.xd, self.yd, compute=self.compute)
+            self._plan_e2e.run()
+        else:
+            self.op.apply(self.xd, out=self.yd, compute=self.compute)
         self.yh.copy_(self.yd, non_blocking=True)
 
     def e2e_bytes(self):
@@ -433,6 +448,9 @@ class ApplyRun:
         return oracle_baseline(self.data)
 
     def close(self):
+        for name in ("_plan", "_plan_e2e"):
+            if getattr(self, name, None) is not None:
+                getattr(self, name).close()
         self.op.close()
 
 

@@ -143,6 +143,32 @@ qtt_status qtt_apply(const qtt_op *A, const void *x, void *y, int64_t nrhs,
 qtt_status qtt_apply_noalloc(const qtt_op *A, const double *x, double *y,
                              int64_t nrhs, int64_t ld, void *stream);
 
+/* ------------------------------------------------------ recorded applies */
+/* qtt_plan_* -- one qtt_apply recorded once as a CUDA graph and replayed.
+ * The paper has no counterpart: a small operator (the 8^3 volume problem has
+ * d = 9) spends more time launching its d kernels than running them, and a
+ * replay issues the whole sweep (its scratch allocation and every step) as
+ * one graph launch.
+ *   qtt_plan_create : records y = A x exactly as qtt_apply(A, x, y, nrhs, ld,
+ *                     io_dtype, compute) would run it (same checks, same
+ *                     kernels) on a private stream; nothing is executed.
+ *                     The addresses x, y (device, caller-owned) are fixed in
+ *                     the plan: their CONTENTS are read and written at each
+ *                     replay.  A must outlive the plan.  Returns the same
+ *                     errors as qtt_apply, or QTT_ERR_CUDA if the runtime
+ *                     refuses to record it.
+ *   qtt_plan_run    : one replay, asynchronous on `stream` (ordered after
+ *                     prior work on it); the result is bitwise that of
+ *                     qtt_apply with the same arguments.
+ *   qtt_plan_destroy: frees the graph (NULL is a no-op).
+ * A plan may be run on several streams, but replays of one plan must not
+ * overlap (they share x, y and the graph's scratch). */
+typedef struct qtt_plan qtt_plan;
+qtt_status qtt_plan_create(qtt_plan **out, const qtt_op *A, const void *x, void *y,
+                           int64_t nrhs, int64_t ld, qtt_dtype io_dtype, qtt_dtype compute);
+qtt_status qtt_plan_run(qtt_plan *P, void *stream);
+qtt_status qtt_plan_destroy(qtt_plan *P);
+
 /* qtt_residual -- r = f - (a x + K x), all FP64, the forward residual of the
  * second-kind system (a I + K) x = f (Sec. 3, eq. (nystrom): A = a I +
  * B K W C), with the subtraction fused into the last core step of the K

@@ -19,7 +19,11 @@ namespace qtt {
 static thread_local std::string g_last_error;
 static std::atomic<uint64_t> g_launches{0};
 
-void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local uint64_t t_launches = 0;  // this thread's launches (plan recording)
+void count_launches(uint64_t n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
 
 qtt_status fail(qtt_status s, const std::string &msg) {
   g_last_error = msg;
@@ -649,6 +653,63 @@ qtt_status qtt_apply(const qtt_op *A, const void *x, void *y, int64_t nrhs, int6
   if (io_dtype == QTT_TF32)
     return fail(QTT_ERR_INVALID_ARG, "qtt_apply: TF32 is not a storage type (use F32)");
   return apply_lp(A, compute, x, io_dtype, y, io_dtype, nrhs, ld, st, LpEpilogue());
+}
+
+qtt_status qtt_plan_create(qtt_plan **out, const qtt_op *A, const void *x, void *y,
+                           int64_t nrhs, int64_t ld, qtt_dtype io_dtype, qtt_dtype compute) {
+  if (!out) return fail(QTT_ERR_INVALID_ARG, "qtt_plan_create: out is NULL");
+  *out = nullptr;
+  qtt_plan *P = new (std::nothrow) qtt_plan();
+  if (!P) return fail(QTT_ERR_OOM, "qtt_plan_create: host allocation failed");
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete P;
+    return cuda_fail(e, "qtt_plan_create: stream");
+  }
+  // record the apply (relaxed mode: the first call of a kernel family sets
+  // its attributes, which is not a stream operation)
+  const uint64_t before = t_launches;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  qtt_status s = QTT_OK;
+  if (e == cudaSuccess) s = qtt_apply(A, x, y, nrhs, ld, io_dtype, compute, cs);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess || e2 != cudaSuccess || s != QTT_OK) {
+    if (g) cudaGraphDestroy(g);
+    delete P;
+    if (s != QTT_OK) return s;
+    return cuda_fail(e != cudaSuccess ? e : e2, "qtt_plan_create: stream capture");
+  }
+  P->launches = t_launches - before;
+  g_launches.fetch_sub(P->launches, std::memory_order_relaxed);  // recorded, not run
+  t_launches = before;
+  P->graph = g;
+  e = cudaGraphInstantiate(&P->exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    delete P;
+    return cuda_fail(e, "qtt_plan_create: instantiate");
+  }
+  *out = P;
+  return QTT_OK;
+}
+
+qtt_status qtt_plan_run(qtt_plan *P, void *stream) {
+  if (!P || !P->exec) return fail(QTT_ERR_INVALID_ARG, "qtt_plan_run: no plan");
+  const cudaError_t e = cudaGraphLaunch(P->exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "qtt_plan_run: graph launch");
+  count_launches(P->launches);
+  return QTT_OK;
+}
+
+qtt_status qtt_plan_destroy(qtt_plan *P) {
+  if (!P) return QTT_OK;
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  delete P;
+  return QTT_OK;
 }
 
 qtt_status qtt_residual(const qtt_op *K, double a, const double *f, const double *x,

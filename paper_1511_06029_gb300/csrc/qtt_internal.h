@@ -71,6 +71,14 @@ struct qtt_op {
   std::vector<float> head[3];
 };
 
+// One recorded apply (qtt_plan_*): the instantiated graph and how many of
+// the library's kernels one replay launches.
+struct qtt_plan {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t launches = 0;
+};
+
 namespace qtt {
 
 // FP64 core step (Algorithm 2, one k).  in/out rhs strides in elements.

@@ -41,6 +41,9 @@ SIGNATURES = {
     "qtt_apply": (_I, [_P, _P, _P, _L, _L, _I, _I, _P]),
     "qtt_residual": (_I, [_P, _D, _P, _P, _P, _L, _L, _P]),
     "qtt_apply_noalloc": (_I, [_P, _P, _P, _L, _L, _P]),
+    "qtt_plan_create": (_I, [ctypes.POINTER(_P), _P, _P, _P, _L, _L, _I, _I]),
+    "qtt_plan_run": (_I, [_P, _P]),
+    "qtt_plan_destroy": (_I, [_P]),
     "qtt_solve": (_I, [_P, _P, _P, _P, _L, _L, _P, _P, _P]),
     "qtt_status_string": (ctypes.c_char_p, [_I]),
     "qtt_last_error": (ctypes.c_char_p, []),
@@ -147,6 +150,40 @@ def _block(t, N, what):
     return t.shape[0], (t.stride(0) if t.shape[0] > 1 else N)
 
 
+class Plan:
+    """One apply recorded as a CUDA graph (qtt_plan_*): x and out are fixed,
+    their contents are read and written at every run()."""
+
+    def __init__(self, op, x, out, compute="f64"):
+        nrhs, ld = _block(x, op.N, "qtt_plan_create")
+        n2, ld2 = _block(out, op.N, "qtt_plan_create")
+        if n2 != nrhs or ld2 != ld or out.dtype != x.dtype:
+            raise QTTError(QTT_ERR_INVALID_ARG, "qtt_plan_create", "out shape/stride/dtype mismatch")
+        self.op, self.x, self.out = op, x, out  # keep the operator and buffers alive
+        h = _P()
+        _check(load_library().qtt_plan_create(ctypes.byref(h), op.handle,
+                                              ctypes.c_void_p(x.data_ptr()),
+                                              ctypes.c_void_p(out.data_ptr()), nrhs, ld,
+                                              DTYPES[_io_name(x)], DTYPES[compute]),
+               "qtt_plan_create")
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(load_library().qtt_plan_run(self.handle, _stream_handle(stream)), "qtt_plan_run")
+        return self.out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().qtt_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Operator:
     """A QTT matrix resident on the GPU (qtt_create / qtt_destroy)."""
 
@@ -197,6 +234,11 @@ class Operator:
                                         DTYPES[io], DTYPES[compute], _stream_handle(stream)),
                "qtt_apply")
         return out
+
+    def plan(self, x, out, compute: str = "f64"):
+        """Record y = A x for these two tensors as a CUDA graph (qtt_plan_create);
+        Plan.run() replays it on whatever x holds at that time."""
+        return Plan(self, x, out, compute)
 
     def residual(self, f, x, a: float = 1.0, out=None, stream=None):
         """r = f - (a x + K x) in FP64 (qtt_residual)."""
