@@ -1,4 +1,6 @@
-// Two consecutive BF16 core steps fused on the tensor cores.
+// Two consecutive BF16 core steps fused on the tensor cores (mma.sync).  The
+// apply uses it for pairs the tcgen05 pair kernel (step_tc2.cu) does not
+// take: k = 3, or ranks with r_k % 8 != 0, in [16, 48].
 //
 // Steps k and k+1 of Algorithm 2 only mix position bits k and k+1, so the
 // four positions of a "quad" (bits k, k+1 free, the others fixed) are closed
