@@ -7,7 +7,10 @@ times, on samples the oracle can afford:
 * a d = 22 request through the solve server (GMRES(30), BF16 P, FP64
   residual), its residual recomputed by the oracle;
 * the full batch of 256 uneven operators (FP32): whole outputs of the smallest
-  operators and one right-hand side of a d = 20 operator against the oracle.
+  operators and one right-hand side of a d = 20 operator against the oracle;
+* the BF16 apply of the d = 21, r_max = 48 operator to 64 right-hand sides
+  (head kernel, tcgen05 step pairs, single steps): two of the 64 outputs
+  against the oracle's FP64 apply of the same BF16 inputs.
 """
 import math
 
@@ -92,3 +95,18 @@ def test_batched_full_size_samples(qtt):
     B.close()
     for o in ops:
         o.close()
+
+
+def test_bf16_apply_full_size_samples(qtt):
+    import torch
+    data = inputs.synthetic_operator(21, 48, 3)
+    x = torch.from_numpy(inputs.gaussian_rhs(data.N, 64, 4)).to(torch.bfloat16).cuda()
+    op = qtt.Operator(data, packs=("bf16",))
+    y = op.apply(x, compute="bf16")
+    qtt.sync_status()
+    op.close()
+    for c in (0, 63):
+        xc = x[c:c + 1].double().cpu().numpy()
+        ref = oracle.apply(data, xc)
+        err = rel_l2(y[c:c + 1].double().cpu().numpy(), ref)
+        assert err <= 4 * math.sqrt(data.d) * 2.0 ** -8, (c, err)
