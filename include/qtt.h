@@ -314,8 +314,16 @@ uint64_t qtt_kernel_launches(void);
 const char *qtt_last_error(void);
 /* Synchronise `stream` and report device-side errors (QTT_ERR_CUDA for a
  * sticky CUDA error, QTT_ERR_TIMEOUT if a bounded wait in a library kernel
- * gave up). */
+ * gave up).  The status word is cleared once reported. */
 qtt_status qtt_sync_status(void *stream);
+
+/* qtt_selftest_wait -- exercises the failure path of the library's device
+ * waits without a fault (no counterpart in the paper): launches one kernel
+ * whose bounded wait, on a barrier phase that nothing completes, runs out
+ * after `seconds` (0 < seconds <= 10); the kernel records QTT_ERR_TIMEOUT in
+ * the device status word and returns, so the next qtt_sync_status(stream)
+ * returns QTT_ERR_TIMEOUT and the context stays usable. */
+qtt_status qtt_selftest_wait(double seconds, void *stream);
 
 #ifdef __cplusplus
 }

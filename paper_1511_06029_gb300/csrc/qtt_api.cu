@@ -737,6 +737,14 @@ qtt_status qtt_residual(const qtt_op *K, double a, const double *f, const double
   return apply_f64(K, x, r, nrhs, ld, static_cast<cudaStream_t>(stream), e);
 }
 
+qtt_status qtt_selftest_wait(double seconds, void *stream) {
+  if (!(seconds > 0.0 && seconds <= 10.0))
+    return fail(QTT_ERR_INVALID_ARG, "qtt_selftest_wait: seconds must be in (0, 10]");
+  const cudaError_t e = wait_selftest(seconds, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "qtt_selftest_wait");
+  return QTT_OK;
+}
+
 qtt_status qtt_sync_status(void *stream) {
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "qtt_sync_status");

@@ -52,5 +52,8 @@ cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st);
 // Device status word of the tcgen05 kernels (QTT_ERR_TIMEOUT after a bounded
 // wait gave up); returns it and clears it.
 cudaError_t tc_status_take(int *status);
+// Launch a kernel whose bounded wait runs out after about `seconds` (the
+// failure path of the tcgen05 kernels, exercised without a GPU fault).
+cudaError_t wait_selftest(double seconds, cudaStream_t st);
 
 }  // namespace qtt

@@ -233,16 +233,31 @@ __device__ __forceinline__ void mbar_arrive(unsigned a) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(a) : "memory");
 }
 // Bounded wait that also gives up once another role raised the abort flag.
-__device__ __forceinline__ bool wait_bar(unsigned a, unsigned parity, volatile int *abort) {
+__device__ __forceinline__ bool wait_bar(unsigned a, unsigned parity, volatile int *abort,
+                                         long long budget = kWaitBudget) {
   const long long t0 = clock64();
   for (;;) {
     if (mbar_try(a, parity)) return true;
     if (*abort) return false;
-    if (clock64() - t0 > kWaitBudget) {
+    if (clock64() - t0 > budget) {
       *abort = 1;
       return false;
     }
   }
+}
+
+// Self-test of the bounded waits: one thread waits, through wait_bar, for a
+// phase of an mbarrier that nothing completes; when the budget runs out it
+// records QTT_ERR_TIMEOUT in the status word and returns, as the pair
+// kernel's roles do.
+__global__ void wait_selftest_kernel(long long budget) {
+  __shared__ unsigned long long bar;
+  __shared__ int abort;
+  if (threadIdx.x != 0) return;
+  abort = 0;
+  mbar_init(su32(&bar), 1);
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  if (!wait_bar(su32(&bar), 0u, &abort, budget)) atomicCAS(&g_tc_status, 0, (int)QTT_ERR_TIMEOUT);
 }
 
 // Shared-memory plan (byte offsets from a 1024-aligned base).
@@ -600,6 +615,15 @@ cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st) {
     case 6: return launch_x<6>(tin, tout, s, S, smem, grid, st);
   }
   return cudaErrorNotSupported;
+}
+
+cudaError_t wait_selftest(double seconds, cudaStream_t st) {
+  int dev = 0, khz = 2000000;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  wait_selftest_kernel<<<1, 32, 0, st>>>((long long)(seconds * 1e3 * khz));
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t tc_status_take(int *status) {

@@ -41,6 +41,7 @@ SIGNATURES = {
     "qtt_apply": (_I, [_P, _P, _P, _L, _L, _I, _I, _P]),
     "qtt_residual": (_I, [_P, _D, _P, _P, _P, _L, _L, _P]),
     "qtt_apply_noalloc": (_I, [_P, _P, _P, _L, _L, _P]),
+    "qtt_selftest_wait": (_I, [_D, _P]),
     "qtt_plan_create": (_I, [ctypes.POINTER(_P), _P, _P, _P, _L, _L, _I, _I]),
     "qtt_plan_run": (_I, [_P, _P]),
     "qtt_plan_destroy": (_I, [_P]),
@@ -430,6 +431,13 @@ class Server:
 def kernel_launches() -> int:
     """Kernels the library has launched so far (qtt_kernel_launches)."""
     return int(load_library().qtt_kernel_launches())
+
+
+def selftest_wait(seconds: float, stream=None):
+    """Launch a kernel whose bounded device wait runs out after `seconds`
+    (qtt_selftest_wait); the next sync_status() raises QTT_ERR_TIMEOUT."""
+    _check(load_library().qtt_selftest_wait(float(seconds), _stream_handle(stream)),
+           "qtt_selftest_wait")
 
 
 def sync_status(stream=None):
