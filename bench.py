@@ -367,7 +367,8 @@ class ApplyRun:
 
     def fused_bytes(self):
         """Bytes the BF16 launches must move: the head kernel (first m steps)
-        reads r_0 and writes r_m planes; a fused pair of tensor-core steps
+        reads r_0 and writes r_m planes, the tail kernel (last t steps) reads
+        r_{d-t} planes and writes y; a fused pair of tensor-core steps
         (k, k+1) reads r_k and writes r_{k+2} planes, the planes between them
         stay on chip; every other step reads r_k and writes r_{k+1}.
         The pairing rule is the library's: k + 2 < d and either the TMA +
@@ -378,15 +379,22 @@ class ApplyRun:
         m = 0  # the head kernel: steps 0 .. m-1 (m = 2 or 3) with r_1 .. r_m <= 8
         while m < 3 and m + 1 < d.d and r[m + 1] <= 8:
             m += 1
-        if m >= 2:
+        if m < 2:
+            m = 0
+        if m:
             b += r[0] + r[m]
             ks.append(tuple(range(m)))
             k = m
-        while k < d.d:
+        t = 0  # the tail kernel: steps d-t .. d-1 (t = 2 or 3) with r_{d-t} .. r_d <= 8
+        while t < 3 and d.d - (t + 1) >= max(1, m) and r[d.d - t - 1] <= 8:
+            t += 1
+        kend = d.d - (t if t >= 2 else 0)
+        while k < kend:
+            fits = k + 2 < d.d and k + 1 < kend
             tc2 = k >= 4 and d.N >= 256 and r[k] % 8 == 0 and \
-                all(8 <= r[k + t] <= 56 for t in range(3)) if k + 2 < d.d else False
-            mma2 = k >= 3 and all(16 <= r[k + t] <= 48 for t in range(3)) \
-                and (d.N >> 2) % 8 == 0 if k + 2 < d.d else False
+                all(8 <= r[k + i] <= 56 for i in range(3)) if fits else False
+            mma2 = k >= 3 and all(16 <= r[k + i] <= 48 for i in range(3)) \
+                and (d.N >> 2) % 8 == 0 if fits else False
             if tc2 or mma2:
                 b += r[k] + r[k + 2]
                 ks.append((k, k + 1))
@@ -395,6 +403,9 @@ class ApplyRun:
                 b += r[k] + r[k + 1]
                 ks.append((k,))
                 k += 1
+        if kend < d.d:
+            b += r[kend] + r[d.d]
+            ks.append(tuple(range(kend, d.d)))
         return b * d.N * self.nrhs * 2, ks
 
     def roofline(self, mean_s):

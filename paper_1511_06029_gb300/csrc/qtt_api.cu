@@ -284,8 +284,11 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
     const int64_t nc = std::min<int64_t>(chunk, nrhs - c0);
     int src = 0;  // scratch half holding the current intermediate (k >= 1)
     int k0 = 0;
-    const std::vector<float> &hcores = A->head[mode == LP_F32 ? 0 : mode == LP_TF32 ? 1 : 2];
+    const int mi = mode == LP_F32 ? 0 : mode == LP_TF32 ? 1 : 2;
+    const std::vector<float> &hcores = A->head[mi];
     const int hm = use_fusion() && !hcores.empty() ? head_steps(A->ranks.data(), d) : 0;
+    const int tm = use_fusion() && !A->tail[mi].empty() ? tail_steps(A->ranks.data(), d, hm) : 0;
+    const int kend = d - tm;  // steps k0 .. kend-1 here, kend .. d-1 in the tail kernel
     if (hm) {
       // steps 0 .. hm-1 in one launch; y_hm lands in scratch half 0
       StepHead h;
@@ -308,8 +311,9 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
       }
       k0 = hm;
     }
-    for (int k = k0; k < d; ++k) {
-      const bool pair = tc && use_fusion() && k + 2 < d && A->mp[k] && A->mp[k + 1];
+    for (int k = k0; k < kend; ++k) {
+      const bool pair =
+          tc && use_fusion() && k + 2 < d && k + 1 < kend && A->mp[k] && A->mp[k + 1];
       const bool tc5 = pair && use_tcgen05() &&
                        tc2_steps_eligible(k, A->ranks[k], A->ranks[k + 1], A->ranks[k + 2], N);
       const bool mma2 =
@@ -414,6 +418,39 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
         return cuda_fail(e, "step_lp launch");
       }
       if (k > 0) src ^= 1;
+    }
+    if (tm) {
+      // steps kend .. d-1 in one launch: y_kend -> y (with the epilogue)
+      StepTail t;
+      std::memset(&t, 0, sizeof(t));
+      t.in = buf[src];
+      t.in_rhs_stride = (int64_t)A->ranks[kend] * N;
+      t.out = static_cast<char *>(y) + (size_t)c0 * ld * ysz;
+      t.out_rhs_stride = ld;
+      for (int s2 = 0; s2 <= tm; ++s2) t.r[s2] = A->ranks[kend + s2];
+      t.N = N;
+      t.nrhs = nc;
+      t.k0 = kend;
+      t.m = tm;
+      t.mode = mode;
+      t.out_type = yt;
+      if (epi.on) {
+        t.epi = 1;
+        t.u = epi.u ? static_cast<const char *>(epi.u) + (size_t)c0 * ld * ysz : nullptr;
+        t.v = epi.v ? static_cast<const char *>(epi.v) + (size_t)c0 * ld * ysz : nullptr;
+        t.u_rhs_stride = ld;
+        t.s_acc = epi.s_acc;
+        t.s_u = epi.s_u;
+        t.s_v = epi.s_v;
+      }
+      // cores kend .. d-1 are slots 3 - tm .. 2 of the tail copy
+      std::memcpy(t.G, A->tail[mi].data() + (size_t)(3 - tm) * 16 * 8 * 2,
+                  sizeof(float) * (size_t)tm * 16 * 8 * 2);
+      const cudaError_t e = launch_step_tail(t, st);
+      if (e != cudaSuccess) {
+        scratch_free(scratch, st);
+        return cuda_fail(e, "tail step launch");
+      }
     }
   }
   scratch_free(scratch, st);
@@ -527,26 +564,39 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores
               L[(((size_t)a * 2 + j) * rp + b) * 2 + i] = G[(((size_t)a * 2 + i) * 2 + j) * rb + b];
     }
     std::vector<float> lp(lpd.begin(), lpd.end());
-    // head-kernel copies of cores 0..2 (the same values as the packed copies)
-    auto head_copy = [&](auto value_of) {
+    // head- and tail-kernel copies of cores 0..2 and d-3..d-1 (the same values
+    // as the packed copies); a core with a rank above 8 stays zero (the
+    // kernels never take it)
+    auto small_copy = [&](int kfirst, auto value_of) {
       std::vector<float> hc(3 * 16 * 8 * 2, 0.0f);
-      for (int k = 0; k < 3 && k < d; ++k) {
-        if (ranks[k] > kHeadMaxRank || ranks[k + 1] > kHeadMaxRank) break;
+      for (int slot = 0; slot < 3; ++slot) {
+        const int k = kfirst + slot;
+        if (k < 0 || k >= d || ranks[k] > kHeadMaxRank || ranks[k + 1] > kHeadMaxRank) continue;
         const int rp = A->rpad[k + 1];
         for (int a = 0; a < ranks[k]; ++a)
           for (int j = 0; j < 2; ++j)
             for (int b = 0; b < ranks[k + 1]; ++b)
               for (int i = 0; i < 2; ++i)
-                hc[(((size_t)k * 16 + 2 * a + j) * 8 + b) * 2 + i] =
+                hc[(((size_t)slot * 16 + 2 * a + j) * 8 + b) * 2 + i] =
                     value_of(A->offlp[k] + (((int64_t)a * 2 + j) * rp + b) * 2 + i);
       }
       return hc;
     };
-    if (precision_mask & QTT_PACK_F32) A->head[0] = head_copy([&](int64_t q) { return lp[q]; });
-    if (precision_mask & QTT_PACK_TF32)
-      A->head[1] = head_copy([&](int64_t q) { return host_tf32_rne(lp[q]); });
-    if (precision_mask & QTT_PACK_BF16)
-      A->head[2] = head_copy([&](int64_t q) { return __bfloat162float(__double2bfloat16(lpd[q])); });
+    auto v32 = [&](int64_t q) { return lp[q]; };
+    auto vtf = [&](int64_t q) { return host_tf32_rne(lp[q]); };
+    auto vbf = [&](int64_t q) { return __bfloat162float(__double2bfloat16(lpd[q])); };
+    if (precision_mask & QTT_PACK_F32) {
+      A->head[0] = small_copy(0, v32);
+      A->tail[0] = small_copy(d - 3, v32);
+    }
+    if (precision_mask & QTT_PACK_TF32) {
+      A->head[1] = small_copy(0, vtf);
+      A->tail[1] = small_copy(d - 3, vtf);
+    }
+    if (precision_mask & QTT_PACK_BF16) {
+      A->head[2] = small_copy(0, vbf);
+      A->tail[2] = small_copy(d - 3, vbf);
+    }
     auto upload = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
       cudaError_t e2 = cudaMalloc(dst, bytes);
       if (e2 != cudaSuccess) return e2;

@@ -69,6 +69,9 @@ struct qtt_op {
   // (F32, TF32, BF16), [k][2a + j][b][i] with 16 x 8 x 2 floats per core;
   // empty when the first ranks are too large.
   std::vector<float> head[3];
+  // The same for the last three cores (d-3, d-2, d-1 as slots 0, 1, 2), for
+  // the tail kernel.
+  std::vector<float> tail[3];
 };
 
 // One recorded apply (qtt_plan_*): the instantiated graph and how many of

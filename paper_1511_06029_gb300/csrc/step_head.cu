@@ -212,7 +212,179 @@ cudaError_t by_input(const StepHead &s, cudaStream_t st) {
   }
 }
 
+// ------------------------------------------------------------------ tail
+// Steps d-m .. d-1 mix only position bits d-m .. d-1 (the top bits), so the
+// 2^m positions p + t 2^(d-m) (t < 2^m) are closed under them.  As in the
+// head, a lane pair holds one such group (the lane parity is the top bit),
+// steps d-m .. d-2 run in registers and step d-1 exchanges halves by
+// shuffles; the last step's FP32 result goes to y through the one-step
+// kernel's output conversion and epilogue, so the result is bitwise that of
+// m separate launches.
+
+// s_v v + s_u u + s_acc acc in the output type's precision (FP64 for FP64
+// outputs, FP32 otherwise), as the one-step kernel's last step computes it.
+__device__ __forceinline__ double tail_epi(const double *u, const double *v, int64_t p,
+                                           const StepTail &s, float acc) {
+  double t = v ? s.s_v * v[p] : 0.0;
+  if (u) t += s.s_u * u[p];
+  return t + s.s_acc * (double)acc;
+}
+__device__ __forceinline__ float tail_epi(const float *u, const float *v, int64_t p,
+                                          const StepTail &s, float acc) {
+  float t = v ? (float)s.s_v * v[p] : 0.0f;
+  if (u) t += (float)s.s_u * u[p];
+  return t + (float)s.s_acc * acc;
+}
+__device__ __forceinline__ float tail_epi(const __nv_bfloat16 *u, const __nv_bfloat16 *v,
+                                          int64_t p, const StepTail &s, float acc) {
+  float t = v ? (float)s.s_v * __bfloat162float(v[p]) : 0.0f;
+  if (u) t += (float)s.s_u * __bfloat162float(u[p]);
+  return t + (float)s.s_acc * acc;
+}
+__device__ __forceinline__ void st_out(double *p, double v) { *p = v; }
+__device__ __forceinline__ void st_out(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_out(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void st_acc(double *p, float v) { *p = (double)v; }
+__device__ __forceinline__ void st_acc(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_acc(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
+template <int MODE, typename TMID, typename TOUT, int M>
+__global__ void __launch_bounds__(kThreads, 2) step_tail_kernel(const __grid_constant__ StepTail s) {
+  constexpr int P = 1 << M;
+  constexpr int T = P / 2;
+  const int64_t lowN = (int64_t)1 << s.k0;      // positions below the tail's bits
+  const int64_t tidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = tidx < 2 * lowN;
+  const int h = (int)(tidx & 1);
+  const int64_t plow = tidx >> 1;
+  const int64_t c = blockIdx.y;
+  auto pos = [&](int q) { return plow + ((int64_t)(q + h * T) << s.k0); };
+  float y[kR][T], z[kR][T];
+  {
+    const TMID *in = static_cast<const TMID *>(s.in) + c * s.in_rhs_stride;
+#pragma unroll
+    for (int a = 0; a < kR; ++a)
+#pragma unroll
+      for (int q = 0; q < T; ++q)
+        y[a][q] = active && a < s.r[0] ? round_mode<MODE>(to_f(in[(int64_t)a * s.N + pos(q)]))
+                                       : 0.0f;
+  }
+  int rin = s.r[0];
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    const int rout = s.r[k + 1];
+#pragma unroll
+    for (int b = 0; b < kR; ++b)
+#pragma unroll
+      for (int q = 0; q < T; ++q) z[b][q] = 0.0f;
+    if (k < M - 1) {
+#pragma unroll
+      for (int a = 0; a < kR; ++a) {
+        if (a >= rin) break;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+#pragma unroll
+          for (int b = 0; b < kR; ++b) {
+            if (b >= rout) break;
+            const float g0 = s.G[k][2 * a + j][b][0], g1 = s.G[k][2 * a + j][b][1];
+#pragma unroll
+            for (int q = 0; q < T; ++q) {
+              if (((q >> k) & 1) != 0) continue;
+              const float v = y[a][q | (j << k)];
+              z[b][q] = fmaf(g0, v, z[b][q]);
+              z[b][q | (1 << k)] = fmaf(g1, v, z[b][q | (1 << k)]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < kR; ++b)
+#pragma unroll
+        for (int q = 0; q < T; ++q) y[b][q] = round_mode<MODE>(z[b][q]);
+    } else {
+#pragma unroll
+      for (int a = 0; a < kR; ++a) {
+        if (a >= rin) break;
+        float other[T];
+#pragma unroll
+        for (int q = 0; q < T; ++q) other[q] = __shfl_xor_sync(0xffffffffu, y[a][q], 1);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+#pragma unroll
+          for (int b = 0; b < kR; ++b) {
+            if (b >= rout) break;
+            const float g = h ? s.G[k][2 * a + j][b][1] : s.G[k][2 * a + j][b][0];
+#pragma unroll
+            for (int q = 0; q < T; ++q) z[b][q] = fmaf(g, j == h ? y[a][q] : other[q], z[b][q]);
+          }
+        }
+      }
+    }
+    rin = rout;
+  }
+  if (!active) return;
+  // r_d = 1: the last step's accumulators z[0][q] are y at pos(q)
+  TOUT *out = static_cast<TOUT *>(s.out) + c * s.out_rhs_stride;
+  if (s.epi) {
+    const TOUT *u = s.u ? static_cast<const TOUT *>(s.u) + c * s.u_rhs_stride : nullptr;
+    const TOUT *v = s.v ? static_cast<const TOUT *>(s.v) + c * s.u_rhs_stride : nullptr;
+#pragma unroll
+    for (int q = 0; q < T; ++q) st_out(out + pos(q), tail_epi(u, v, pos(q), s, z[0][q]));
+  } else {
+#pragma unroll
+    for (int q = 0; q < T; ++q) st_acc(out + pos(q), z[0][q]);
+  }
+}
+
+template <int MODE, typename TMID, typename TOUT>
+cudaError_t launch_tail_t(const StepTail &s, cudaStream_t st) {
+  const int64_t lanes = (int64_t)2 << s.k0;
+  const unsigned gx = (unsigned)((lanes + kThreads - 1) / kThreads);
+  for (int64_t c0 = 0; c0 < s.nrhs; c0 += 65535) {
+    StepTail t = s;
+    const int64_t nc = (s.nrhs - c0) < 65535 ? (s.nrhs - c0) : 65535;
+    t.in = static_cast<const TMID *>(s.in) + c0 * s.in_rhs_stride;
+    t.out = static_cast<TOUT *>(s.out) + c0 * s.out_rhs_stride;
+    if (t.u) t.u = static_cast<const TOUT *>(s.u) + c0 * s.u_rhs_stride;
+    if (t.v) t.v = static_cast<const TOUT *>(s.v) + c0 * s.u_rhs_stride;
+    if (s.m == 2)
+      step_tail_kernel<MODE, TMID, TOUT, 2><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
+    else
+      step_tail_kernel<MODE, TMID, TOUT, 3><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
+    count_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <int MODE, typename TMID>
+cudaError_t tail_by_output(const StepTail &s, cudaStream_t st) {
+  switch (s.out_type) {
+    case QTT_F64: return launch_tail_t<MODE, TMID, double>(s, st);
+    case QTT_BF16: return launch_tail_t<MODE, TMID, __nv_bfloat16>(s, st);
+    default: return launch_tail_t<MODE, TMID, float>(s, st);
+  }
+}
+
 }  // namespace
+
+int tail_steps(const int *ranks, int d, int head) {
+  int m = 0;
+  while (m < 3 && d - (m + 1) >= 1 && d - (m + 1) >= head && ranks[d - m - 1] <= kHeadMaxRank)
+    ++m;
+  return m >= 2 ? m : 0;
+}
+
+cudaError_t launch_step_tail(const StepTail &s, cudaStream_t st) {
+  if (s.m < 2 || s.m > 3) return cudaErrorInvalidValue;
+  switch (s.mode) {
+    case LP_F32: return tail_by_output<LP_F32, float>(s, st);
+    case LP_TF32: return tail_by_output<LP_TF32, float>(s, st);
+    case LP_BF16: return tail_by_output<LP_BF16, __nv_bfloat16>(s, st);
+  }
+  return cudaErrorInvalidValue;
+}
 
 int head_steps(const int *ranks, int d) {
   int m = 0;

@@ -58,6 +58,30 @@ struct StepHead {
 int head_steps(const int *ranks, int d);
 cudaError_t launch_step_head(const StepHead &s, cudaStream_t st);
 
+// The last m = 2 or 3 steps in one launch (step_head.cu), when r_{d-m} ..
+// r_d are all <= kHeadMaxRank: reads y_{d-m} once and writes y (any output
+// type, with the last step's epilogue).
+struct StepTail {
+  const void *in;          // y_{d-m}, the mode's intermediate type, planar
+  int64_t in_rhs_stride;
+  void *out;               // y, element type out_type, rhs stride (ld)
+  int64_t out_rhs_stride;
+  int r[4];                // ranks r_{d-m} .. r_d
+  int64_t N, nrhs;
+  int k0, m, mode;
+  qtt_dtype out_type;
+  // out = s_v v + s_u u + s_acc acc when epi (u, v of out_type, may be NULL)
+  int epi;
+  const void *u;
+  const void *v;
+  int64_t u_rhs_stride;
+  double s_acc, s_u, s_v;
+  float G[3][2 * kHeadMaxRank][kHeadMaxRank][2];  // cores d-m .. d-1, as for StepHead
+};
+// Steps the tail kernel takes (0: none), given the head's steps.
+int tail_steps(const int *ranks, int d, int head);
+cudaError_t launch_step_tail(const StepTail &s, cudaStream_t st);
+
 // Staged (cp.async, persistent) FP32/TF32 step for intermediate-to-
 // intermediate steps with k >= 2 -- see step_f32s.cu.
 bool f32s_step_eligible(const StepLP &s);

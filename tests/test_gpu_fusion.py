@@ -1,8 +1,9 @@
 """Multi-step launches against one launch per step.
 
-The head kernel (steps 0 .. m-1 in registers, ranks <= 8) follows the
-one-step kernel's numerics step by step, so its result must be bitwise the
-unfused one in every reduced precision and for every input type.  The
+The head kernel (steps 0 .. m-1 in registers, ranks <= 8) and the tail
+kernel (the last steps, ranks <= 8, writing y) follow the one-step kernel's
+numerics step by step, so their result must be bitwise the unfused one in
+every reduced precision and for every input and output type.  The
 unfused reference runs in a child process with QTT_NO_FUSION=1 (the switch
 is read once per process); one child computes every case."""
 import itertools
@@ -22,11 +23,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 TORCH = {"f64": "float64", "f32": "float32", "bf16": "bfloat16"}
 
 CASES = [
-    ([1, 2, 4, 8, 6, 1], 3),        # head of 3 steps, then 2 single steps
+    ([1, 2, 4, 8, 6, 1], 3),        # head of 3 steps, tail of 2
     ([1, 3, 5, 7, 2, 1], 2),        # uneven ranks, padded core widths
-    ([1, 2, 4, 1], 4),              # head of 2 steps (d = 3)
-    ([1, 8, 8, 8, 8, 8, 1], 1),     # rank 8 everywhere
+    ([1, 2, 4, 1], 4),              # head of 2 steps, last step single (d = 3)
+    ([1, 8, 8, 8, 8, 8, 1], 1),     # rank 8 everywhere: head of 3, tail of 3
     ([1, 2, 16, 4, 1], 2),          # r_2 > 8: no head (m would be 1)
+    ([1, 2, 4, 8, 12, 12, 8, 4, 2, 1], 2),   # head, three single steps, tail of 3
+    ([1, 4, 8, 12, 6, 3, 1], 3),    # head of 2, two single steps, tail of 2
 ]
 GRID = list(itertools.product(range(len(CASES)), ["f32", "tf32", "bf16"], ["f64", "f32", "bf16"]))
 

@@ -110,3 +110,28 @@ def test_fused_pairs_bf16_error_bound(qtt, case, nrhs):
     err = rel_l2(y.double().cpu().numpy(), oracle.apply(data, x))
     op.close()
     assert err <= 4 * math.sqrt(d) * 2.0 ** -8, err
+
+
+@pytest.mark.parametrize("d,rmax,nrhs", [(12, 16, 2), (14, 48, 1), (16, 32, 3)])
+def test_bench_byte_accounting_matches_the_launches(qtt, d, rmax, nrhs):
+    """The benchmark's HBM roofline counts the bytes of the launches the
+    library makes (head kernel, fused pairs, single steps); its plan must be
+    the dispatch the library actually performs, launch for launch."""
+    import torch
+    import bench
+    data = inputs.synthetic_operator(d, rmax, 5)
+
+    class Spec:
+        pass
+    run = Spec()
+    run.data, run.nrhs, run.compute = data, nrhs, "bf16"
+    _, plan = bench.ApplyRun.fused_bytes(run)
+    op = qtt.Operator(data, packs=("bf16",))
+    x = torch.from_numpy(inputs.gaussian_rhs(data.N, nrhs, 6)).to(torch.bfloat16).cuda()
+    op.apply(x, compute="bf16")  # first call: one-time setup outside the count
+    torch.cuda.synchronize()
+    n0 = qtt.kernel_launches()
+    op.apply(x, compute="bf16")
+    torch.cuda.synchronize()
+    op.close()
+    assert qtt.kernel_launches() - n0 == len(plan), plan
