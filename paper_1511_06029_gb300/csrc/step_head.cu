@@ -97,8 +97,12 @@ __device__ __forceinline__ void store_vec(__nv_bfloat16 *o, const float *v) {
   }
 }
 
-template <int MODE, typename TIN, typename TMID, int M>
+// HALF: the ranks are 1, 2, 4, 8 (M = 3), known at compile time, so the
+// loops over ranks unroll without bounds tests and no dead plane is zeroed
+// or rounded; otherwise they come from s.r (every rank <= 8).
+template <int MODE, typename TIN, typename TMID, int M, bool HALF>
 __global__ void __launch_bounds__(kThreads, 2) step_head_kernel(const __grid_constant__ StepHead s) {
+  static_assert(!HALF || M == 3, "the halving profile has three steps");
   constexpr int P = 1 << M;   // positions of a group
   constexpr int T = P / 2;    // positions per thread: two lanes share a group
   // lane pair (2 g, 2 g + 1) holds group g: the lane with h = 1 the positions
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__(kThreads, 2) step_head_kernel(const __grid_con
   int rin = 1;
 #pragma unroll
   for (int k = 0; k < M; ++k) {
-    const int rout = s.r[k + 1];
+    const int rout = HALF ? 2 << k : s.r[k + 1];
 #pragma unroll
     for (int b = 0; b < kR; ++b)
 #pragma unroll
@@ -193,9 +197,11 @@ cudaError_t launch_m(const StepHead &s, cudaStream_t st) {
     t.in = static_cast<const TIN *>(s.in) + c0 * s.in_rhs_stride;
     t.out = static_cast<TMID *>(s.out) + c0 * s.out_rhs_stride;
     if (s.m == 2)
-      step_head_kernel<MODE, TIN, TMID, 2><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
+      step_head_kernel<MODE, TIN, TMID, 2, false><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
+    else if (s.r[1] == 2 && s.r[2] == 4 && s.r[3] == 8)
+      step_head_kernel<MODE, TIN, TMID, 3, true><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
     else
-      step_head_kernel<MODE, TIN, TMID, 3><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
+      step_head_kernel<MODE, TIN, TMID, 3, false><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
     count_launches(1);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -248,8 +254,11 @@ __device__ __forceinline__ void st_acc(double *p, float v) { *p = (double)v; }
 __device__ __forceinline__ void st_acc(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st_acc(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
-template <int MODE, typename TMID, typename TOUT, int M>
+// HALF: the ranks are 8, 4, 2, 1 (M = 3), known at compile time (as in the
+// head kernel); otherwise they come from s.r (every rank <= 8).
+template <int MODE, typename TMID, typename TOUT, int M, bool HALF>
 __global__ void __launch_bounds__(kThreads, 2) step_tail_kernel(const __grid_constant__ StepTail s) {
+  static_assert(!HALF || M == 3, "the halving profile has three steps");
   constexpr int P = 1 << M;
   constexpr int T = P / 2;
   const int64_t lowN = (int64_t)1 << s.k0;      // positions below the tail's bits
@@ -266,13 +275,14 @@ __global__ void __launch_bounds__(kThreads, 2) step_tail_kernel(const __grid_con
     for (int a = 0; a < kR; ++a)
 #pragma unroll
       for (int q = 0; q < T; ++q)
-        y[a][q] = active && a < s.r[0] ? round_mode<MODE>(to_f(in[(int64_t)a * s.N + pos(q)]))
-                                       : 0.0f;
+        y[a][q] = active && a < (HALF ? 8 : s.r[0])
+                      ? round_mode<MODE>(to_f(in[(int64_t)a * s.N + pos(q)]))
+                      : 0.0f;
   }
-  int rin = s.r[0];
+  int rin = HALF ? 8 : s.r[0];
 #pragma unroll
   for (int k = 0; k < M; ++k) {
-    const int rout = s.r[k + 1];
+    const int rout = HALF ? 4 >> k : s.r[k + 1];
 #pragma unroll
     for (int b = 0; b < kR; ++b)
 #pragma unroll
@@ -348,9 +358,11 @@ cudaError_t launch_tail_t(const StepTail &s, cudaStream_t st) {
     if (t.u) t.u = static_cast<const TOUT *>(s.u) + c0 * s.u_rhs_stride;
     if (t.v) t.v = static_cast<const TOUT *>(s.v) + c0 * s.u_rhs_stride;
     if (s.m == 2)
-      step_tail_kernel<MODE, TMID, TOUT, 2><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
+      step_tail_kernel<MODE, TMID, TOUT, 2, false><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
+    else if (s.r[0] == 8 && s.r[1] == 4 && s.r[2] == 2)
+      step_tail_kernel<MODE, TMID, TOUT, 3, true><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
     else
-      step_tail_kernel<MODE, TMID, TOUT, 3><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
+      step_tail_kernel<MODE, TMID, TOUT, 3, false><<<dim3(gx, (unsigned)nc), kThreads, 0, st>>>(t);
     count_launches(1);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -15,7 +15,8 @@
 //             the rounding the unfused path applies when it stores y_{k+1})
 //   D2 = M_{k+1} T  in TMEM: lanes 2c + i_{k+1}, columns 64 i_k + quad
 //   O         output tile, rows (i_k, c, i_{k+1}) of 64 quads (128-byte
-//             swizzle) -- one TMA box store into y_{k+2}
+//             swizzle) -- one TMA box store into y_{k+2} (k < 6: rows (u / 64,
+//             c) of the chunk's 256 consecutive positions u)
 // Both MMAs are M = 128 (rows 2b + i; rows past 2 r are padding whose
 // results are never read), N = 128, K = 16 per instruction.  M_k and M_{k+1}
 // stay in shared memory for the CTA's lifetime (K-major, 128-byte swizzle).
@@ -32,7 +33,10 @@
 // The MN order of the stage is then (position bits k+2.., j_{k+1}, x); T and
 // the output tile use (bits k+2.., i_k, x).  The output view orders (x,
 // i_{k+1}, P, i_k, hi) so that the rows one epilogue warp writes are
-// consecutive in the swizzle pattern.  r_k % 8 == 0 makes the box's K extent
+// consecutive in the swizzle pattern.  For k < 6 a chunk's positions are 256
+// consecutive ones, so the output goes out as 128-byte rows of a 3-D view
+// (64 positions, P, position / 64) instead: the TMA engine moves about one
+// box row per 4 cycles, and rows of X < 64 values would cap the store.  r_k % 8 == 0 makes the box's K extent
 // 2 r_k the padded K of the MMA, so no plane of a neighbouring right-hand
 // side is read.
 //
@@ -174,6 +178,13 @@ __device__ __forceinline__ void tma_store5(const CUtensorMap *m, unsigned src, i
       "cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5, %6}], "
       "[%1];\n" ::"l"(m),
       "r"(src), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store3(const CUtensorMap *m, unsigned src, int c0, int c1,
+                                           int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];\n" ::"l"(m),
+      "r"(src), "r"(c0), "r"(c1), "r"(c2)
       : "memory");
 }
 __device__ __forceinline__ void expect_tx(unsigned mbar, unsigned bytes) {
@@ -479,8 +490,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_arrive(su32(&B.tready[b]));
       if (epi_any(!wait_bar(su32(&B.d2full[b]), (unsigned)(n >> 1) & 1u, abort), g)) break;
       tc_fence_after();
-      // D2 -> O[g] -> one TMA store.  D2 column n = (2 hi + i) X + x; the
-      // store box's rows are (2 hi + i, c, i_{k+1}), X values each
+      // D2 -> O[g] -> one TMA store.  D2 column n = (2 hi + i) X + x.  For
+      // k < 6 the chunk's 256 positions of a plane are consecutive, u = x +
+      // X (i + 2 i_{k+1} + 4 hi): rows (u / 64, c) of 64 values, 128-byte
+      // swizzle; else the store box's rows are (2 hi + i, c, i_{k+1}), X
+      // values each
       if (leader) bulk_wait_read0();  // the group's previous store has read O
       epi_sync(g);
       if (32 * qr < s.Mp2) {
@@ -493,8 +507,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int p = 0; p < 4; ++p) {
               const int n = 64 * half + 32 * xb + 8 * p;
               const int beta2 = n >> XLOG, x = n & (Rw::X - 1);
-              const unsigned off = (unsigned)(beta2 * orows + row) * Rw::bytes + 2u * x;
-              *reinterpret_cast<uint4 *>(O + Rw::swz(off)) = pack8(v + 8 * p);
+              if constexpr (XLOG < 6) {
+                const int u = x + Rw::X * ((beta2 & 1) + 2 * (row & 1) + 4 * (beta2 >> 1));
+                const unsigned off = (unsigned)((u >> 6) * s.r2 + (row >> 1)) * 128u + 2u * (u & 63);
+                *reinterpret_cast<uint4 *>(O + Rows<6>::swz(off)) = pack8(v + 8 * p);
+              } else {
+                const unsigned off = (unsigned)(beta2 * orows + row) * Rw::bytes + 2u * x;
+                *reinterpret_cast<uint4 *>(O + Rw::swz(off)) = pack8(v + 8 * p);
+              }
             }
           }
         }
@@ -505,8 +525,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       epi_sync(g);
       if (leader) {
         const int64_t c = t / cpr, q0 = (t % cpr) * kQ;
-        tma_store5(&tout, su32(O), (int)(q0 & lowmask), 0, (int)(c * s.r2), 0,
-                   (int)(q0 >> s.k));
+        if constexpr (XLOG < 6)
+          tma_store3(&tout, su32(O), 0, (int)(c * s.r2), (int)(q0 >> 4));
+        else
+          tma_store5(&tout, su32(O), (int)(q0 & lowmask), 0, (int)(c * s.r2), 0,
+                     (int)(q0 >> s.k));
         bulk_commit();
       }
     }
@@ -526,10 +549,29 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 constexpr size_t kSmemLimit = 227 * 1024;
 
+// The driver's tensor-map encoder, looked up through the runtime (the library
+// does not link libcuda, so it loads on machines without a driver).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  return encode;
+}
+
 // 5-D view of a planar BF16 buffer [P][N] for the pair at bit k: dims (x:
 // bits 0..k-1, a: bit `b1`, P, b: bit `b3`, hi: bits k+2..), box (X, 2, box_p,
 // 2, 64 / X) with X = 2^min(k, 6), swizzle spanning one X-value row.
 // Returns false if the driver rejects it.
+// L2 promotion: 256 bytes while a chunk's rows of a plane are contiguous
+// (k <= 6); for k > 6 they lie 2^k positions apart and the other half of a
+// 256-byte fetch belongs to a chunk another CTA reads later (it measured
+// about 30 % extra DRAM reads), so rows are fetched as single 128-byte lines.
 bool encode_view(CUtensorMap *m, const void *ptr, int k, int64_t N, int64_t planes, int b1,
                  int b3, int box_p) {
   const int xl = k < 6 ? k : 6;
@@ -543,20 +585,26 @@ bool encode_view(CUtensorMap *m, const void *ptr, int k, int64_t N, int64_t plan
                                  : xl == 4 ? CU_TENSOR_MAP_SWIZZLE_32B
                                            : CU_TENSOR_MAP_SWIZZLE_NONE;
   const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-  // the driver's encoder, looked up through the runtime (the library does not
-  // link libcuda, so it loads on machines without a driver)
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      fn = nullptr;
-    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }();
+  const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
   if (!encode) return false;
   return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(ptr), dims, strides,
                 box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                k > 6 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B : CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 3-D view of a planar BF16 buffer [P][N] as rows of 64 consecutive
+// positions: dims (e < 64, P, position / 64), box (64, box_p, 4) -- one
+// chunk's 256 consecutive positions of box_p planes, 128-byte swizzle.
+bool encode_flat(CUtensorMap *m, const void *ptr, int64_t N, int64_t planes, int box_p) {
+  const cuuint64_t dims[3] = {64, (cuuint64_t)planes, (cuuint64_t)(N >> 6)};
+  const cuuint64_t strides[2] = {(cuuint64_t)N * 2, 128};
+  const cuuint32_t box[3] = {64, (cuuint32_t)box_p, 4};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return false;
+  return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims, strides,
+                box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -602,7 +650,8 @@ cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st) {
     return cudaErrorNotSupported;
   CUtensorMap tin, tout;
   if (!encode_view(&tin, s.in, s.k, s.N, s.nrhs * s.r0, s.k, s.k + 1, s.r0) ||
-      !encode_view(&tout, s.out, s.k, s.N, s.nrhs * s.r2, s.k + 1, s.k, s.r2))
+      !(s.k < 6 ? encode_flat(&tout, s.out, s.N, s.nrhs * s.r2, s.r2)
+                : encode_view(&tout, s.out, s.k, s.N, s.nrhs * s.r2, s.k + 1, s.k, s.r2)))
     return cudaErrorNotSupported;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
