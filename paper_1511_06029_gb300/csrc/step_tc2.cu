@@ -44,11 +44,13 @@
 //   warp 0      one lane issues the TMA loads into a ring of S stages
 //   warp 1      allocates TMEM; one lane issues the MMAs: MMA1 of chunk n
 //               (frees its stage on completion) ahead of MMA2 of chunk n-1
-//   warps 2-17  two epilogue groups of eight warps; group g takes the chunks
-//               n = g (mod 2): D1 -> T[g]; D2 -> O[g] -> TMA store.  While
-//               one group waits for its MMA, the other works.
-// TMEM holds two accumulator buffers of 128 columns (chunk n uses n % 2;
-// D2 overwrites D1 of the same chunk once the epilogue has read it).
+//   warps 2-17  G epilogue groups of 16 / G warps (G = 4 where the tiles of
+//               four leave room for three ring stages, else 2); group g
+//               takes the chunks n = g (mod G): D1 -> T[g]; D2 -> O[g] ->
+//               TMA store.  While one group waits for its MMA, the others
+//               work; MMA2 of chunk n - G/2 follows MMA1 of chunk n.
+// TMEM holds G accumulator buffers of 128 columns (chunk n uses n % G; D2
+// overwrites D1 of the same chunk once the epilogue has read it).
 //
 // Every wait is bounded: a clock budget after which the CTA raises a shared
 // abort flag, every role leaves its loop, the CTA drains its copies, frees
@@ -56,6 +58,7 @@
 // qtt_sync_status) and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cstdlib>
 #include <cuda_bf16.h>
 
 #include "qtt_internal.h"
@@ -70,14 +73,13 @@ namespace {
 constexpr int kProducerWarp = 0;
 constexpr int kMmaWarp = 1;
 constexpr int kEpiWarp0 = 2;
-constexpr int kEpilogue = 256;             // threads of one epilogue group
-constexpr int kGroups = 2;                 // warps 2-9 and 10-17
-constexpr int kThreads = 64 + kGroups * kEpilogue;
+constexpr int kEpiThreads = 512;           // warps 2-17: G groups of 512 / G threads
+constexpr int kMaxGroups = 4;
+constexpr int kThreads = 64 + kEpiThreads;
 constexpr int kQ = 64;                     // quads per chunk
 constexpr int kCols = 2 * kQ;              // N of both MMAs
 constexpr int kMaxStages = 8;
-constexpr int kBarBytes = 256;             // mbarriers, TMEM address, abort flag
-constexpr int kTmemCols = 256;             // two accumulator buffers
+constexpr int kBarBytes = 512;             // mbarriers, TMEM address, abort flag
 constexpr long long kWaitBudget = 4000000000LL;  // clock64 ticks (about 2 s)
 
 __device__ __forceinline__ unsigned su32(const void *p) {
@@ -200,19 +202,21 @@ __device__ __forceinline__ void bulk_wait_read0() {
 }
 // Barrier of the epilogue warps that also ORs a flag over them: the abort
 // decision stays uniform, so no epilogue thread is left at a barrier.
-// (Named barrier 1 + g belongs to epilogue group g.)
+// (Named barrier 1 + g belongs to epilogue group g of NT threads.)
+template <int NT>
 __device__ __forceinline__ bool epi_any(bool v, int g) {
   unsigned r;
   asm volatile(
       "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n"
       " selp.u32 %0, 1, 0, q;\n}\n"
       : "=r"(r)
-      : "r"((unsigned)v), "r"(1 + g), "n"(kEpilogue)
+      : "r"((unsigned)v), "r"(1 + g), "n"(NT)
       : "memory");
   return r != 0;
 }
+template <int NT>
 __device__ __forceinline__ void epi_sync(int g) {
-  asm volatile("bar.sync %0, %1;\n" ::"r"(1 + g), "n"(kEpilogue) : "memory");
+  asm volatile("bar.sync %0, %1;\n" ::"r"(1 + g), "n"(NT) : "memory");
 }
 __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
@@ -234,7 +238,8 @@ __device__ __forceinline__ uint4 pack8(const float *v) {
 
 struct Bars {
   unsigned long long full[kMaxStages], empty[kMaxStages];
-  unsigned long long d1full[2], d2full[2], dfree[2], tready[2];
+  unsigned long long d1full[kMaxGroups], d2full[kMaxGroups], dfree[kMaxGroups],
+      tready[kMaxGroups];
   uint32_t tmem;
   int abort;
 };
@@ -284,10 +289,11 @@ __device__ __forceinline__ unsigned a_offset(int Mp, int r, int kc) {
 }
 
 struct Plan {
-  unsigned a1, a2, t0, t1, o0, o1, s0, stage, obytes, end;
+  unsigned a1, a2, t[kMaxGroups], o[kMaxGroups], s0, stage, obytes, end;
 };
 __host__ __device__ inline unsigned up1k(unsigned v) { return (v + 1023u) & ~1023u; }
-__host__ __device__ inline Plan make_plan(const StepMMA2 &s, int S) {
+// G epilogue groups (a T and an output tile each), S ring stages
+__host__ __device__ inline Plan make_plan(const StepMMA2 &s, int S, int G) {
   Plan p;
   const unsigned Kp2 = (unsigned)s.Mp1;
   // every tile 1024-aligned (the 128-byte swizzle repeats every 8 rows)
@@ -295,13 +301,13 @@ __host__ __device__ inline Plan make_plan(const StepMMA2 &s, int S) {
   p.a2 = up1k(p.a1 + a_bytes(s.Mp1, s.Kp1));
   // T[0] follows A2: the M = 128 padding rows of M_{k+1} read past A2 into
   // it (finite data; those rows are never used)
-  p.t0 = up1k(p.a2 + a_bytes(s.Mp2, (int)Kp2));
-  p.t1 = p.t0 + 2u * Kp2 * 128u;
+  p.t[0] = up1k(p.a2 + a_bytes(s.Mp2, (int)Kp2));
+  for (int g = 1; g < G; ++g) p.t[g] = p.t[g - 1] + 2u * Kp2 * 128u;
   p.obytes = (unsigned)(2 * 2 * s.r2 * 128);
-  p.o0 = up1k(p.t1 + 2u * Kp2 * 128u);
-  p.o1 = up1k(p.o0 + p.obytes);
+  p.o[0] = up1k(p.t[G - 1] + 2u * Kp2 * 128u);
+  for (int g = 1; g < G; ++g) p.o[g] = up1k(p.o[g - 1] + p.obytes);
   p.stage = (unsigned)(s.Kp1 * kCols * 2);
-  p.s0 = up1k(p.o1 + p.obytes);
+  p.s0 = up1k(p.o[G - 1] + p.obytes);
   p.end = p.s0 + (unsigned)S * p.stage;
   return p;
 }
@@ -328,15 +334,24 @@ struct Rows {
   }
 };
 
-template <int XLOG>
+// G epilogue groups of 16 / G warps (G = 2 or 4): group g takes the chunks
+// n = g (mod G) with TMEM buffer g, T[g] and O[g]; MMA2 of chunk n - G/2
+// follows MMA1 of chunk n, so a group has G/2 chunk slots to turn D1 into T
+// and as many to read D2 before its buffer is needed again.
+template <int XLOG, int G>
 __global__ void __launch_bounds__(kThreads, 1)
     step_tc2_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
                     StepMMA2 s, int S) {
   using Rw = Rows<XLOG>;
+  constexpr int kGroupThreads = kEpiThreads / G;
+  constexpr int kParts = kGroupThreads / 128;  // warps per TMEM lane quadrant in a group
+  constexpr int kColsW = kCols / kParts;       // accumulator columns per warp
+  constexpr int kLag = G / 2;
+  constexpr uint32_t kTmemCols = 128u * G;
   extern __shared__ __align__(1024) unsigned char smraw[];
   // 1024-aligned base for the swizzled tiles
   unsigned char *base = smraw + ((1024u - (su32(smraw) & 1023u)) & 1023u);
-  const Plan P = make_plan(s, S);
+  const Plan P = make_plan(s, S, G);
   Bars &B = *reinterpret_cast<Bars *>(base);
   const int Kp2 = s.Mp1;
   unsigned char *sA1 = base + P.a1, *sA2 = base + P.a2;
@@ -356,11 +371,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(su32(&B.full[i]), 1);
       mbar_init(su32(&B.empty[i]), 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < G; ++i) {
       mbar_init(su32(&B.d1full[i]), 1);
       mbar_init(su32(&B.d2full[i]), 1);
-      mbar_init(su32(&B.dfree[i]), kEpilogue);
-      mbar_init(su32(&B.tready[i]), kEpilogue);
+      mbar_init(su32(&B.dfree[i]), kGroupThreads);
+      mbar_init(su32(&B.tready[i]), kGroupThreads);
     }
     B.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -386,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t nq = s.N >> 2;
   const int64_t cpr = nq / kQ;
   const int64_t nchunks = cpr * s.nrhs;
-  const int64_t G = gridDim.x;
+  const int64_t NG = gridDim.x;
   const int lowmask = (1 << s.k) - 1;
 
   if (warp == kProducerWarp) {
@@ -394,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int n = 0;
       for (;; ++n) {
-        const int64_t t = blockIdx.x + (int64_t)n * G;
+        const int64_t t = blockIdx.x + (int64_t)n * NG;
         if (t >= nchunks) break;
         const int st = n % S;
         if (n >= S && !wait_bar(su32(&B.empty[st]), (unsigned)((n / S) - 1) & 1u, abort)) break;
@@ -415,14 +430,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------------------------------------------------------- MMA issue
     if (lane == 0) {
       const unsigned a1 = base32 + P.a1, a2 = base32 + P.a2;
-      for (int n = 0;; ++n) {
-        const int64_t t = blockIdx.x + (int64_t)n * G;
-        const bool has = t < nchunks;
-        if (has) {
-          const int st = n % S, b = n & 1;
+      // this CTA's chunks n = 0 .. mine - 1 are blockIdx.x + n gridDim.x
+      const int64_t mine = nchunks > blockIdx.x ? (nchunks - 1 - blockIdx.x) / NG + 1 : 0;
+      for (int64_t n = 0;; ++n) {
+        if (n < mine) {
+          const int st = (int)(n % S), b = (int)(n % G);
           if (!wait_bar(su32(&B.full[st]), (unsigned)(n / S) & 1u, abort)) break;
-          if (n >= 2 && !wait_bar(su32(&B.dfree[b]), (unsigned)((n >> 1) - 1) & 1u, abort))
-            break;
+          if (n >= G && !wait_bar(su32(&B.dfree[b]), (unsigned)(n / G - 1) & 1u, abort)) break;
           tc_fence_after();
           const unsigned sb = base32 + P.s0 + (unsigned)st * P.stage;
           for (int ks = 0; ks < s.Kp1 / 16; ++ks)
@@ -432,51 +446,54 @@ __global__ void __launch_bounds__(kThreads, 1)
           mma_commit(su32(&B.empty[st]));
           mma_commit(su32(&B.d1full[b]));
         }
-        if (n >= 1) {
-          const int m = n - 1, bm = m & 1;
-          if (!wait_bar(su32(&B.tready[bm]), (unsigned)(m >> 1) & 1u, abort)) break;
+        const int64_t m = n - kLag;
+        if (m >= 0 && m < mine) {
+          const int bm = (int)(m % G);
+          if (!wait_bar(su32(&B.tready[bm]), (unsigned)(m / G) & 1u, abort)) break;
           tc_fence_after();
-          const unsigned t32 = base32 + (bm ? P.t1 : P.t0);
+          const unsigned t32 = base32 + P.t[bm];
           for (int ks = 0; ks < Kp2 / 16; ++ks)
             mma_bf16(tmem + (uint32_t)(bm * 128),
                      smem_desc(a2 + (ks >> 2) * s.Mp2 * 128 + (ks & 3) * 32, 16, 1024, 2),
                      Rw::desc(t32, Kp2, ks), ks > 0);
           mma_commit(su32(&B.d2full[bm]));
         }
-        if (!has) break;
+        if (m >= mine - 1) break;
       }
     }
   } else {
     // ---------------------------------------------------------------- epilogue
-    // group g takes the chunks n = g, g + 2, ... (TMEM buffer g, T[g], O[g]),
-    // so one group's epilogue overlaps the other's MMAs
-    const int g = (warp - kEpiWarp0) >> 3;
-    const int qr = warp & 3, half = ((warp - kEpiWarp0) >> 2) & 1;
+    // group g takes the chunks n = g, g + G, ... (TMEM buffer g, T[g], O[g]),
+    // so one group's epilogue overlaps the others' MMAs.  A warp reads the
+    // TMEM lanes of its quadrant (warp % 4), columns kColsW part ..
+    const int g = (warp - kEpiWarp0) / (kGroupThreads / 32);
+    const int qr = warp & 3, part = ((warp - kEpiWarp0) >> 2) % kParts;
     const int row = 32 * qr + lane;  // TMEM lane = D row
-    const bool leader = tid == (kEpiWarp0 + 8 * g) * 32;
-    unsigned char *sT = base + (g ? P.t1 : P.t0);
-    unsigned char *O = base + (g ? P.o1 : P.o0);
-    const uint32_t tl = ((uint32_t)(32 * qr) << 16) + (uint32_t)(64 * half);
+    const bool leader = tid == (kEpiWarp0 + (kGroupThreads / 32) * g) * 32;
+    unsigned char *sT = base + P.t[g];
+    unsigned char *O = base + P.o[g];
+    const uint32_t tl = ((uint32_t)(32 * qr) << 16) + (uint32_t)(kColsW * part);
     const int orows = 2 * s.r2;
-    for (int n = g;; n += kGroups) {
-      const int64_t t = blockIdx.x + (int64_t)n * G;
+    for (int n = g;; n += G) {
+      const int64_t t = blockIdx.x + (int64_t)n * NG;
       if (t >= nchunks) break;
       const int b = g;
       const uint32_t tb = tmem + tl + (uint32_t)(b * 128);
-      if (epi_any(!wait_bar(su32(&B.d1full[b]), (unsigned)(n >> 1) & 1u, abort), g)) break;
+      if (epi_any<kGroupThreads>(!wait_bar(su32(&B.d1full[b]), (unsigned)(n / G) & 1u, abort), g))
+        break;
       tc_fence_after();
       // D1 -> T.  D1 column n = (2 hi + j') X + x (the stage's MN order);
       // T row K2 = 2b + j', its MN order (2 hi + i) X + x
       if (32 * qr < s.Mp1) {
 #pragma unroll
-        for (int xb = 0; xb < 2; ++xb) {
+        for (int xb = 0; xb < kColsW / 32; ++xb) {
           float v[32];
           tmem_ld32(tb + 32 * xb, v);
           if (row < Kp2) {
             const int i = row & 1, bb = row >> 1;
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
-              const int n = 64 * half + 32 * xb + 8 * p;
+              const int n = kColsW * part + 32 * xb + 8 * p;
               const int beta = n >> XLOG, x = n & (Rw::X - 1);
               const int k2 = 2 * bb + (beta & 1), beta2 = (beta & ~1) | i;
               const unsigned off = (unsigned)(beta2 * Kp2 + k2) * Rw::bytes + 2u * x;
@@ -488,7 +505,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(su32(&B.tready[b]));
-      if (epi_any(!wait_bar(su32(&B.d2full[b]), (unsigned)(n >> 1) & 1u, abort), g)) break;
+      if (epi_any<kGroupThreads>(!wait_bar(su32(&B.d2full[b]), (unsigned)(n / G) & 1u, abort), g))
+        break;
       tc_fence_after();
       // D2 -> O[g] -> one TMA store.  D2 column n = (2 hi + i) X + x.  For
       // k < 6 the chunk's 256 positions of a plane are consecutive, u = x +
@@ -496,16 +514,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       // swizzle; else the store box's rows are (2 hi + i, c, i_{k+1}), X
       // values each
       if (leader) bulk_wait_read0();  // the group's previous store has read O
-      epi_sync(g);
+      epi_sync<kGroupThreads>(g);
       if (32 * qr < s.Mp2) {
 #pragma unroll
-        for (int xb = 0; xb < 2; ++xb) {
+        for (int xb = 0; xb < kColsW / 32; ++xb) {
           float v[32];
           tmem_ld32(tb + 32 * xb, v);
           if (row < orows) {
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
-              const int n = 64 * half + 32 * xb + 8 * p;
+              const int n = kColsW * part + 32 * xb + 8 * p;
               const int beta2 = n >> XLOG, x = n & (Rw::X - 1);
               if constexpr (XLOG < 6) {
                 const int u = x + Rw::X * ((beta2 & 1) + 2 * (row & 1) + 4 * (beta2 >> 1));
@@ -522,7 +540,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       mbar_arrive(su32(&B.dfree[b]));
       fence_async_smem();
-      epi_sync(g);
+      epi_sync<kGroupThreads>(g);
       if (leader) {
         const int64_t c = t / cpr, q0 = (t % cpr) * kQ;
         if constexpr (XLOG < 6)
@@ -613,16 +631,33 @@ bool encode_flat(CUtensorMap *m, const void *ptr, int64_t N, int64_t planes, int
 
 namespace {
 
-template <int XLOG>
+template <int XLOG, int G>
 cudaError_t launch_x(const CUtensorMap &tin, const CUtensorMap &tout, const StepMMA2 &s, int S,
                      size_t smem, unsigned grid, cudaStream_t st) {
   // one CTA per SM: the shared-memory limit is raised once per instantiation
   static cudaError_t attr = cudaFuncSetAttribute(
-      step_tc2_kernel<XLOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+      step_tc2_kernel<XLOG, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
   if (attr != cudaSuccess) return attr;
-  step_tc2_kernel<XLOG><<<grid, kThreads, smem, st>>>(tin, tout, s, S);
+  step_tc2_kernel<XLOG, G><<<grid, kThreads, smem, st>>>(tin, tout, s, S);
   count_launches(1);
   return cudaGetLastError();
+}
+
+// Ring stages that fit beside the tiles of G groups (0 if fewer than two).
+int stages_for(const StepMMA2 &s, int G) {
+  const Plan p0 = make_plan(s, 0, G);
+  if (p0.end + 2 * p0.stage + 1024 > kSmemLimit) return 0;
+  const int S = (int)((kSmemLimit - 1024 - p0.end) / p0.stage);
+  return S > kMaxStages ? kMaxStages : S;
+}
+
+// QTT_TC2_GROUPS=2 keeps two epilogue groups everywhere (for comparisons).
+bool four_groups_allowed() {
+  static const bool ok = [] {
+    const char *e = getenv("QTT_TC2_GROUPS");
+    return !(e && e[0] == '2');
+  }();
+  return ok;
 }
 
 }  // namespace
@@ -638,12 +673,17 @@ bool tc2_steps_eligible(int k, int r0, int r1, int r2, int64_t N) {
 }
 
 cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st) {
-  // as many ring stages as the shared memory holds
-  const Plan p0 = make_plan(s, 0);
-  if (p0.end + 2 * p0.stage + 1024 > kSmemLimit) return cudaErrorNotSupported;
-  int S = (int)((kSmemLimit - 1024 - p0.end) / p0.stage);
-  if (S > kMaxStages) S = kMaxStages;
-  const size_t smem = make_plan(s, S).end + 1024;
+  // Four epilogue groups (four chunks between their MMAs at once) where
+  // their tiles leave room for at least three ring stages -- the small-rank
+  // pairs, whose time per chunk is set by the MMA -> epilogue -> MMA chain
+  // rather than by bytes; else two.  As many ring stages as fit.
+  int G = 4, S = four_groups_allowed() ? stages_for(s, 4) : 0;
+  if (S < 3) {
+    G = 2;
+    S = stages_for(s, 2);
+  }
+  if (S < 2) return cudaErrorNotSupported;
+  const size_t smem = make_plan(s, S, G).end + 1024;
   // the input view needs the buffer to hold exactly nrhs right-hand sides of r_k
   // planes each, back to back (as the apply's scratch does)
   if (s.in_rhs_stride != (int64_t)s.r0 * s.N || s.out_rhs_stride != (int64_t)s.r2 * s.N)
@@ -658,10 +698,19 @@ cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t nchunks = (s.N >> 2) / kQ * s.nrhs;
   const unsigned grid = (unsigned)(nchunks < sms ? nchunks : sms);
-  switch (s.k < 6 ? s.k : 6) {
-    case 4: return launch_x<4>(tin, tout, s, S, smem, grid, st);
-    case 5: return launch_x<5>(tin, tout, s, S, smem, grid, st);
-    case 6: return launch_x<6>(tin, tout, s, S, smem, grid, st);
+  const int xl = s.k < 6 ? s.k : 6;
+  if (G == 4) {
+    switch (xl) {
+      case 4: return launch_x<4, 4>(tin, tout, s, S, smem, grid, st);
+      case 5: return launch_x<5, 4>(tin, tout, s, S, smem, grid, st);
+      case 6: return launch_x<6, 4>(tin, tout, s, S, smem, grid, st);
+    }
+  } else {
+    switch (xl) {
+      case 4: return launch_x<4, 2>(tin, tout, s, S, smem, grid, st);
+      case 5: return launch_x<5, 2>(tin, tout, s, S, smem, grid, st);
+      case 6: return launch_x<6, 2>(tin, tout, s, S, smem, grid, st);
+    }
   }
   return cudaErrorNotSupported;
 }

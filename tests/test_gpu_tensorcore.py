@@ -95,6 +95,54 @@ def test_fused_pairs_integer_exact(qtt, ranks, nrhs):
     assert np.array_equal(y, oracle.apply(data, x))
 
 
+@pytest.mark.parametrize("ranks,nrhs", [
+    ([1, 2, 4, 8, 16, 32, 32, 32, 32, 32, 32, 32, 16, 8, 8, 8, 4, 2, 1], 3),   # four groups
+    ([1, 2, 4, 8, 16, 48, 48, 48, 48, 40, 32, 24, 16, 16, 8, 8, 4, 2, 1], 2),  # two and four
+])
+def test_fused_pairs_integer_exact_many_chunks(qtt, ranks, nrhs):
+    """d = 18: thousands of 64-quad chunks, so every CTA of the pair kernel
+    cycles each ring stage, TMEM buffer and epilogue group many times."""
+    import torch
+    d = len(ranks) - 1
+    data = _rank_diagonal_operator(d, 0, sum(ranks) + 1, ranks=ranks)
+    x = np.random.default_rng(d + 1).integers(-1, 2, size=(nrhs, 1 << d)).astype(np.float64)
+    op = qtt.Operator(data, packs=("bf16",))
+    y = op.apply(torch.from_numpy(x).float().cuda(), compute="bf16").double().cpu().numpy()
+    qtt.sync_status()
+    op.close()
+    assert np.array_equal(y, oracle.apply(data, x))
+
+
+GROUPS_CHILD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1511_06029_gb300 import inputs, qtt
+data = inputs.synthetic_operator(18, 32, 31)
+x = torch.from_numpy(inputs.gaussian_rhs(data.N, 3, 32)).to(torch.bfloat16).cuda()
+op = qtt.Operator(data, packs=("bf16",))
+np.save(sys.argv[2], op.apply(x, compute="bf16").float().cpu().numpy())
+op.close()
+"""
+
+
+def test_epilogue_group_count_is_bitwise_neutral(qtt, tmp_path):
+    """Four epilogue groups (ranks <= 32) against two (QTT_TC2_GROUPS=2): the
+    group count only schedules, so the results agree bit for bit."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for groups in ("4", "2"):
+        f = tmp_path / f"y{groups}.npy"
+        env = dict(os.environ, QTT_TC2_GROUPS=groups)
+        r = subprocess.run([sys.executable, "-c", GROUPS_CHILD, root, str(f)], env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs.append(np.load(f))
+    assert np.array_equal(outs[0].view(np.uint32), outs[1].view(np.uint32))
+
+
 @pytest.mark.parametrize("case,nrhs", [
     ([1, 2, 4, 16, 16, 16, 1], 2), ([1, 3, 8, 24, 40, 31, 48, 17, 1], 3), (11, 3), (20, 2)])
 def test_fused_pairs_bf16_error_bound(qtt, case, nrhs):
