@@ -484,6 +484,10 @@ extern "C" qtt_status qtt_solve(const qtt_op *K, const qtt_op *P, const double *
   if (s != QTT_OK) return s;
   if (prm->kind != QTT_SOLVE_DIRECT)
     for (int64_t k = 0; k < nrhs; ++k)
-      if (info[k].status != QTT_OK) return QTT_ERR_NOT_CONVERGED;
+      if (info[k].status != QTT_OK)
+        return fail(QTT_ERR_NOT_CONVERGED,
+                    "qtt_solve: right-hand side " + std::to_string(k) + " ended at relative residual " +
+                        std::to_string(info[k].rel_residual) + " after " +
+                        std::to_string(info[k].iters) + " iterations");
   return QTT_OK;
 }
