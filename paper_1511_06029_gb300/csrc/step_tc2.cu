@@ -79,6 +79,7 @@ constexpr int kThreads = 64 + kEpiThreads;
 constexpr int kQ = 64;                     // quads per chunk
 constexpr int kCols = 2 * kQ;              // N of both MMAs
 constexpr int kMaxStages = 8;
+constexpr int kMaxKs = 7;                  // K steps of 16: 2 r rounded up to 16, r <= 56
 constexpr int kBarBytes = 512;             // mbarriers, TMEM address, abort flag
 constexpr long long kWaitBudget = 4000000000LL;  // clock64 ticks (about 2 s)
 
@@ -235,6 +236,25 @@ __device__ __forceinline__ uint4 pack8(const float *v) {
   o.w = *reinterpret_cast<unsigned *>(&h);
   return o;
 }
+
+// Walk over chunks t0, t0 + step, ...: t = c cpr + w (right-hand side c,
+// chunk w of it), advanced by an addition and at most one carry per step.
+struct ChunkWalk {
+  int64_t t, c, w, dc, dw, cpr;
+  __device__ ChunkWalk(int64_t t0, int64_t step, int64_t cpr_)
+      : t(t0), c(t0 / cpr_), w(t0 % cpr_), dc(step / cpr_), dw(step % cpr_), cpr(cpr_) {}
+  __device__ void next() {
+    t += dc * cpr + dw;
+    c += dc;
+    w += dw;
+    if (w >= cpr) {
+      w -= cpr;
+      ++c;
+    }
+  }
+};
+
+static_assert((2 * kTc2MaxRank + 15) / 16 <= kMaxKs, "K steps of the largest rank");
 
 struct Bars {
   unsigned long long full[kMaxStages], empty[kMaxStages];
@@ -407,17 +427,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == kProducerWarp) {
     // ---------------------------------------------------------------- TMA loads
     if (lane == 0) {
-      int n = 0;
-      for (;; ++n) {
-        const int64_t t = blockIdx.x + (int64_t)n * NG;
-        if (t >= nchunks) break;
-        const int st = n % S;
-        if (n >= S && !wait_bar(su32(&B.empty[st]), (unsigned)((n / S) - 1) & 1u, abort)) break;
-        const int64_t c = t / cpr, q0 = (t % cpr) * kQ;
+      // chunk t = blockIdx.x + n gridDim.x is (rhs c, chunk w of it); both
+      // advance without a division per chunk, as do the ring slot and parity
+      ChunkWalk cw(blockIdx.x, NG, cpr);
+      int n = 0, st = 0;
+      unsigned ph = 0;
+      for (;; ++n, cw.next()) {
+        if (cw.t >= nchunks) break;
+        if (n >= S && !wait_bar(su32(&B.empty[st]), ph ^ 1u, abort)) break;
+        const int64_t q0 = cw.w * kQ;
         const unsigned fb = su32(&B.full[st]);
         expect_tx(fb, P.stage);
         tma_load5(base32 + P.s0 + (unsigned)st * P.stage, &tin, (int)(q0 & lowmask), 0,
-                  (int)(c * s.r0), 0, (int)(q0 >> s.k), fb);
+                  (int)(cw.c * s.r0), 0, (int)(q0 >> s.k), fb);
+        if (++st == S) {
+          st = 0;
+          ph ^= 1u;
+        }
       }
       if (*abort) {
         // loads still in flight land before the CTA's shared memory goes
@@ -429,33 +455,57 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------------- MMA issue
     if (lane == 0) {
-      const unsigned a1 = base32 + P.a1, a2 = base32 + P.a2;
+      // Descriptors: every field but the start address (bits 0-13, the
+      // shared address >> 4) is fixed per operand, so each MMA ORs the
+      // masked start into a template -- the same value smem_desc gives.
+      // Per K step of 16: A moves 32 bytes within a 128-byte swizzle atom,
+      // Mp rows of 128 bytes per atom of 64; B moves 16 rows of its tile.
+      constexpr unsigned kBStep = Rw::B == 0 ? 256u : 16u * Rw::bytes;  // bytes per K step
+      const int nk1 = s.Kp1 / 16, nk2 = Kp2 / 16;
+      const uint64_t tA = smem_desc(0, 16, 1024, 2);
+      const uint64_t tS = Rw::desc(0, s.Kp1, 0), tT = Rw::desc(0, Kp2, 0);
+      unsigned aA1[kMaxKs], aA2[kMaxKs];
+#pragma unroll
+      for (int ks = 0; ks < kMaxKs; ++ks) {
+        aA1[ks] = base32 + P.a1 + (unsigned)((ks >> 2) * s.Mp1 * 128 + (ks & 3) * 32);
+        aA2[ks] = base32 + P.a2 + (unsigned)((ks >> 2) * s.Mp2 * 128 + (ks & 3) * 32);
+      }
       // this CTA's chunks n = 0 .. mine - 1 are blockIdx.x + n gridDim.x
-      const int64_t mine = nchunks > blockIdx.x ? (nchunks - 1 - blockIdx.x) / NG + 1 : 0;
-      for (int64_t n = 0;; ++n) {
+      const int mine = nchunks > blockIdx.x ? (int)((nchunks - 1 - blockIdx.x) / NG + 1) : 0;
+      int st = 0;
+      unsigned ph = 0;  // ring slot of chunk n and the parity of its fill
+      for (int n = 0;; ++n) {
         if (n < mine) {
-          const int st = (int)(n % S), b = (int)(n % G);
-          if (!wait_bar(su32(&B.full[st]), (unsigned)(n / S) & 1u, abort)) break;
+          const int b = n % G;
+          if (!wait_bar(su32(&B.full[st]), ph, abort)) break;
           if (n >= G && !wait_bar(su32(&B.dfree[b]), (unsigned)(n / G - 1) & 1u, abort)) break;
           tc_fence_after();
           const unsigned sb = base32 + P.s0 + (unsigned)st * P.stage;
-          for (int ks = 0; ks < s.Kp1 / 16; ++ks)
-            mma_bf16(tmem + (uint32_t)(b * 128),
-                     smem_desc(a1 + (ks >> 2) * s.Mp1 * 128 + (ks & 3) * 32, 16, 1024, 2),
-                     Rw::desc(sb, s.Kp1, ks), ks > 0);
+          const uint32_t d = tmem + (uint32_t)(b * 128);
+#pragma unroll
+          for (int ks = 0; ks < kMaxKs; ++ks)
+            if (ks < nk1)
+              mma_bf16(d, tA | ((aA1[ks] >> 4) & 0x3FFFu), tS | (((sb + ks * kBStep) >> 4) & 0x3FFFu),
+                       ks > 0);
           mma_commit(su32(&B.empty[st]));
           mma_commit(su32(&B.d1full[b]));
+          if (++st == S) {
+            st = 0;
+            ph ^= 1u;
+          }
         }
-        const int64_t m = n - kLag;
+        const int m = n - kLag;
         if (m >= 0 && m < mine) {
-          const int bm = (int)(m % G);
+          const int bm = m % G;
           if (!wait_bar(su32(&B.tready[bm]), (unsigned)(m / G) & 1u, abort)) break;
           tc_fence_after();
           const unsigned t32 = base32 + P.t[bm];
-          for (int ks = 0; ks < Kp2 / 16; ++ks)
-            mma_bf16(tmem + (uint32_t)(bm * 128),
-                     smem_desc(a2 + (ks >> 2) * s.Mp2 * 128 + (ks & 3) * 32, 16, 1024, 2),
-                     Rw::desc(t32, Kp2, ks), ks > 0);
+          const uint32_t d = tmem + (uint32_t)(bm * 128);
+#pragma unroll
+          for (int ks = 0; ks < kMaxKs; ++ks)
+            if (ks < nk2)
+              mma_bf16(d, tA | ((aA2[ks] >> 4) & 0x3FFFu), tT | (((t32 + ks * kBStep) >> 4) & 0x3FFFu),
+                       ks > 0);
           mma_commit(su32(&B.d2full[bm]));
         }
         if (m >= mine - 1) break;
@@ -474,9 +524,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char *O = base + P.o[g];
     const uint32_t tl = ((uint32_t)(32 * qr) << 16) + (uint32_t)(kColsW * part);
     const int orows = 2 * s.r2;
-    for (int n = g;; n += G) {
-      const int64_t t = blockIdx.x + (int64_t)n * NG;
-      if (t >= nchunks) break;
+    ChunkWalk cw(blockIdx.x + (int64_t)g * NG, (int64_t)G * NG, cpr);
+    for (int n = g;; n += G, cw.next()) {
+      if (cw.t >= nchunks) break;
       const int b = g;
       const uint32_t tb = tmem + tl + (uint32_t)(b * 128);
       if (epi_any<kGroupThreads>(!wait_bar(su32(&B.d1full[b]), (unsigned)(n / G) & 1u, abort), g))
@@ -542,11 +592,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       fence_async_smem();
       epi_sync<kGroupThreads>(g);
       if (leader) {
-        const int64_t c = t / cpr, q0 = (t % cpr) * kQ;
+        const int64_t q0 = cw.w * kQ;
         if constexpr (XLOG < 6)
-          tma_store3(&tout, su32(O), 0, (int)(c * s.r2), (int)(q0 >> 4));
+          tma_store3(&tout, su32(O), 0, (int)(cw.c * s.r2), (int)(q0 >> 4));
         else
-          tma_store5(&tout, su32(O), (int)(q0 & lowmask), 0, (int)(c * s.r2), 0,
+          tma_store5(&tout, su32(O), (int)(q0 & lowmask), 0, (int)(cw.c * s.r2), 0,
                      (int)(q0 >> s.k));
         bulk_commit();
       }
