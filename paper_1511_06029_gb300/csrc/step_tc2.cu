@@ -36,14 +36,17 @@
 // consecutive in the swizzle pattern.  For k < 6 a chunk's positions are 256
 // consecutive ones, so the output goes out as 128-byte rows of a 3-D view
 // (64 positions, P, position / 64) instead: the TMA engine moves about one
-// box row per 4 cycles, and rows of X < 64 values would cap the store.  r_k % 8 == 0 makes the box's K extent
-// 2 r_k the padded K of the MMA, so no plane of a neighbouring right-hand
-// side is read.
+// box row per 4 cycles, and rows of X < 64 values would cap the store.
+// r_k % 8 == 0 makes the box's K extent 2 r_k the padded K of the MMA, so no
+// plane of a neighbouring right-hand side is read.
 //
 // Warp roles, connected by mbarriers (a software pipeline over chunks):
 //   warp 0      one lane issues the TMA loads into a ring of S stages
 //   warp 1      allocates TMEM; one lane issues the MMAs: MMA1 of chunk n
-//               (frees its stage on completion) ahead of MMA2 of chunk n-1
+//               (frees its stage on completion) ahead of MMA2 of chunk
+//               n - G/2.  This thread sets the pace, so its per-MMA work is
+//               one OR of the start address into a descriptor template and
+//               chunks and ring slots advance by counters (no divisions)
 //   warps 2-17  G epilogue groups of 16 / G warps (G = 4 where the tiles of
 //               four leave room for three ring stages, else 2); group g
 //               takes the chunks n = g (mod G): D1 -> T[g]; D2 -> O[g] ->
