@@ -144,6 +144,23 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(dist, v: float, device) -> float:
+    """The largest of every rank's v (an all-reduce MAX over the process
+    group); v itself when there is no group."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(work_per_step: float, steps: int, world: int, t_max: float) -> float:
+    """Whole-job throughput of `world` replicas: all ranks' work over the
+    slowest rank's time."""
+    return work_per_step * steps * world / t_max
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -834,12 +851,8 @@ def run_ours(args, spec):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(v):
+        return max_over_ranks(dist, v, "cuda")
 
     from paper_1511_06029_gb300 import qtt as _q
     for _ in range(args.warmup):
@@ -864,8 +877,8 @@ def run_ours(args, spec):
     clocks = sampler.stop()
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_s = ev[0].elapsed_time(ev[-1]) / 1e3
-    t_max = max_over_ranks(total_s)
-    value = run.work() * args.steps * world / t_max
+    t_max = slowest(total_s)
+    value = job_value(run.work(), args.steps, world, t_max)
 
     # end to end through the public API with pinned host buffers
     for _ in range(max(1, min(args.warmup, 2))):
@@ -878,7 +891,7 @@ def run_ours(args, spec):
         run.e2e_step()
     e1.record()
     torch.cuda.synchronize()
-    e2e_t = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    e2e_t = slowest(e0.elapsed_time(e1) / 1e3)
     h2d, d2h = run.e2e_bytes()
 
     line = {
@@ -891,7 +904,7 @@ def run_ours(args, spec):
         "roofline": dict(run.roofline(total_s / args.steps),
                          step_ms_min=min(step_ms), step_ms_max=max(step_ms)),
         "clocks": clocks,
-        "e2e": {"value": run.work() * args.steps * world / e2e_t, "unit": run.unit,
+        "e2e": {"value": job_value(run.work(), args.steps, world, e2e_t), "unit": run.unit,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "result_matches_device": run.e2e_check()},
         # kernels of libqtt launched in the timed region (library counter); a
