@@ -33,6 +33,11 @@ Function -> passage it follows:
   solve_gmres       right-preconditioned GMRES(m) (Sec. 5.3: QTT inverse of
                     the preconditioned system used inside GMRES)
   power_norm        ||K||_2 by power iteration on K^T K
+  vec_full          dense vector of a QTT vector (Sec. 2.2 entry formula)
+  apply_tt          compressed matrix-vector product c = A b, QTT vector in
+                    and out (Sec. 4.2, compressed product equation)
+  tt_round          TT rounding with the Algorithm 1 threshold per unfolding
+                    (orthogonalisation, then truncated SVDs; numpy QR/SVD)
 """
 from __future__ import annotations
 
@@ -311,3 +316,87 @@ def power_norm(op, v0, max_iter: int = 100, rtol: float = 1e-6, threads: int = 0
                              ctypes.byref(sigma), ctypes.byref(it), threads),
            "power_norm")
     return sigma.value, it.value
+
+
+# ------------------------------------------------- compressed vectors (numpy)
+# A QTT vector has .ranks (s_0 = s_d = 1) and .cores shaped (s_k, 2, s_{k+1}),
+# element t = G_1[:, t_1, :] ... G_d[:, t_d, :] with t_k bit k of t (least
+# significant first, as for the operators).
+
+class Vec:
+    """Minimal QTT-vector container for results built by the oracle."""
+
+    def __init__(self, ranks, cores):
+        self.ranks = [int(v) for v in ranks]
+        self.cores = cores
+
+    @property
+    def d(self):
+        return len(self.ranks) - 1
+
+
+def vec_full(v) -> np.ndarray:
+    """Dense vector of a QTT vector from the entry formula (Sec. 2.2):
+    contracted last core first; the row index of the running block is the
+    already-placed low bits."""
+    d = len(v.ranks) - 1
+    # block[t_high, alpha]: entries over the bits k..d-1, for rank alpha_k
+    block = np.asarray(v.cores[d - 1], dtype=np.float64)[:, :, 0].T  # (2, s_{d-1})
+    for k in range(d - 2, -1, -1):
+        G = np.asarray(v.cores[k], dtype=np.float64)  # (s_k, 2, s_{k+1})
+        # new index = t_k + 2 * t_high: bit k is the least significant here
+        nb = np.einsum("aib,hb->hia", G, block)  # (high, t_k, s_k)
+        block = nb.reshape(-1, G.shape[0])
+    return block[:, 0]
+
+
+def apply_tt(A, v) -> Vec:
+    """Compressed matrix-vector product c = A b (Sec. 4.2, the compressed
+    product equation): core k of c is, for every merged rank pair, the sum
+    over j_k of A's core slice (alpha_{k-1}, i_k j_k, alpha_k) times b's
+    (beta_{k-1}, j_k, beta_k); the pair (alpha, beta) becomes one rank index
+    alpha s + beta, so the ranks multiply."""
+    d = len(A.ranks) - 1
+    if len(v.ranks) - 1 != d:
+        raise OracleError("operator and vector have different d")
+    cores = []
+    for k in range(d):
+        GA = np.asarray(A.cores[k], dtype=np.float64)  # (r, 2 i, 2 j, r')
+        Gb = np.asarray(v.cores[k], dtype=np.float64)  # (s, 2 j, s')
+        C = np.einsum("aijc,bje->abice", GA, Gb)
+        r, s, _, rc, se = C.shape
+        cores.append(C.reshape(r * s, 2, rc * se))
+    return Vec([a * b for a, b in zip(A.ranks, v.ranks)], cores)
+
+
+def tt_round(t, eps: float):
+    """TT rounding of an operator or a vector: left-to-right QR
+    orthogonalisation, then right-to-left truncated SVDs, each keeping the
+    smallest rank whose discarded singular values have 2-norm <= eps
+    ||t||_F / sqrt(d-1) (the threshold of Algorithm 1), so that
+    ||t - round(t)||_F <= eps ||t||_F.  Returns the same kind of object."""
+    d = len(t.ranks) - 1
+    is_op = np.asarray(t.cores[0]).ndim == 4
+    cores = [np.asarray(c, dtype=np.float64).reshape(c.shape[0], -1, c.shape[-1]).copy()
+             for c in t.cores]
+    # left-to-right: cores 0 .. d-2 become left-orthonormal
+    for k in range(d - 1):
+        ra, n, rb = cores[k].shape
+        Q, R = np.linalg.qr(cores[k].reshape(ra * n, rb))
+        cores[k] = Q.reshape(ra, n, Q.shape[1])
+        nxt = cores[k + 1]
+        cores[k + 1] = np.einsum("ab,bnc->anc", R, nxt)
+    delta = eps * np.linalg.norm(cores[d - 1]) / np.sqrt(max(d - 1, 1))
+    # right-to-left: truncate the unfolding between cores k-1 and k
+    for k in range(d - 1, 0, -1):
+        ra, n, rb = cores[k].shape
+        U, S, Vt = np.linalg.svd(cores[k].reshape(ra, n * rb), full_matrices=False)
+        keep = len(S)
+        while keep > 1 and np.sqrt(np.sum(S[keep - 1:] ** 2)) <= delta:
+            keep -= 1
+        cores[k] = Vt[:keep].reshape(keep, n, rb)
+        cores[k - 1] = np.einsum("pna,ab->pnb", cores[k - 1], U[:, :keep] * S[:keep])
+    ranks = [1] + [c.shape[2] for c in cores[:-1]] + [1]
+    if is_op:
+        return Op(ranks, [c.reshape(c.shape[0], 2, 2, c.shape[2]) for c in cores])
+    return Vec(ranks, cores)

@@ -252,3 +252,98 @@ def test_entries_match_dense(oracle_mod):
     I = rng.integers(0, 512, size=300)
     J = rng.integers(0, 512, size=300)
     assert np.allclose(oracle_mod.entries(op, I, J), A[I, J], rtol=1e-13, atol=1e-15)
+
+
+# ------------------------------------------- compressed vectors and rounding
+def _random_vec(oracle_mod, d, ranks, seed):
+    rng = np.random.default_rng(seed)
+    cores = [rng.standard_normal((ranks[k], 2, ranks[k + 1])) for k in range(d)]
+    return oracle_mod.Vec(ranks, cores)
+
+
+def _vec_dense_bruteforce(v):
+    """Entry formula element by element (Sec. 2.2): t's bits pick one slice
+    of each core; small d only."""
+    d = len(v.ranks) - 1
+    out = np.empty(1 << d)
+    for t in range(1 << d):
+        m = np.eye(1)
+        for k in range(d):
+            m = m @ v.cores[k][:, (t >> k) & 1, :]
+        out[t] = m[0, 0]
+    return out
+
+
+def test_qtt_vector_entries(oracle_mod):
+    """vec_full against the entry formula and, for rank 1, numpy's kron."""
+    v = _random_vec(oracle_mod, 6, [1, 2, 3, 3, 2, 2, 1], 40)
+    assert rel_l2(oracle_mod.vec_full(v), _vec_dense_bruteforce(v)) <= 1e-14
+    rng = np.random.default_rng(41)
+    parts = [rng.standard_normal(2) for _ in range(5)]
+    kron = parts[-1]
+    for p in parts[-2::-1]:
+        kron = np.kron(kron, p)  # bit 0 (first core) varies fastest
+    v1 = oracle_mod.Vec([1] * 6, [p.reshape(1, 2, 1) for p in parts])
+    assert np.array_equal(oracle_mod.vec_full(v1), kron)
+
+
+@pytest.mark.parametrize("d,seed", [(6, 42), (9, 43)])
+def test_compressed_matvec_matches_dense(oracle_mod, d, seed):
+    """Sec. 4.2 compressed product: the full vector of A b equals the dense
+    matrix (numpy slice products) times the full vector b; ranks multiply."""
+    rng = np.random.default_rng(seed)
+    ra = [1] + list(rng.integers(1, 5, d - 1)) + [1]
+    rb = [1] + list(rng.integers(1, 4, d - 1)) + [1]
+    A = inputs.random_cores(d, ra, seed)
+    b = _random_vec(oracle_mod, d, rb, seed + 100)
+    c = oracle_mod.apply_tt(A, b)
+    assert c.ranks == [x * y for x, y in zip(ra, rb)]
+    ref = oracle_mod.dense(A) @ _vec_dense_bruteforce(b)
+    assert rel_l2(oracle_mod.vec_full(c), ref) <= 1e-13
+
+
+@pytest.mark.parametrize("eps", [1e-1, 1e-3, 1e-6])
+def test_rounding_error_bound(oracle_mod, eps):
+    """||T - round(T)||_F <= eps ||T||_F (the Algorithm 1 threshold per
+    unfolding, d - 1 unfoldings), ranks never above the input's."""
+    d = 7
+    A = inputs.random_cores(d, [1, 2, 4, 6, 6, 4, 2, 1], 44)
+    B = inputs.random_cores(d, [1, 2, 3, 5, 3, 3, 2, 1], 45)
+    T = oracle_mod.tt_sum(A, B)
+    R = oracle_mod.tt_round(T, eps)
+    full_t, full_r = oracle_mod.dense(T), oracle_mod.dense(R)
+    err = np.linalg.norm(full_t - full_r) / np.linalg.norm(full_t)
+    assert err <= eps * (1 + 1e-10), err
+    assert all(r <= t for r, t in zip(R.ranks, T.ranks))
+    # the same on a compressed vector
+    v = _random_vec(oracle_mod, d, [1, 2, 4, 8, 8, 4, 2, 1], 46)
+    w = oracle_mod.tt_round(v, eps)
+    fv, fw = oracle_mod.vec_full(v), oracle_mod.vec_full(w)
+    assert np.linalg.norm(fv - fw) <= eps * np.linalg.norm(fv) * (1 + 1e-10)
+
+
+def test_rounding_recovers_redundant_ranks(oracle_mod):
+    """A + A has twice A's ranks but is 2 A: rounding at a tiny eps returns
+    ranks no larger than A's and the same matrix; a Kronecker product (rank
+    1) summed with itself rounds back to rank 1."""
+    ra = [1, 2, 4, 3, 2, 1]
+    A = inputs.random_cores(5, ra, 47)
+    R = oracle_mod.tt_round(oracle_mod.tt_sum(A, A), 1e-12)
+    assert all(r <= a for r, a in zip(R.ranks, ra))
+    assert rel_l2(oracle_mod.dense(R), 2 * oracle_mod.dense(A)) <= 1e-12
+    K = inputs.random_cores(5, [1] * 6, 48)
+    RK = oracle_mod.tt_round(oracle_mod.tt_sum(K, K), 1e-12)
+    assert RK.ranks == [1] * 6
+    assert rel_l2(oracle_mod.dense(RK), 2 * oracle_mod.dense(K)) <= 1e-12
+
+
+def test_rounded_compressed_matvec(oracle_mod):
+    """The compressed product followed by rounding stays within eps of the
+    dense product, with ranks below the product ranks."""
+    d = 8
+    A = inputs.random_cores(d, [1, 2, 4, 4, 4, 4, 4, 2, 1], 49)
+    b = _random_vec(oracle_mod, d, [1, 2, 2, 2, 2, 2, 2, 2, 1], 50)
+    c = oracle_mod.tt_round(oracle_mod.apply_tt(A, b), 1e-8)
+    ref = oracle_mod.dense(A) @ oracle_mod.vec_full(b)
+    assert rel_l2(oracle_mod.vec_full(c), ref) <= 1e-8 * (1 + 1e-6)
+    assert max(c.ranks) <= 8
