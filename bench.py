@@ -107,6 +107,7 @@ WORKLOADS = {
                              compute="bf16"),
     "apply_f64_d21": dict(kind="apply", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=64,
                           compute="f64"),
+    "compressed_tt": dict(kind="compressed", d=21, rmax=48, seed=3, smax=48, vec_seed=7),
     "batched_f32": dict(kind="batched", compute="f32", count=256, seed=4),
     "batched_tf32": dict(kind="batched", compute="tf32", count=256, seed=4),
     "batched_f32_small": dict(kind="batched", compute="f32", count=24, seed=4,
@@ -644,7 +645,95 @@ class RefineRun:
         self.op.close()
 
 
-RUNNERS = {"apply": ApplyRun, "batched": BatchedRun, "refine": RefineRun}
+class CompressedRun:
+    """The compressed product c = A b of Sec. 4.2 for a QTT vector b: the
+    d = 21, r <= 48 operator and a random QTT vector of ranks
+    min(2^k, 2^(d-k), s_max); one qtt_apply_tt per step writes c's cores
+    (ranks r_k s_k) to HBM.  Work: 3 flops (two products, one sum) per entry
+    of c."""
+
+    def __init__(self, spec, rank, stream):
+        import torch
+        from paper_1511_06029_gb300 import qtt
+        self.spec = spec
+        self.data = make_operator(spec)
+        d, r = self.data.d, self.data.ranks
+        self.br = [min(1 << k, 1 << (d - k), spec["smax"]) for k in range(d + 1)]
+        rng = np.random.default_rng(spec["vec_seed"] + 1000 * rank)
+        self.bh = np.concatenate([rng.standard_normal(2 * self.br[k] * self.br[k + 1])
+                                  for k in range(d)])
+        self.op = qtt.Operator(self.data, stream=stream)
+        self.b = torch.from_numpy(self.bh).cuda()
+        self.stream = stream
+        self.out_elems = sum(2 * r[k] * self.br[k] * r[k + 1] * self.br[k + 1] for k in range(d))
+        self.c = torch.empty(self.out_elems, dtype=torch.float64, device="cuda")
+        self.bd = torch.empty_like(self.b)
+        self.cd = torch.empty_like(self.c)
+        self.bhp = torch.from_numpy(self.bh).pin_memory()
+        self.chp = torch.empty(self.out_elems, dtype=torch.float64).pin_memory()
+        self.unit = "GFLOP/s"
+        self.launches = d
+
+    def step(self):
+        self.op.apply_tt(self.br, self.b, out=self.c, stream=self.stream)
+
+    def e2e_step(self):
+        self.bd.copy_(self.bhp, non_blocking=True)
+        self.op.apply_tt(self.br, self.bd, out=self.cd)
+        self.chp.copy_(self.cd, non_blocking=True)
+
+    def e2e_bytes(self):
+        return self.bh.nbytes, self.out_elems * 8
+
+    def e2e_check(self):
+        import torch
+        return bool(torch.equal(self.chp, self.c.cpu()))
+
+    def work(self):
+        return 3.0 * self.out_elems / 1e9
+
+    def bytes_per_step(self):
+        r = self.data.ranks
+        nparams = sum(4 * r[k] * r[k + 1] for k in range(self.data.d))
+        return 8.0 * (self.out_elems + self.bh.size + nparams)
+
+    def roofline(self, mean_s):
+        peak = measured_peaks().get("hbm_gbs") or 6800.0
+        gbs = self.bytes_per_step() / mean_s / 1e9
+        return {"bound": "hbm", "kernel": "compressed_core_kernel (one launch per core)",
+                "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                "traffic": None, "bytes_per_step": self.bytes_per_step(),
+                "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json)"}
+
+    def cpu_baseline(self):
+        import oracle
+        b = oracle.Vec(self.br, [])
+        off = 0
+        for k in range(self.data.d):
+            n = 2 * self.br[k] * self.br[k + 1]
+            b.cores.append(self.bh[off:off + n].reshape(self.br[k], 2, self.br[k + 1]))
+            off += n
+        t0 = time.perf_counter()
+        oracle.apply_tt(self.data, b)
+        dt = time.perf_counter() - t0
+        return {"value": self.work() / dt, "unit": "GFLOP/s", "cores": host_cores(),
+                "kind": "oracle",
+                "sample": f"the whole product, one call of oracle.apply_tt (numpy einsum, "
+                          f"{dt:.1f} s)"}
+
+    def close(self):
+        self.op.close()
+
+    def config(self):
+        d = self.data
+        return {"workload": self.spec["name"], "d": d.d, "N": d.N, "rmax": max(d.ranks),
+                "vector_rmax": max(self.br), "product_rmax": max(
+                    a * b for a, b in zip(d.ranks, self.br)),
+                "output_doubles": self.out_elems, "l2": "output 0.5+ GB per step, larger than L2"}
+
+
+RUNNERS = {"apply": ApplyRun, "batched": BatchedRun, "refine": RefineRun,
+           "compressed": CompressedRun}
 
 # --------------------------------------------------------------- serving
 def _build_pair(args):

@@ -169,6 +169,28 @@ qtt_status qtt_plan_create(qtt_plan **out, const qtt_op *A, const void *x, void 
 qtt_status qtt_plan_run(qtt_plan *P, void *stream);
 qtt_status qtt_plan_destroy(qtt_plan *P);
 
+/* ---------------------------------------------------- compressed vectors */
+/* qtt_apply_tt -- the compressed matrix-vector product c = A b of Sec. 4.2,
+ * for a right-hand side b given in QTT form: core k of c merges A's and b's
+ * rank pairs (alpha, beta) into alpha s_k + beta and sums over the column
+ * bit j_k:
+ *   C_k[alpha s + beta][i][alpha' s' + beta']
+ *       = sum_j G_k[alpha][i][j][alpha'] b_k[beta][j][beta'],
+ * so c's ranks are r_k s_k (no rounding).  Each entry is computed as
+ * fl(fl(a_0 b_0) + fl(a_1 b_1)) in FP64.
+ *   b_ranks : host array of d + 1 ranks s_0 .. s_d (s_0 = s_d = 1, each in
+ *             [1, 4096], every r_k s_k <= 32767), d = A's d.
+ *   b_cores : device FP64, b's cores back to back, core k [s_k][2][s_{k+1}]
+ *             C order (bit j_k of the vector index, least significant
+ *             first, as for x in qtt_apply).
+ *   c_cores : device FP64, caller-owned, qtt_apply_tt_size() elements; c's
+ *             cores back to back, core k [r_k s_k][2][r_{k+1} s_{k+1}].
+ * Asynchronous on `stream`; d launches.  Errors: QTT_ERR_INVALID_ARG (NULL
+ * pointer, bad ranks, sizes past the limits), QTT_ERR_CUDA. */
+qtt_status qtt_apply_tt_size(const qtt_op *A, const int *b_ranks, int64_t *n_elems);
+qtt_status qtt_apply_tt(const qtt_op *A, const int *b_ranks, const double *b_cores,
+                        double *c_cores, void *stream);
+
 /* qtt_residual -- r = f - (a x + K x), all FP64, the forward residual of the
  * second-kind system (a I + K) x = f (Sec. 3, eq. (nystrom): A = a I +
  * B K W C), with the subtraction fused into the last core step of the K

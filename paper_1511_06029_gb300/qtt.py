@@ -41,6 +41,8 @@ SIGNATURES = {
     "qtt_apply": (_I, [_P, _P, _P, _L, _L, _I, _I, _P]),
     "qtt_residual": (_I, [_P, _D, _P, _P, _P, _L, _L, _P]),
     "qtt_apply_noalloc": (_I, [_P, _P, _P, _L, _L, _P]),
+    "qtt_apply_tt_size": (_I, [_P, _P, ctypes.POINTER(_L)]),
+    "qtt_apply_tt": (_I, [_P, _P, _P, _P, _P]),
     "qtt_selftest_wait": (_I, [_D, _P]),
     "qtt_plan_create": (_I, [ctypes.POINTER(_P), _P, _P, _P, _L, _L, _I, _I]),
     "qtt_plan_run": (_I, [_P, _P]),
@@ -235,6 +237,38 @@ class Operator:
                                         DTYPES[io], DTYPES[compute], _stream_handle(stream)),
                "qtt_apply")
         return out
+
+    def apply_tt(self, b_ranks, b_cores, out=None, stream=None):
+        """Compressed product c = A b for a QTT vector b (qtt_apply_tt).
+        b_ranks: d + 1 ints; b_cores: CUDA float64 tensor of b's cores back to
+        back (core k [s_k][2][s_{k+1}]).  Returns (c_ranks, c_cores) with
+        c_cores a CUDA float64 tensor of c's cores back to back (core k
+        [r_k s_k][2][r_{k+1} s_{k+1}]), written into `out` when given."""
+        torch = _torch()
+        lib = load_library()
+        br = np.ascontiguousarray(np.asarray(b_ranks, dtype=np.int32))
+        if br.shape != (self.d + 1,):
+            raise QTTError(QTT_ERR_INVALID_ARG, "qtt_apply_tt", "b_ranks needs d + 1 entries")
+        if not (b_cores.is_cuda and b_cores.dtype == torch.float64 and b_cores.is_contiguous()):
+            raise QTTError(QTT_ERR_INVALID_ARG, "qtt_apply_tt",
+                           "b_cores must be a contiguous CUDA float64 tensor")
+        need = sum(2 * int(br[k]) * int(br[k + 1]) for k in range(self.d))
+        if b_cores.numel() != need:
+            raise QTTError(QTT_ERR_INVALID_ARG, "qtt_apply_tt", f"b_cores needs {need} elements")
+        n = ctypes.c_int64(0)
+        _check(lib.qtt_apply_tt_size(self.handle, br.ctypes.data_as(_P), ctypes.byref(n)),
+               "qtt_apply_tt_size")
+        if out is None:
+            out = torch.empty(n.value, dtype=torch.float64, device=b_cores.device)
+        elif not (out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
+                  and out.numel() == n.value):
+            raise QTTError(QTT_ERR_INVALID_ARG, "qtt_apply_tt",
+                           f"out must be a contiguous CUDA float64 tensor of {n.value} elements")
+        _check(lib.qtt_apply_tt(self.handle, br.ctypes.data_as(_P),
+                                ctypes.c_void_p(b_cores.data_ptr()),
+                                ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+               "qtt_apply_tt")
+        return [a * int(b) for a, b in zip(self.ranks, br)], out
 
     def plan(self, x, out, compute: str = "f64"):
         """Record y = A x for these two tensors as a CUDA graph (qtt_plan_create);

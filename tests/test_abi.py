@@ -76,3 +76,7 @@ def test_apply_rejects_null_operator(lib):
     assert lib.qtt_apply(None, None, None, 1, 4, 0, 0, None) == qtt.QTT_ERR_INVALID_ARG
     assert lib.qtt_destroy(None) == qtt.QTT_OK
     assert lib.qtt_op_d(None) == -1
+    import ctypes
+    n = ctypes.c_int64(-1)
+    assert lib.qtt_apply_tt_size(None, None, ctypes.byref(n)) == qtt.QTT_ERR_INVALID_ARG
+    assert lib.qtt_apply_tt(None, None, None, None, None) == qtt.QTT_ERR_INVALID_ARG
