@@ -94,3 +94,28 @@ def test_replica_aggregation_over_two_gloo_ranks():
     assert got == [(0, 3.0, 10.0 * 4 * 2 / 3.0), (1, 3.0, 10.0 * 4 * 2 / 3.0)]
     assert bench.max_over_ranks(None, 1.5, "cpu") == 1.5
     assert bench.job_value(10.0, 4, 1, 2.0) == 20.0
+
+
+class _Apply:
+    def __init__(self, data, nrhs):
+        self.data, self.nrhs = data, nrhs
+
+
+def test_bf16_byte_model_matches_the_launch_lists():
+    """The BF16 roofline's byte model (bench.ApplyRun.fused_bytes) mirrors the
+    library's dispatch: its launch groups are those of the ncu launch lists
+    of the BF16 applies (d = 21, r <= 48, 64 RHS: 10 launches; d = 24,
+    r <= 32, 1 RHS: 12 launches), and at d = 21 its bytes agree with the
+    summed DRAM counters (163.31 GB measured; the 268 MB planes do not fit
+    in L2) to 1 %."""
+    import bench
+    from paper_1511_06029_gb300 import inputs
+    run = _Apply(inputs.synthetic_operator(21, 48, 3), 64)
+    fb, plan = bench.ApplyRun.fused_bytes(run)
+    assert plan == [(0, 1, 2), (3,), (4, 5), (6, 7), (8, 9), (10, 11), (12, 13), (14, 15),
+                    (16, 17), (18, 19, 20)]
+    assert abs(fb - 163.31e9) <= 0.01 * 163.31e9
+    run = _Apply(inputs.synthetic_operator(24, 32, 2), 1)
+    _, plan = bench.ApplyRun.fused_bytes(run)
+    assert plan == [(0, 1, 2), (3,), (4, 5), (6, 7), (8, 9), (10, 11), (12, 13), (14, 15),
+                    (16, 17), (18, 19), (20,), (21, 22, 23)]
