@@ -38,6 +38,8 @@ Function -> passage it follows:
                     and out (Sec. 4.2, compressed product equation)
   tt_round          TT rounding with the Algorithm 1 threshold per unfolding
                     (orthogonalisation, then truncated SVDs; numpy QR/SVD)
+  tt_svd            QTT decomposition of a dense matrix, Algorithm 1 step by
+                    step (truncated SVD of each unfolding; numpy SVD)
 """
 from __future__ import annotations
 
@@ -400,3 +402,37 @@ def tt_round(t, eps: float):
     if is_op:
         return Op(ranks, [c.reshape(c.shape[0], 2, 2, c.shape[2]) for c in cores])
     return Vec(ranks, cores)
+
+
+def tt_svd(A: np.ndarray, eps: float) -> Op:
+    """QTT decomposition of a dense 2^d x 2^d matrix by Algorithm 1: the
+    tensor's modes are the bit pairs (i_k, j_k), k = 0 .. d-1 (index order
+    of Sec. 2.1, least significant bit first); each unfolding M_k is split
+    by a truncated SVD keeping the smallest rank whose discarded singular
+    values have 2-norm <= eps ||A||_F / sqrt(d-1); U_k becomes core k and
+    S_k V_k^T the next unfolding.  ||A - A_tt||_F <= eps ||A||_F."""
+    A = np.asarray(A, dtype=np.float64)
+    N = A.shape[0]
+    d = int(round(np.log2(N)))
+    if A.shape != (N, N) or (1 << d) != N:
+        raise OracleError("tt_svd needs a 2^d x 2^d matrix")
+    # A[i, j] with i = sum_k i_k 2^k: C-order axes (i_{d-1} .. i_0, j_{d-1} .. j_0)
+    T = A.reshape([2] * (2 * d))
+    order = []
+    for k in range(d):
+        order += [d - 1 - k, 2 * d - 1 - k]          # (i_k, j_k), k = 0 first
+    T = np.transpose(T, order)
+    delta = eps * np.linalg.norm(A) / np.sqrt(max(d - 1, 1))
+    cores, ranks = [], [1]
+    M = T.reshape(4, -1)                             # first unfolding, r_0 = 1
+    for k in range(d - 1):
+        U, S, Vt = np.linalg.svd(M, full_matrices=False)
+        keep = len(S)
+        while keep > 1 and np.sqrt(np.sum(S[keep - 1:] ** 2)) <= delta:
+            keep -= 1
+        cores.append(U[:, :keep].reshape(ranks[-1], 2, 2, keep))
+        ranks.append(keep)
+        M = (S[:keep, None] * Vt[:keep]).reshape(keep * 4, -1)
+    cores.append(M.reshape(ranks[-1], 2, 2, 1))
+    ranks.append(1)
+    return Op(ranks, cores)

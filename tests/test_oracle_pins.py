@@ -347,3 +347,46 @@ def test_rounded_compressed_matvec(oracle_mod):
     ref = oracle_mod.dense(A) @ oracle_mod.vec_full(b)
     assert rel_l2(oracle_mod.vec_full(c), ref) <= 1e-8 * (1 + 1e-6)
     assert max(c.ranks) <= 8
+
+
+# ------------------------------------------------------------ TT-SVD (Alg. 1)
+def test_tt_svd_recovers_low_rank_operator(oracle_mod):
+    """Algorithm 1 at a tiny eps on the dense matrix of a QTT operator with
+    generic cores returns its ranks and its matrix."""
+    ranks = [1, 2, 4, 3, 4, 2, 1]
+    A = inputs.random_cores(6, ranks, 51)
+    D = oracle_mod.dense(A)
+    T = oracle_mod.tt_svd(D, 1e-13)
+    assert T.ranks == ranks
+    assert rel_l2(oracle_mod.dense(T), D) <= 1e-13
+
+
+@pytest.mark.parametrize("eps", [3e-1, 1e-2])
+def test_tt_svd_error_bound(oracle_mod, eps):
+    """||A - A_tt||_F <= eps ||A||_F on a full-rank random matrix."""
+    D = np.random.default_rng(52).standard_normal((64, 64))
+    T = oracle_mod.tt_svd(D, eps)
+    assert np.linalg.norm(oracle_mod.dense(T) - D) <= eps * np.linalg.norm(D) * (1 + 1e-12)
+
+
+def test_tt_svd_kronecker_is_rank_one(oracle_mod):
+    """A Kronecker product of 2 x 2 matrices (last factor outermost, bit 0
+    innermost) has every QTT rank 1."""
+    rng = np.random.default_rng(53)
+    parts = [rng.standard_normal((2, 2)) for _ in range(5)]
+    D = parts[-1]
+    for p in parts[-2::-1]:
+        D = np.kron(D, p)
+    T = oracle_mod.tt_svd(D, 1e-12)
+    assert T.ranks == [1] * 6
+    assert rel_l2(oracle_mod.dense(T), D) <= 1e-13
+
+
+def test_tt_svd_laplace_volume(oracle_mod):
+    """The 8^3 Laplace volume matrix at eps = 1e-8: within the bound, and the
+    same ranks as the input generator's own (independent) Algorithm 1 code."""
+    D = inputs.laplace_volume_dense(8)
+    T = oracle_mod.tt_svd(D, 1e-8)
+    assert np.linalg.norm(oracle_mod.dense(T) - D) <= 1e-8 * np.linalg.norm(D) * (1 + 1e-9)
+    gen, _ = inputs.laplace_volume(8, 1e-8)
+    assert T.ranks == list(gen.ranks)
