@@ -40,6 +40,8 @@ Function -> passage it follows:
                     (orthogonalisation, then truncated SVDs; numpy QR/SVD)
   tt_svd            QTT decomposition of a dense matrix, Algorithm 1 step by
                     step (truncated SVD of each unfolding; numpy SVD)
+  apply_general     y = A x with m_k x n_k modes (Sec. 3.1 tensorisation),
+                    rectangular operators included
 """
 from __future__ import annotations
 
@@ -436,3 +438,33 @@ def tt_svd(A: np.ndarray, eps: float) -> Op:
     cores.append(M.reshape(ranks[-1], 2, 2, 1))
     ranks.append(1)
     return Op(ranks, cores)
+
+
+def apply_general(cores, x) -> np.ndarray:
+    """y = A x for a QTT-format matrix with general mode sizes (Sec. 3.1's
+    tensorisation with m_k x n_k modes; rectangular when prod m != prod n).
+    cores[k] has shape (r_k, m_k, n_k, r_{k+1}); x has shape (prod n,) or
+    (nrhs, prod n) with column index j = sum_k j_k prod_{l<k} n_l (first mode
+    fastest, as for the binary case); y's row index likewise.  The sweep
+    runs core 0 first, keeping (unused column modes, produced row modes,
+    rank) as the state."""
+    G = [np.asarray(c, dtype=np.float64) for c in cores]
+    x = np.asarray(x, dtype=np.float64)
+    single = x.ndim == 1
+    X = x.reshape(1, -1) if single else x
+    m = [g.shape[1] for g in G]
+    n = [g.shape[2] for g in G]
+    if X.shape[1] != int(np.prod(n)):
+        raise OracleError("x length != prod n_k")
+    R = X.shape[0]
+    # Z[rhs, remaining high column modes, n_k, produced rows, alpha_k]
+    Z = X.reshape(R, -1, n[0], 1, 1)
+    for k, g in enumerate(G):
+        Y = np.einsum("rhjla,aijb->rhilb", Z, g)        # (R, high, m_k, low, r')
+        Y = Y.reshape(R, Y.shape[1], m[k] * Y.shape[3], g.shape[3])
+        if k + 1 < len(G):
+            Z = Y.reshape(R, Y.shape[1] // n[k + 1], n[k + 1], Y.shape[2], g.shape[3])
+        else:
+            Z = Y
+    y = Z.reshape(R, -1)
+    return y[0] if single else y

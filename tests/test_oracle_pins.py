@@ -390,3 +390,56 @@ def test_tt_svd_laplace_volume(oracle_mod):
     assert np.linalg.norm(oracle_mod.dense(T) - D) <= 1e-8 * np.linalg.norm(D) * (1 + 1e-9)
     gen, _ = inputs.laplace_volume(8, 1e-8)
     assert T.ranks == list(gen.ranks)
+
+
+# ------------------------------------------------ general mode sizes (Sec. 3.1)
+def _general_cores(ms, ns, ranks, seed):
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal((ranks[k], ms[k], ns[k], ranks[k + 1])) for k in range(len(ms))]
+
+
+def _general_dense_bruteforce(cores):
+    """A(i, j) element by element: the mixed-radix digits of i and j (first
+    mode fastest) pick one slice of each core, multiplied in order."""
+    ms = [c.shape[1] for c in cores]
+    ns = [c.shape[2] for c in cores]
+    M, N = int(np.prod(ms)), int(np.prod(ns))
+    D = np.empty((M, N))
+    for i in range(M):
+        for j in range(N):
+            p, ii, jj = np.eye(1), i, j
+            for c, m, n in zip(cores, ms, ns):
+                p = p @ c[:, ii % m, jj % n, :]
+                ii, jj = ii // m, jj // n
+            D[i, j] = p[0, 0]
+    return D
+
+
+@pytest.mark.parametrize("ms,ns,ranks", [
+    ([3, 2, 4], [2, 5, 3], [1, 2, 3, 1]),        # rectangular 24 x 30
+    ([2, 3, 3, 2], [3, 2, 2, 3], [1, 3, 2, 2, 1]),
+    ([4, 4], [4, 4], [1, 5, 1]),
+])
+def test_general_modes_match_bruteforce(oracle_mod, ms, ns, ranks):
+    cores = _general_cores(ms, ns, ranks, sum(ms) + sum(ns))
+    D = _general_dense_bruteforce(cores)
+    x = np.random.default_rng(54).standard_normal((3, D.shape[1]))
+    y = oracle_mod.apply_general(cores, x)
+    assert y.shape == (3, D.shape[0])
+    assert rel_l2(y, x @ D.T) <= 1e-14
+
+
+def test_general_modes_kronecker_and_binary_case(oracle_mod):
+    """Rank 1: A is the Kronecker product of the mode matrices (last mode
+    outermost); m = n = 2: the binary oracle's apply."""
+    rng = np.random.default_rng(55)
+    mats = [rng.standard_normal((m, n)) for m, n in [(3, 2), (2, 4), (5, 3)]]
+    D = mats[-1]
+    for p in mats[-2::-1]:
+        D = np.kron(D, p)
+    cores = [mt.reshape(1, *mt.shape, 1) for mt in mats]
+    x = rng.standard_normal(D.shape[1])
+    assert rel_l2(oracle_mod.apply_general(cores, x), D @ x) <= 1e-14
+    A = inputs.random_cores(7, [1, 2, 4, 5, 5, 4, 2, 1], 56)
+    xb = rng.standard_normal((2, 128))
+    assert rel_l2(oracle_mod.apply_general(A.cores, xb), oracle_mod.apply(A, xb)) <= 1e-14
