@@ -42,6 +42,9 @@ Function -> passage it follows:
                     step (truncated SVD of each unfolding; numpy SVD)
   apply_general     y = A x with m_k x n_k modes (Sec. 3.1 tensorisation),
                     rectangular operators included
+  local_frames,     the inversion's local system (appendix on local linear
+  local_apply       systems): interfaces Psi_{k-1}, Phi_k by their
+                    recursions, and the three-core product Psi G_k Phi W_k
 """
 from __future__ import annotations
 
@@ -468,3 +471,35 @@ def apply_general(cores, x) -> np.ndarray:
             Z = Y
     y = Z.reshape(R, -1)
     return y[0] if single else y
+
+
+# ------------------------------------- local system of the inversion sweeps
+# For the inversion A X = I with X in QTT form (cores W_k(gamma, j, p,
+# gamma'), row bit j, column bit p), fixing every core of X but W_k leaves the
+# reduced system P^T (I (x) A) P vec(W_k) = P^T vec(I) (appendix on the local
+# linear systems).  Its left-hand side is a three-core QTT matrix-vector
+# product with the interfaces Psi_{k-1} (cores before k) and Phi_k (cores
+# after k).
+
+def local_frames(G_cores, W_cores, k):
+    """(Psi_{k-1}, Phi_k) of the appendix's local-system formula, built by
+    their recursions: Psi over cores 0 .. k-1 from Psi = 1, Phi over cores
+    d-1 .. k+1 from Phi = 1.  Index order [alpha (A's rank), beta (the
+    projected X), gamma (the applied X)]."""
+    G = [np.asarray(c, dtype=np.float64) for c in G_cores]
+    W = [np.asarray(c, dtype=np.float64) for c in W_cores]
+    psi = np.ones((1, 1, 1))
+    for l in range(k):
+        psi = np.einsum("abc,bipB,aijA,cjpC->ABC", psi, W[l], G[l], W[l])
+    phi = np.ones((1, 1, 1))
+    for l in range(len(G) - 1, k, -1):
+        phi = np.einsum("bipB,aijA,cjpC,ABC->abc", W[l], G[l], W[l], phi)
+    return psi, phi
+
+
+def local_apply(psi, Gk, phi, Wk) -> np.ndarray:
+    """The local system's left-hand side applied to W_k: the sum over
+    alpha, gamma and j of Psi_{k-1} G_k Phi_k W_k, indexed (beta_{k-1}, i_k,
+    p_k, beta_k) -- the appendix's three-core QTT matrix-vector product."""
+    return np.einsum("abc,aijA,ABC,cjpC->bipB", psi, np.asarray(Gk, dtype=np.float64), phi,
+                     np.asarray(Wk, dtype=np.float64))

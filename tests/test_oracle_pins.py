@@ -443,3 +443,29 @@ def test_general_modes_kronecker_and_binary_case(oracle_mod):
     A = inputs.random_cores(7, [1, 2, 4, 5, 5, 4, 2, 1], 56)
     xb = rng.standard_normal((2, 128))
     assert rel_l2(oracle_mod.apply_general(A.cores, xb), oracle_mod.apply(A, xb)) <= 1e-14
+
+
+# ------------------------------------------------- inversion local systems
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_local_system_apply_is_the_projected_product(oracle_mod, k):
+    """Entry e = (beta_{k-1}, i_k, p_k, beta_k) of the local left-hand side
+    is the Frobenius inner product <X_e, A X>, X_e being X with core k
+    replaced by the unit tensor at e: the projected system P^T (I (x) A) P
+    vec(W_k) computed with dense matrices."""
+    d = 4
+    A = inputs.random_cores(d, [1, 2, 3, 2, 1], 57)
+    X = inputs.random_cores(d, [1, 3, 2, 3, 1], 58)
+    DA, DX = oracle_mod.dense(A), oracle_mod.dense(X)
+    AX = DA @ DX
+    psi, phi = oracle_mod.local_frames(A.cores, X.cores, k)
+    y = oracle_mod.local_apply(psi, A.cores[k], phi, X.cores[k])
+    Wk = X.cores[k]
+    assert y.shape == Wk.shape
+    ref = np.empty_like(Wk)
+    for e in np.ndindex(*Wk.shape):
+        unit = np.zeros_like(Wk)
+        unit[e] = 1.0
+        cores = list(X.cores)
+        cores[k] = unit
+        ref[e] = np.sum(oracle_mod.dense(inputs.QTTData(X.ranks, cores)) * AX)
+    assert rel_l2(y, ref) <= 1e-13
