@@ -287,11 +287,45 @@ def oracle_baseline(op, target_s=8.0):
 
 
 # --------------------------------------------------------------- reference
+def run_reference_compressed(args, spec):
+    """The oracle's compressed product (numpy) on the same operator and QTT
+    vector as CompressedRun, whole problem per step."""
+    import oracle
+    op = make_operator(spec)
+    d = op.d
+    br = [min(1 << k, 1 << (d - k), spec["smax"]) for k in range(d + 1)]
+    rng = np.random.default_rng(spec["vec_seed"])
+    b = oracle.Vec(br, [rng.standard_normal((br[k], 2, br[k + 1])) for k in range(d)])
+    out = sum(2 * op.ranks[k] * br[k] * op.ranks[k + 1] * br[k + 1] for k in range(d))
+    for _ in range(args.warmup):
+        oracle.apply_tt(op, b)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.apply_tt(op, b)
+    dt = time.perf_counter() - t0
+    value = 3.0 * out * args.steps / dt / 1e9
+    sample = f"the whole product ({out} output entries), oracle.apply_tt (numpy einsum)"
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": host_cores(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args, spec):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
+    if spec["kind"] == "compressed":
+        return run_reference_compressed(args, spec)
     if spec["kind"] == "batched":
         it = inputs.batched_workload(count=1, seed=spec["seed"])[0]
         op = inputs.synthetic_operator(it["d"], it["rmax"], it["op_seed"])
