@@ -72,11 +72,39 @@ sys.path.insert(0, ROOT)
 from paper_1511_06029_gb300 import inputs  # noqa: E402
 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# Plain ALU pipes of one GB300 (no FP64/FP32 figure is measured in
-# MEASURED_PEAKS.json): FP64 1.25 TFLOP/s nominal (2 FMA/clk/SM), FP32
-# 152 SMs x 128 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s.
-FP64_NOMINAL_GFLOPS = 1250.0
-FP32_NOMINAL_GFLOPS = 152 * 128 * 2 * 2.07
+# Plain ALU pipes of one GB300 (MEASURED_PEAKS.json measures no FP64/FP32
+# figure), derived from unit counts and the clock: FP64 = SMs x 2 DFMA per
+# clock x 2 flops x SM clock (1.259 TFLOP/s at 152 SMs and 2070 MHz); FP32 =
+# SMs x 128 FMA lanes x 2 flops x SM clock (80.5 TFLOP/s).  The clock is the
+# median SM clock sampled during the timed region (the maximum clock when no
+# sample is available).
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+FP64_FLOP_PER_CLK_SM = 2 * 2
+FP32_FLOP_PER_CLK_SM = 128 * 2
+_CLOCK = {"sm_mhz": None, "sms": None}
+
+
+def _sm_clock_mhz():
+    return _CLOCK["sm_mhz"] or SM_MAX_MHZ
+
+
+def _sms():
+    return _CLOCK["sms"] or SM_COUNT
+
+
+def fp64_peak_gflops():
+    return _sms() * FP64_FLOP_PER_CLK_SM * _sm_clock_mhz() / 1e3
+
+
+def fp32_peak_gflops():
+    return _sms() * FP32_FLOP_PER_CLK_SM * _sm_clock_mhz() / 1e3
+
+
+def _peak_source(kind):
+    per = FP64_FLOP_PER_CLK_SM if kind == "fp64" else FP32_FLOP_PER_CLK_SM
+    return (f"{kind.upper()} pipe: {_sms()} SMs x {per} flop/clk x {_sm_clock_mhz():.0f} MHz "
+            f"(median SM clock sampled in the timed region)")
 METRIC = "QTT-apply GFLOP/s"
 # DRAM bytes (read + write) per launch of the workload's kernel from one ncu
 # capture of the same command, averaged over one apply's launches; valid for
@@ -477,10 +505,10 @@ class ApplyRun:
                     "launches_per_apply": len(plan),
                     "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json)"}
         if self.compute == "f64":
-            peak, src = FP64_NOMINAL_GFLOPS, "FP64 pipe, 1.25 TFLOP/s nominal (2 FMA/clk/SM)"
+            peak, src = fp64_peak_gflops(), _peak_source("fp64")
         else:
-            peak, src = FP32_NOMINAL_GFLOPS, ("FP32 pipe, 152 SMs x 128 FMA/clk x 2.07 GHz "
-                                               "(the kernel multiplies on CUDA cores)")
+            peak, src = fp32_peak_gflops(), _peak_source("fp32") + \
+                " (the kernel multiplies on CUDA cores)"
         r = {"bound": "alu", "kernel": KERNEL[self.compute], "achieved": achieved, "peak": peak,
              "unit": "GFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": src}
         t = NCU_TRAFFIC.get(self.spec["name"])
@@ -571,8 +599,8 @@ class BatchedRun:
     def roofline(self, mean_s):
         achieved = self.flops / mean_s / 1e9
         r = {"bound": "alu", "kernel": f"batch_kernel<{self.variant % 100}>", "achieved": achieved,
-             "peak": FP32_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-             "frac": achieved / FP32_NOMINAL_GFLOPS, "traffic": None,
+             "peak": fp32_peak_gflops(), "unit": "GFLOP/s",
+             "frac": achieved / fp32_peak_gflops(), "traffic": None,
              "peak_source": "FP32 pipe, 152 SMs x 128 FMA/clk x 2.07 GHz"}
         pk = measured_peaks().get("bf16_tflops")
         if pk and self.compute == "tf32":
@@ -659,9 +687,9 @@ class RefineRun:
             f64_flops += self.data.flops(self.nrhs) * its * self.spec["inner"]
         achieved = f64_flops / mean_s / 1e9
         return {"bound": "alu", "kernel": "step_f64_kernel (FP64 residual applies)",
-                "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-                "frac": achieved / FP64_NOMINAL_GFLOPS, "traffic": None,
-                "peak_source": "FP64 pipe, 1.25 TFLOP/s nominal"}
+                "achieved": achieved, "peak": fp64_peak_gflops(), "unit": "GFLOP/s",
+                "frac": achieved / fp64_peak_gflops(), "traffic": None,
+                "peak_source": _peak_source("fp64")}
 
     def config(self):
         its = self.last_info[0][0] if self.last_info else None
@@ -932,7 +960,7 @@ def run_serve(args, spec):
                     "speedup_vs_plain_fp64_at_saturation":
                         sat_rate / (len(res_64) / wall_64) if plain_n == len(trace) else None},
         "roofline": {"bound": "alu", "kernel": "step_f64_kernel (FP64 residual/Arnoldi applies)",
-                     "achieved": None, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+                     "achieved": None, "peak": fp64_peak_gflops(), "unit": "GFLOP/s",
                      "frac": None, "traffic": None},
         "clocks": clocks,
         "e2e": {"value": mixed_rate, "unit": "solves/s",
@@ -946,7 +974,7 @@ def run_serve(args, spec):
     f64 = sum(4.0 * (1 << r["d"]) * r["nrhs"] * ops[r["d"]]["data"][0].sigma * (r["iters"] + 2)
               for r in res_p)
     line["roofline"]["achieved"] = f64 / wall_p / 1e9
-    line["roofline"]["frac"] = line["roofline"]["achieved"] / FP64_NOMINAL_GFLOPS
+    line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak_gflops()
     for o in ops.values():
         for k in ("K", "P64", "Pbf"):
             o[k].close()
@@ -998,6 +1026,8 @@ def run_ours(args, spec):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
+    _CLOCK["sm_mhz"] = clocks.get("sm_mhz")
+    _CLOCK["sms"] = torch.cuda.get_device_properties(local).multi_processor_count
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_s = ev[0].elapsed_time(ev[-1]) / 1e3
     t_max = slowest(total_s)

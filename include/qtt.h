@@ -33,6 +33,9 @@
  *   - Threads.  Distinct operators may be used from distinct threads.  One
  *     operator may be applied concurrently on several streams: it is
  *     read-only after qtt_create.
+ *   - Devices.  An operator lives on the device that was current at
+ *     qtt_create; every call that uses it needs that device current and
+ *     returns QTT_ERR_INVALID_ARG otherwise.
  */
 #ifndef QTT_H_
 #define QTT_H_
@@ -83,8 +86,11 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks,
                       const double *cores, unsigned precision_mask,
                       void *stream);
 
-/* qtt_destroy -- free the operator's device memory after all work queued on
- * the streams it was used on has finished.  NULL is a no-op. */
+/* qtt_destroy -- release the operator.  Returns at once: its device memory
+ * goes back to the library's pool once the work already queued that reads
+ * it has finished (every apply, solve, plan replay and batch run records
+ * its use on its stream), without synchronising the device or holding up
+ * other streams.  NULL is a no-op.  The handle is invalid afterwards. */
 qtt_status qtt_destroy(qtt_op *A);
 
 /* Queries (host-side, no device work). */
@@ -131,9 +137,14 @@ qtt_status qtt_apply(const qtt_op *A, const void *x, void *y, int64_t nrhs,
  * library holds until the process exits.
  *   Limit : d > 1 needs 2 x max_{0<k<d} ranks[k] x N x nrhs <= 8,388,608
  *           doubles; larger calls return QTT_ERR_INVALID_ARG (use qtt_apply).
- *   Set-up: the first call on each device looks up the array's device
- *           address (with that device current); make that first call before
- *           any stream capture.
+ *   Set-up: the array is committed on a device when the module holding it
+ *           is first loaded there.  qtt_create does that (it allocates the
+ *           operator anyway), so create the operator on each device BEFORE
+ *           handing the rest of the device's memory to another allocator;
+ *           qtt_apply_noalloc then allocates nothing.  Each call looks up
+ *           the array's device address with the current device (which must
+ *           be the operator's).  After a device reset the module and the
+ *           64 MiB are loaded again by the next lookup.
  *   Races : every call on a device shares the one array, which keeps the
  *           last call's contents (nothing in it needs to start at zero).
  *           Calls whose work overlaps on the GPU -- on different streams, or
@@ -190,6 +201,44 @@ qtt_status qtt_plan_destroy(qtt_plan *P);
 qtt_status qtt_apply_tt_size(const qtt_op *A, const int *b_ranks, int64_t *n_elems);
 qtt_status qtt_apply_tt(const qtt_op *A, const int *b_ranks, const double *b_cores,
                         double *c_cores, void *stream);
+
+/* ------------------------------------------------ general mode sizes */
+/* A QTT matrix whose core k has m_k row modes and n_k column modes (the
+ * tensorisation of Sec. 3.1 with m_k x n_k modes; Sec. 4.2 counts 2 m_k n_k
+ * r_k r_{k+1} flops per column of a core step), so that the matrix is
+ * (prod m_k) x (prod n_k) -- rectangular when the products differ.
+ *   qtt_gcreate : d in [1, 60]; ranks[0..d] with ranks[0] = ranks[d] = 1,
+ *                 each in [1, 4096]; m[k], n[k] in [1, 16]; cores: host FP64,
+ *                 core k as [ranks[k]][m[k]][n[k]][ranks[k+1]] in C order,
+ *                 back to back (copied; the caller keeps ownership).  The
+ *                 row index is i = sum_k i_k prod_{l<k} m_l and the column
+ *                 index j = sum_k j_k prod_{l<k} n_l (first mode fastest, as
+ *                 for the binary operators).  Returns after the uploads on
+ *                 `stream`.  Errors: QTT_ERR_INVALID_ARG, QTT_ERR_OOM,
+ *                 QTT_ERR_CUDA.
+ *   qtt_gapply  : y = A x (transpose = 0: x has prod n_k entries per
+ *                 right-hand side, y prod m_k) or y = A^T x (transpose = 1:
+ *                 the lengths exchanged), FP64, by the sweep of Algorithm 2
+ *                 with mixed-radix positions.  x, y: device FP64, nrhs
+ *                 columns with leading dimensions ldx, ldy >= their
+ *                 lengths; no overlap.  Scratch (two buffers of the largest
+ *                 intermediate) from the library's pool; right-hand sides in
+ *                 chunks when it is short.  Asynchronous on `stream`.
+ *                 Errors: QTT_ERR_INVALID_ARG, QTT_ERR_OOM, QTT_ERR_CUDA.
+ *   qtt_gdestroy: releases A after the work queued on it (no device-wide
+ *                 synchronisation); NULL is a no-op.
+ *   qtt_gop_rows/cols: prod m_k / prod n_k (-1 for NULL);
+ *   qtt_gop_flops: flops of one apply per right-hand side (transposed or
+ *                 not). */
+typedef struct qtt_gop qtt_gop;
+qtt_status qtt_gcreate(qtt_gop **out, int d, const int *ranks, const int *m, const int *n,
+                       const double *cores, void *stream);
+qtt_status qtt_gapply(const qtt_gop *A, const double *x, double *y, int64_t nrhs,
+                      int64_t ldx, int64_t ldy, int transpose, void *stream);
+qtt_status qtt_gdestroy(qtt_gop *A);
+int64_t qtt_gop_rows(const qtt_gop *A);
+int64_t qtt_gop_cols(const qtt_gop *A);
+double qtt_gop_flops(const qtt_gop *A, int transpose);
 
 /* qtt_residual -- r = f - (a x + K x), all FP64, the forward residual of the
  * second-kind system (a I + K) x = f (Sec. 3, eq. (nystrom): A = a I +
@@ -279,6 +328,15 @@ qtt_status qtt_batch_run(qtt_batch *B, void *stream);
 /* Synchronise `stream`; QTT_ERR_TIMEOUT if a dependency wait in the last
  * runs gave up (the status word is then cleared). */
 qtt_status qtt_batch_status(qtt_batch *B, void *stream);
+/* qtt_batch_selftest_timeout -- exercises the batch kernel's bounded
+ * dependency wait without a fault (no counterpart in the paper): launches the
+ * batch's first wave alone, with its work list started past every item that
+ * has no dependency, so that the items it runs wait on work that is never
+ * done; each wait gives up after `seconds` (0 < seconds <= 10), the kernel
+ * records QTT_ERR_TIMEOUT and every CTA returns.  The next qtt_batch_status
+ * then returns QTT_ERR_TIMEOUT; the batch stays usable (each run resets its
+ * counters).  QTT_ERR_UNSUPPORTED if no operator of the first wave has d > 1. */
+qtt_status qtt_batch_selftest_timeout(qtt_batch *B, double seconds, void *stream);
 /* Tile variant = pairs per lane (2 or 4: chunks of 64 or 128 position pairs,
  * wider for small ranks) + 100 x chunks per work item (1..64, default 8)
  * + 10000 x depth of the cp.async ring (2 or 3, default 3); re-plans and
@@ -338,6 +396,20 @@ const char *qtt_last_error(void);
  * sticky CUDA error, QTT_ERR_TIMEOUT if a bounded wait in a library kernel
  * gave up).  The status word is cleared once reported. */
 qtt_status qtt_sync_status(void *stream);
+
+/* qtt_set_scratch_limit -- cap the scratch (the sweep's intermediates,
+ * Krylov bases) that all applies and solves of the process hold at once, in
+ * bytes; 0 removes the cap.  The paper has no counterpart: it bounds the
+ * library's own memory beside a caller's other allocations.  Under the cap,
+ * qtt_apply and the solves process right-hand sides in chunks (results are
+ * bitwise the same) and return QTT_ERR_OOM when one right-hand side does not
+ * fit. */
+qtt_status qtt_set_scratch_limit(size_t bytes);
+/* qtt_scratch_stats -- bytes of scratch handed out and not yet returned (all
+ * devices), and the current device's pool: bytes reserved from the device
+ * and bytes in use (scratch plus operator cores and batch tables).  Any
+ * pointer may be NULL. */
+qtt_status qtt_scratch_stats(size_t *in_use, size_t *pool_reserved, size_t *pool_used);
 
 /* qtt_selftest_wait -- exercises the failure path of the library's device
  * waits without a fault (no counterpart in the paper): launches one kernel

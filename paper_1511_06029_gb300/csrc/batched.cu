@@ -403,6 +403,7 @@ struct WaveDev {
   unsigned *d_done = nullptr;
   int nseg = 0;
   int64_t total = 0;
+  int64_t first_dep = -1;  // index of the first item that waits on another
   int max_rin = 1;
 };
 
@@ -423,6 +424,11 @@ struct qtt_batch {
   size_t scratch_bytes = 0;
   unsigned long long *d_next = nullptr;  // one counter per wave
   int *d_status = nullptr;
+  cudaEvent_t last_run = nullptr;  // recorded after each run (for destroy)
+  // qtt_batch_selftest_timeout: start wave 0 at this item with this wait
+  // budget (clock cycles), launching that wave alone (-1: normal runs)
+  int64_t selftest_start = -1;
+  long long selftest_budget = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   double flops = 0.0;
@@ -437,12 +443,22 @@ size_t op_scratch_bytes(const qtt_op *A, int64_t nrhs) {
   return (size_t)2 * A->rmax_inner * ((size_t)1 << A->d) * (size_t)nrhs * sizeof(float);
 }
 
+// Device buffers of a batch come from the library's pool (persistent_alloc)
+// and go back stream-ordered, after the batch's last run.
+void release(qtt_batch *B, std::vector<void *> ptrs) {
+  std::vector<cudaEvent_t> after;
+  if (B->last_run) after.push_back(B->last_run);
+  release_after(ptrs, after);
+}
+
 void free_waves(qtt_batch *B) {
+  std::vector<void *> ptrs;
   for (auto &w : B->waves) {
-    if (w.d_ops) cudaFree(w.d_ops);
-    if (w.d_segs) cudaFree(w.d_segs);
-    if (w.d_done) cudaFree(w.d_done);
+    ptrs.push_back(w.d_ops);
+    ptrs.push_back(w.d_segs);
+    ptrs.push_back(w.d_done);
   }
+  release(B, ptrs);
   B->waves.clear();
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
@@ -470,18 +486,19 @@ qtt_status build_plan(qtt_batch *B, cudaStream_t st) {
     maxw = std::max(maxw, cur);
   }
   if (B->scratch_bytes < maxw) {
-    if (B->scratch) cudaFree(B->scratch);
+    release(B, {B->scratch});
     B->scratch = nullptr;
     B->scratch_bytes = 0;
-    size_t fr = 0, tot = 0;
-    cudaMemGetInfo(&fr, &tot);
-    if (maxw + ((size_t)256 << 20) > fr) return fail(QTT_ERR_OOM, "batch: scratch does not fit");
-    QTT_CUDA_TRY(cudaMalloc(&B->scratch, maxw));
+    if (maxw > scratch_available()) return fail(QTT_ERR_OOM, "batch: scratch does not fit");
+    if (qtt_status as = persistent_alloc(reinterpret_cast<void **>(&B->scratch), maxw, st))
+      return as;
     B->scratch_bytes = maxw;
   }
-  if (B->d_next) cudaFree(B->d_next);
+  release(B, {B->d_next});
   B->d_next = nullptr;
-  QTT_CUDA_TRY(cudaMalloc(&B->d_next, sizeof(unsigned long long) * std::max<size_t>(1, groups.size())));
+  if (qtt_status as = persistent_alloc(reinterpret_cast<void **>(&B->d_next),
+                                       sizeof(unsigned long long) * std::max<size_t>(1, groups.size()), st))
+    return as;
   // every wave's kernel is sized for the largest rank of the batch
   int max_rank_all = 1;
   for (const qtt_op *A : B->ops)
@@ -550,9 +567,15 @@ qtt_status build_plan(qtt_batch *B, cudaStream_t st) {
       }
     wv.nseg = (int)segs.size();
     wv.total = first;
-    QTT_CUDA_TRY(cudaMalloc(&wv.d_ops, sizeof(BOp) * hops.size()));
-    QTT_CUDA_TRY(cudaMalloc(&wv.d_segs, sizeof(BSeg) * segs.size()));
-    QTT_CUDA_TRY(cudaMalloc(&wv.d_done, sizeof(unsigned) * segs.size()));
+    for (const BSeg &sg : segs)
+      if (sg.dep >= 0 && (wv.first_dep < 0 || sg.first < wv.first_dep)) wv.first_dep = sg.first;
+    for (auto pr : {std::make_pair(reinterpret_cast<void **>(&wv.d_ops), sizeof(BOp) * hops.size()),
+                    std::make_pair(reinterpret_cast<void **>(&wv.d_segs), sizeof(BSeg) * segs.size()),
+                    std::make_pair(reinterpret_cast<void **>(&wv.d_done), sizeof(unsigned) * segs.size())})
+      if (qtt_status as = persistent_alloc(pr.first, pr.second, st)) {
+        release(B, {wv.d_ops, wv.d_segs, wv.d_done});
+        return as;
+      }
     QTT_CUDA_TRY(cudaMemcpyAsync(wv.d_ops, hops.data(), sizeof(BOp) * hops.size(),
                                  cudaMemcpyHostToDevice, st));
     QTT_CUDA_TRY(cudaMemcpyAsync(wv.d_segs, segs.data(), sizeof(BSeg) * segs.size(),
@@ -585,10 +608,19 @@ qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
   int clk_khz = 2000000;
   cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
   B->grid = std::max(1, per_sm) * sms;
-  for (size_t wi = 0; wi < B->waves.size(); ++wi) {
+  const bool selftest = B->selftest_start >= 0;
+  for (size_t wi = 0; wi < (selftest ? (size_t)1 : B->waves.size()); ++wi) {
     auto &w = B->waves[wi];
     QTT_CUDA_TRY(cudaMemsetAsync(w.d_done, 0, sizeof(unsigned) * w.nseg, st));
-    QTT_CUDA_TRY(cudaMemsetAsync(B->d_next + wi, 0, sizeof(unsigned long long), st));
+    if (selftest) {
+      // the work list starts past every item without a dependency: the
+      // items the others wait on are never taken
+      const unsigned long long start = (unsigned long long)B->selftest_start;
+      QTT_CUDA_TRY(cudaMemcpyAsync(B->d_next + wi, &start, sizeof(start), cudaMemcpyHostToDevice, st));
+      QTT_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+      QTT_CUDA_TRY(cudaMemsetAsync(B->d_next + wi, 0, sizeof(unsigned long long), st));
+    }
     BWave bw;
     bw.ops = w.d_ops;
     bw.segs = w.d_segs;
@@ -598,7 +630,7 @@ qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
     bw.next = B->d_next + wi;
     bw.status = B->d_status;
     bw.tf32 = B->compute == QTT_TF32;
-    bw.wait_budget = (long long)clk_khz * 1000LL * 4;  // ~4 s of clock
+    bw.wait_budget = selftest ? B->selftest_budget : (long long)clk_khz * 1000LL * 4;  // ~4 s
     bw.max_k = max_k;
     bw.core_floats = core_floats;
     batch_kernel<TN, 6, NS><<<B->grid, kThreads, smem, st>>>(bw);
@@ -668,6 +700,7 @@ qtt_status qtt_batch_create(qtt_batch **out, int nops, const qtt_op *const *ops,
     if (nrhs[i] < 1 || nrhs[i] > (int64_t)1 << 24)
       return fail(QTT_ERR_INVALID_ARG, "qtt_batch_create: nrhs out of range");
     if (ld[i] < ((int64_t)1 << A->d)) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_create: ld < N");
+    if (qtt_status ds = check_device(A, "qtt_batch_create")) return ds;
     if ((compute == QTT_F32 && !A->m32) || (compute == QTT_TF32 && !A->mtf32))
       return fail(QTT_ERR_INVALID_ARG, "qtt_batch_create: operator lacks the packed copy");
     for (int k = 0; k <= A->d; ++k)
@@ -689,8 +722,10 @@ qtt_status qtt_batch_create(qtt_batch **out, int nops, const qtt_op *const *ops,
   cudaMemGetInfo(&fr, &tot);
   B->budget = mem_budget ? mem_budget : std::min<size_t>(fr / 3, (size_t)64 << 30);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMalloc(&B->d_status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(B->d_status, 0, sizeof(int));
+  cudaError_t e = persistent_alloc(reinterpret_cast<void **>(&B->d_status), sizeof(int), st) == QTT_OK
+                      ? cudaSuccess : cudaErrorMemoryAllocation;
+  if (e == cudaSuccess) e = cudaMemsetAsync(B->d_status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     qtt_batch_destroy(B);
     return cuda_fail(e, "qtt_batch_create: status word");
@@ -707,9 +742,41 @@ qtt_status qtt_batch_create(qtt_batch **out, int nops, const qtt_op *const *ops,
 
 qtt_status qtt_batch_run(qtt_batch *B, void *stream) {
   if (!B || !B->exec) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_run: no batch");
-  cudaError_t e = cudaGraphLaunch(B->exec, static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaGraphLaunch(B->exec, st);
   if (e != cudaSuccess) return cuda_fail(e, "qtt_batch_run: graph launch");
+  // the run reads every operator and the batch's own buffers
+  for (const qtt_op *A : B->ops) note_use(A, st);
+  if (!B->last_run) {
+    e = cudaEventCreateWithFlags(&B->last_run, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "qtt_batch_run: event");
+  }
+  e = cudaEventRecord(B->last_run, st);
+  if (e != cudaSuccess) return cuda_fail(e, "qtt_batch_run: event record");
   return QTT_OK;
+}
+
+qtt_status qtt_batch_selftest_timeout(qtt_batch *B, double seconds, void *stream) {
+  if (!B || B->waves.empty()) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_selftest_timeout: no batch");
+  if (!(seconds > 0.0 && seconds <= 10.0))
+    return fail(QTT_ERR_INVALID_ARG, "qtt_batch_selftest_timeout: seconds must be in (0, 10]");
+  if (B->waves[0].first_dep < 0)
+    return fail(QTT_ERR_UNSUPPORTED,
+                "qtt_batch_selftest_timeout: the first wave has no dependent items (every d = 1)");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, clk_khz = 2000000;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+  B->selftest_start = B->waves[0].first_dep;
+  B->selftest_budget = (long long)(seconds * 1e3 * clk_khz);
+  const qtt_status s = launch_waves(B, st);
+  B->selftest_start = -1;
+  B->selftest_budget = 0;
+  for (const qtt_op *A : B->ops) note_use(A, st);
+  if (!B->last_run && cudaEventCreateWithFlags(&B->last_run, cudaEventDisableTiming) != cudaSuccess)
+    return fail(QTT_ERR_CUDA, "qtt_batch_selftest_timeout: event");
+  cudaEventRecord(B->last_run, st);
+  return s;
 }
 
 qtt_status qtt_batch_status(qtt_batch *B, void *stream) {
@@ -793,11 +860,11 @@ qtt_status qtt_batch_info(const qtt_batch *B, int *waves, int *variant, int *gri
 
 qtt_status qtt_batch_destroy(qtt_batch *B) {
   if (!B) return QTT_OK;
-  cudaDeviceSynchronize();
+  // No device-wide synchronisation: the buffers go back to the pool after
+  // the batch's last run (an in-flight graph is freed when it completes).
   free_waves(B);
-  if (B->scratch) cudaFree(B->scratch);
-  if (B->d_next) cudaFree(B->d_next);
-  if (B->d_status) cudaFree(B->d_status);
+  release(B, {B->scratch, B->d_next, B->d_status});
+  if (B->last_run) cudaEventDestroy(B->last_run);
   delete B;
   return QTT_OK;
 }

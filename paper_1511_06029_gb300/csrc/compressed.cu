@@ -86,6 +86,7 @@ extern "C" qtt_status qtt_apply_tt(const qtt_op *A, const int *b_ranks, const do
                                    double *c_cores, void *stream) {
   if (!A || !b_ranks || !b_cores || !c_cores)
     return fail(QTT_ERR_INVALID_ARG, "qtt_apply_tt: NULL argument");
+  if (qtt_status ds = check_device(A, "qtt_apply_tt")) return ds;
   std::vector<int64_t> boff, coff;
   if (!sizes(A, b_ranks, &boff, &coff))
     return fail(QTT_ERR_INVALID_ARG,
@@ -109,7 +110,11 @@ extern "C" qtt_status qtt_apply_tt(const qtt_op *A, const int *b_ranks, const do
                                                       b_ranks[k + 1]);
     count_launches(1);
     const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "qtt_apply_tt: launch");
+    if (e != cudaSuccess) {
+      note_use(A, st);
+      return cuda_fail(e, "qtt_apply_tt: launch");
+    }
   }
+  note_use(A, st);
   return QTT_OK;
 }

@@ -24,34 +24,34 @@ constexpr size_t kNoAllocDoubles = kNoAllocBytes / sizeof(double);
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double *g_scratch_ptr[kMaxDevices] = {};
-
 // Device address of g_noalloc_scratch on the current device.  In host code
 // the symbol itself is only a host-side stand-in, so it is never handed to a
-// kernel; the address comes from cudaGetSymbolAddress, once per device, with
-// that device current.
+// kernel; the address comes from cudaGetSymbolAddress with that device
+// current.  It is looked up on every call (cheap, and it allocates nothing
+// once the array's module is loaded), so a module reloaded after a device
+// reset is picked up at its new address.
 qtt_status scratch_for_current_device(double **out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "qtt_apply_noalloc: cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices)
-    return fail(QTT_ERR_UNSUPPORTED, "qtt_apply_noalloc: device index out of range");
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
-                       "qtt_apply_noalloc: cudaGetSymbolAddress");
-    g_scratch_ptr[dev] = static_cast<double *>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                     "qtt_apply_noalloc: cudaGetSymbolAddress");
+  *out = static_cast<double *>(p);
   return QTT_OK;
 }
 
 }  // namespace
+
+// The first lookup on a device loads the module that holds the array, and
+// loading it is what commits the array's 64 MiB on that device.  qtt_create
+// calls this, so the commitment happens while the caller is still setting
+// up (it allocates the operator's cores anyway), before it hands its memory
+// to another allocator; qtt_apply_noalloc itself then allocates nothing.
+qtt_status noalloc_prepare() {
+  double *p = nullptr;
+  return scratch_for_current_device(&p);
+}
+
 }  // namespace qtt
 
 using namespace qtt;
@@ -59,6 +59,7 @@ using namespace qtt;
 extern "C" qtt_status qtt_apply_noalloc(const qtt_op *A, const double *x, double *y,
                                         int64_t nrhs, int64_t ld, void *stream) {
   if (!A) return fail(QTT_ERR_INVALID_ARG, "qtt_apply_noalloc: NULL operator");
+  if (qtt_status ds = check_device(A, "qtt_apply_noalloc")) return ds;
   const int d = A->d;
   const int64_t N = (int64_t)1 << d;
   if (nrhs < 0) return fail(QTT_ERR_INVALID_ARG, "qtt_apply_noalloc: nrhs < 0");
@@ -113,7 +114,11 @@ extern "C" qtt_status qtt_apply_noalloc(const qtt_op *A, const double *x, double
       p.out_rhs_stride = (int64_t)p.rout * N;
     }
     cudaError_t e = launch_step_f64(p, st);
-    if (e != cudaSuccess) return cuda_fail(e, "qtt_apply_noalloc: step launch");
+    if (e != cudaSuccess) {
+      note_use(A, st);
+      return cuda_fail(e, "qtt_apply_noalloc: step launch");
+    }
   }
+  note_use(A, st);
   return QTT_OK;
 }

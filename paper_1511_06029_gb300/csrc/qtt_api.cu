@@ -9,6 +9,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <unordered_map>
 
 #include "qtt_internal.h"
 #include "step_lp.h"
@@ -76,17 +77,33 @@ static size_t scratch_cached() {
   return reserved > used ? (size_t)(reserved - used) : 0;
 }
 
+// Scratch accounting for the cap of qtt_set_scratch_limit: bytes of scratch
+// handed out and not yet given back (all devices), and each block's size.
+static std::mutex g_scratch_mu;
+static std::unordered_map<void *, size_t> g_scratch_live;
+static size_t g_scratch_in_use = 0;
+static std::atomic<size_t> g_scratch_cap{0};  // 0 = no cap
+
+// What the cap leaves (SIZE_MAX without a cap).
+static size_t scratch_cap_room() {
+  const size_t cap = g_scratch_cap.load(std::memory_order_relaxed);
+  if (!cap) return SIZE_MAX;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  return cap > g_scratch_in_use ? cap - g_scratch_in_use : 0;
+}
+
 size_t scratch_available() {
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
   const size_t cached = scratch_cached();
   // Leave a margin for the driver and other allocators in the process.
   const size_t margin = (size_t)512 << 20;
-  return free_b > margin ? free_b - margin + cached : cached;
+  const size_t avail = free_b > margin ? free_b - margin + cached : cached;
+  return std::min(avail, scratch_cap_room());
 }
 
 size_t scratch_available_at_least(size_t bytes) {
-  const size_t cached = scratch_cached();
+  const size_t cached = std::min(scratch_cached(), scratch_cap_room());
   return cached >= bytes ? cached : scratch_available();
 }
 
@@ -97,17 +114,108 @@ qtt_status scratch_alloc(void **ptr, size_t bytes, cudaStream_t stream) {
   if (!p) return fail(QTT_ERR_CUDA, "cannot create the scratch memory pool");
   if (bytes > scratch_available_at_least(bytes))
     return fail(QTT_ERR_OOM, "scratch of " + std::to_string(bytes) +
-                                 " bytes exceeds free device memory");
+                                 " bytes exceeds free device memory (or the scratch limit)");
   cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes, p, stream);
   if (e != cudaSuccess) {
     *ptr = nullptr;
     return cuda_fail(e, "cudaMallocFromPoolAsync");
   }
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  g_scratch_live[*ptr] = bytes;
+  g_scratch_in_use += bytes;
   return QTT_OK;
 }
 
 void scratch_free(void *ptr, cudaStream_t stream) {
-  if (ptr) cudaFreeAsync(ptr, stream);
+  if (!ptr) return;
+  {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    auto it = g_scratch_live.find(ptr);
+    if (it != g_scratch_live.end()) {
+      g_scratch_in_use -= it->second;
+      g_scratch_live.erase(it);
+    }
+  }
+  cudaFreeAsync(ptr, stream);
+}
+
+// ----------------------------------------------------- long-lived buffers
+qtt_status persistent_alloc(void **ptr, size_t bytes, cudaStream_t stream) {
+  *ptr = nullptr;
+  if (bytes == 0) return QTT_OK;
+  cudaMemPool_t p = pool_for_current_device();
+  if (!p) return fail(QTT_ERR_CUDA, "cannot create the device memory pool");
+  cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes, p, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    if (*ptr) cudaFreeAsync(*ptr, stream);
+    *ptr = nullptr;
+    return cuda_fail(e, "persistent allocation");
+  }
+  return QTT_OK;
+}
+
+namespace {
+std::mutex g_release_mu;
+cudaStream_t g_release[64] = {};
+
+cudaStream_t release_stream_for_current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_release_mu);
+  if (!g_release[dev]) {
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    g_release[dev] = s;
+  }
+  return g_release[dev];
+}
+}  // namespace
+
+void release_after(const std::vector<void *> &ptrs, const std::vector<cudaEvent_t> &after) {
+  cudaStream_t rs = release_stream_for_current_device();
+  bool ordered = rs != nullptr;
+  for (cudaEvent_t ev : after)
+    if (ordered && cudaStreamWaitEvent(rs, ev, 0) != cudaSuccess) ordered = false;
+  if (!ordered) {
+    // no release stream: wait on the host for the recorded uses instead
+    for (cudaEvent_t ev : after) cudaEventSynchronize(ev);
+    if (!rs) cudaDeviceSynchronize();
+  }
+  for (void *p : ptrs)
+    if (p) cudaFreeAsync(p, rs);
+}
+
+void note_use(const qtt_op *A, cudaStream_t stream) {
+  if (!A) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
+  std::lock_guard<std::mutex> lk(A->use_mu);
+  cudaEvent_t ev = nullptr;
+  for (auto &u : A->uses)
+    if (u.first == stream) ev = u.second;
+  if (!ev) {
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    A->uses.emplace_back(stream, ev);
+  }
+  cudaEventRecord(ev, stream);
+}
+
+qtt_status check_device(const qtt_op *A, const char *where) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, where);
+  if (dev != A->device)
+    return fail(QTT_ERR_INVALID_ARG, std::string(where) + ": the operator lives on device " +
+                                         std::to_string(A->device) + " but device " +
+                                         std::to_string(dev) + " is current");
+  return QTT_OK;
 }
 
 // Host copy of the device TF32 rounding: round to nearest even at 13 dropped
@@ -123,6 +231,13 @@ static float host_tf32_rne(float x) {
   return x;
 }
 
+// Records, on every exit of an apply, that the work it queued on `st` reads A.
+struct UseGuard {
+  const qtt_op *A;
+  cudaStream_t st;
+  ~UseGuard() { note_use(A, st); }
+};
+
 // ------------------------------------------------------------ validation
 static bool valid_dtype(qtt_dtype t) {
   return t == QTT_F64 || t == QTT_F32 || t == QTT_TF32 || t == QTT_BF16;
@@ -131,6 +246,7 @@ static bool valid_dtype(qtt_dtype t) {
 // Apply of an FP64 operator, optionally with an epilogue on the last step.
 qtt_status apply_f64(const qtt_op *A, const double *x, double *y, int64_t nrhs,
                      int64_t ld, cudaStream_t st, const Epilogue &epi) {
+  const UseGuard use{A, st};
   const int d = A->d;
   const int64_t N = (int64_t)1 << d;
   // Scratch: two ping-pong buffers of rmax_inner x N per right-hand side.
@@ -245,6 +361,7 @@ static size_t dtype_size(qtt_dtype t) {
 qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype xt, void *y,
                     qtt_dtype yt, int64_t nrhs, int64_t ld, cudaStream_t st,
                     const LpEpilogue &epi) {
+  const UseGuard use{A, st};
   int mode;
   const void *cores;
   switch (compute) {
@@ -528,13 +645,24 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores
             M[(((size_t)b * ra + a) * 2 + j) * 2 + i] = G[(((size_t)a * 2 + i) * 2 + j) * rb + b];
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t bytes = (size_t)off * sizeof(double);
-  cudaError_t e = cudaMalloc(&A->m64, bytes);
-  if (e != cudaSuccess) {
-    delete A;
-    return cuda_fail(e, "qtt_create: cudaMalloc");
+  // qtt_apply_noalloc's static array is committed here, by an entry point
+  // that allocates anyway, so that a later qtt_apply_noalloc allocates nothing
+  {
+    const qtt_status ps = noalloc_prepare();
+    if (ps != QTT_OK) {
+      delete A;
+      return ps;
+    }
   }
-  e = cudaMemcpyAsync(A->m64, packed.data(), bytes, cudaMemcpyHostToDevice, st);
+  const size_t bytes = (size_t)off * sizeof(double);
+  {
+    const qtt_status as = persistent_alloc(reinterpret_cast<void **>(&A->m64), bytes, st);
+    if (as != QTT_OK) {
+      delete A;
+      return as;
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(A->m64, packed.data(), bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     qtt_destroy(A);
@@ -598,9 +726,8 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores
       A->tail[2] = small_copy(d - 3, vbf);
     }
     auto upload = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
-      cudaError_t e2 = cudaMalloc(dst, bytes);
-      if (e2 != cudaSuccess) return e2;
-      e2 = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st);
+      if (persistent_alloc(dst, bytes, st) != QTT_OK) return cudaErrorMemoryAllocation;
+      cudaError_t e2 = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st);
       if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
       return e2;
     };
@@ -657,12 +784,21 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores
 
 qtt_status qtt_destroy(qtt_op *A) {
   if (!A) return QTT_OK;
-  cudaDeviceSynchronize();
-  if (A->m64) cudaFree(A->m64);
-  if (A->m32) cudaFree(A->m32);
-  if (A->mtf32) cudaFree(A->mtf32);
-  if (A->mbf16) cudaFree(A->mbf16);
-  if (A->mma_bf16) cudaFree(A->mma_bf16);
+  // The buffers go back to the pool once the work recorded by note_use has
+  // finished: other streams and the host are not held up (no device-wide
+  // synchronisation).
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != A->device) cudaSetDevice(A->device);
+  std::vector<cudaEvent_t> evs;
+  {
+    std::lock_guard<std::mutex> lk(A->use_mu);
+    for (auto &u : A->uses) evs.push_back(u.second);
+    A->uses.clear();
+  }
+  release_after({A->m64, A->m32, A->mtf32, A->mbf16, A->mma_bf16}, evs);
+  for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+  if (cur >= 0 && cur != A->device) cudaSetDevice(cur);
   delete A;
   return QTT_OK;
 }
@@ -679,6 +815,7 @@ double qtt_op_flops(const qtt_op *A) { return A ? A->flops_per_rhs : 0.0; }
 qtt_status qtt_apply(const qtt_op *A, const void *x, void *y, int64_t nrhs, int64_t ld,
                      qtt_dtype io_dtype, qtt_dtype compute, void *stream) {
   if (!A) return fail(QTT_ERR_INVALID_ARG, "qtt_apply: NULL operator");
+  if (qtt_status ds = check_device(A, "qtt_apply")) return ds;
   if (!valid_dtype(io_dtype) || !valid_dtype(compute))
     return fail(QTT_ERR_INVALID_ARG, "qtt_apply: unknown dtype");
   const int64_t N = (int64_t)1 << A->d;
@@ -732,6 +869,7 @@ qtt_status qtt_plan_create(qtt_plan **out, const qtt_op *A, const void *x, void 
     if (s != QTT_OK) return s;
     return cuda_fail(e != cudaSuccess ? e : e2, "qtt_plan_create: stream capture");
   }
+  P->op = A;
   P->launches = t_launches - before;
   g_launches.fetch_sub(P->launches, std::memory_order_relaxed);  // recorded, not run
   t_launches = before;
@@ -750,6 +888,7 @@ qtt_status qtt_plan_run(qtt_plan *P, void *stream) {
   if (!P || !P->exec) return fail(QTT_ERR_INVALID_ARG, "qtt_plan_run: no plan");
   const cudaError_t e = cudaGraphLaunch(P->exec, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "qtt_plan_run: graph launch");
+  note_use(P->op, static_cast<cudaStream_t>(stream));
   count_launches(P->launches);
   return QTT_OK;
 }
@@ -765,6 +904,7 @@ qtt_status qtt_plan_destroy(qtt_plan *P) {
 qtt_status qtt_residual(const qtt_op *K, double a, const double *f, const double *x,
                         double *r, int64_t nrhs, int64_t ld, void *stream) {
   if (!K) return fail(QTT_ERR_INVALID_ARG, "qtt_residual: NULL operator");
+  if (qtt_status ds = check_device(K, "qtt_residual")) return ds;
   const int64_t N = (int64_t)1 << K->d;
   if (nrhs < 0 || (nrhs > 0 && ld < N))
     return fail(QTT_ERR_INVALID_ARG, "qtt_residual: bad nrhs or ld");
@@ -785,6 +925,27 @@ qtt_status qtt_residual(const qtt_op *K, double a, const double *f, const double
   e.s_u = -a;
   e.s_acc = -1.0;
   return apply_f64(K, x, r, nrhs, ld, static_cast<cudaStream_t>(stream), e);
+}
+
+qtt_status qtt_set_scratch_limit(size_t bytes) {
+  g_scratch_cap.store(bytes, std::memory_order_relaxed);
+  return QTT_OK;
+}
+
+qtt_status qtt_scratch_stats(size_t *in_use, size_t *pool_reserved, size_t *pool_used) {
+  if (in_use) {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    *in_use = g_scratch_in_use;
+  }
+  cudaMemPool_t p = pool_for_current_device();
+  uint64_t reserved = 0, used = 0;
+  if (p) {
+    cudaMemPoolGetAttribute(p, cudaMemPoolAttrReservedMemCurrent, &reserved);
+    cudaMemPoolGetAttribute(p, cudaMemPoolAttrUsedMemCurrent, &used);
+  }
+  if (pool_reserved) *pool_reserved = (size_t)reserved;
+  if (pool_used) *pool_used = (size_t)used;
+  return p ? QTT_OK : fail(QTT_ERR_CUDA, "qtt_scratch_stats: no memory pool");
 }
 
 qtt_status qtt_selftest_wait(double seconds, void *stream) {

@@ -5,7 +5,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/qtt.h"
@@ -29,12 +31,35 @@ void count_launches(uint64_t n);
 // freed blocks cached).  Returns QTT_ERR_OOM if `bytes` cannot be had.
 qtt_status scratch_alloc(void **ptr, size_t bytes, cudaStream_t stream);
 void scratch_free(void *ptr, cudaStream_t stream);
-// Bytes the pool could hand out right now without growing past free memory.
+// Bytes the pool could hand out right now without growing past free memory
+// (and below the cap set by QTT_SCRATCH_CAP_BYTES, when that is set).
 size_t scratch_available();
 // The same, but answered from the pool's own cached bytes (no query of the
 // device's free memory) when those already cover `bytes`.
 size_t scratch_available_at_least(size_t bytes);
 
+// Long-lived device buffers (operator cores, batch tables) come from the same
+// pool, so that releasing them is stream-ordered and never synchronises the
+// device.  persistent_alloc returns once the buffer is usable on any stream.
+qtt_status persistent_alloc(void **ptr, size_t bytes, cudaStream_t stream);
+// Release `ptrs` once every event in `after` has completed, without blocking
+// the host or any other stream: a per-device release stream waits on the
+// events and frees the buffers.
+void release_after(const std::vector<void *> &ptrs, const std::vector<cudaEvent_t> &after);
+
+}  // namespace qtt
+
+struct qtt_op;
+namespace qtt {
+// Record that work just queued on `stream` reads A (one event per stream,
+// re-recorded at each use; nothing is recorded while the stream is being
+// captured into a graph).  qtt_destroy releases A after these events.
+void note_use(const qtt_op *A, cudaStream_t stream);
+// QTT_ERR_INVALID_ARG unless the current device is the one A lives on.
+qtt_status check_device(const qtt_op *A, const char *where);
+// Commit the static array of qtt_apply_noalloc on the current device (loads
+// its module); done by qtt_create, which allocates anyway.
+qtt_status noalloc_prepare();
 }  // namespace qtt
 
 // One QTT matrix resident on the device.  Core k is packed as the matrix
@@ -72,11 +97,16 @@ struct qtt_op {
   // The same for the last three cores (d-3, d-2, d-1 as slots 0, 1, 2), for
   // the tail kernel.
   std::vector<float> tail[3];
+  // Streams that have queued work reading the operator, each with an event
+  // recorded after its latest use (see qtt::note_use).
+  mutable std::mutex use_mu;
+  mutable std::vector<std::pair<cudaStream_t, cudaEvent_t>> uses;
 };
 
 // One recorded apply (qtt_plan_*): the instantiated graph and how many of
 // the library's kernels one replay launches.
 struct qtt_plan {
+  const qtt_op *op = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   uint64_t launches = 0;

@@ -195,6 +195,9 @@ qtt_status qtt_server_submit(qtt_server *S, const qtt_op *K, const qtt_op *P, co
   if (S->prm.kind == QTT_SOLVE_DIRECT ? !P : !K)
     return fail(QTT_ERR_INVALID_ARG, "qtt_server_submit: missing operator for this solve kind");
   if (K && P && K->d != P->d) return fail(QTT_ERR_INVALID_ARG, "qtt_server_submit: d differs");
+  for (const qtt_op *A : {K, P})
+    if (A && A->device != S->device)
+      return fail(QTT_ERR_INVALID_ARG, "qtt_server_submit: operator lives on another device");
   Request *r = new (std::nothrow) Request();
   if (!r) return fail(QTT_ERR_OOM, "qtt_server_submit: host allocation");
   r->K = K;

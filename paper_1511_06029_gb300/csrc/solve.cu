@@ -432,6 +432,9 @@ extern "C" qtt_status qtt_solve(const qtt_op *K, const qtt_op *P, const double *
   if (prm->kind != QTT_SOLVE_DIRECT && !K)
     return fail(QTT_ERR_INVALID_ARG, "qtt_solve: GMRES and REFINE need K");
   if (K && P && K->d != P->d) return fail(QTT_ERR_INVALID_ARG, "qtt_solve: K and P differ in d");
+  for (const qtt_op *A : {K, P})
+    if (A)
+      if (qtt_status ds = check_device(A, "qtt_solve")) return ds;
   const qtt_op *any = K ? K : P;
   const int64_t N = (int64_t)1 << any->d;
   if (nrhs < 0) return fail(QTT_ERR_INVALID_ARG, "qtt_solve: nrhs < 0");

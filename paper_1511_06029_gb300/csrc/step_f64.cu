@@ -216,8 +216,12 @@ cudaError_t launch_step_f64(const StepF64 &s, cudaStream_t stream) {
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     return n;
   }();
-  const int64_t ctas = ((s.N >> 1) + 127) / 128 * ((s.rout + kWarpsY - 1) / kWarpsY) * s.nrhs;
-  if (ctas < 2 * sms) return launch_small(s, stream);
+  // The choice depends on one right-hand side's work only (not on nrhs): the
+  // two kernels sum in different orders, and a right-hand side must get the
+  // same bits whatever else shares its launch (chunked applies, batched
+  // solves, the server's requests).
+  const int64_t ctas_per_rhs = ((s.N >> 1) + 127) / 128 * ((s.rout + kWarpsY - 1) / kWarpsY);
+  if (ctas_per_rhs < 2 * sms) return launch_small(s, stream);
   return launch_tn<kTN>(s, stream);
 }
 

@@ -44,10 +44,19 @@ SIGNATURES = {
     "qtt_apply_tt_size": (_I, [_P, _P, ctypes.POINTER(_L)]),
     "qtt_apply_tt": (_I, [_P, _P, _P, _P, _P]),
     "qtt_selftest_wait": (_I, [_D, _P]),
+    "qtt_set_scratch_limit": (_I, [ctypes.c_size_t]),
+    "qtt_scratch_stats": (_I, [ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                               ctypes.POINTER(ctypes.c_size_t)]),
     "qtt_plan_create": (_I, [ctypes.POINTER(_P), _P, _P, _P, _L, _L, _I, _I]),
     "qtt_plan_run": (_I, [_P, _P]),
     "qtt_plan_destroy": (_I, [_P]),
     "qtt_solve": (_I, [_P, _P, _P, _P, _L, _L, _P, _P, _P]),
+    "qtt_gcreate": (_I, [ctypes.POINTER(_P), _I, _P, _P, _P, _P, _P]),
+    "qtt_gapply": (_I, [_P, _P, _P, _L, _L, _L, _I, _P]),
+    "qtt_gdestroy": (_I, [_P]),
+    "qtt_gop_rows": (_L, [_P]),
+    "qtt_gop_cols": (_L, [_P]),
+    "qtt_gop_flops": (_D, [_P, _I]),
     "qtt_status_string": (ctypes.c_char_p, [_I]),
     "qtt_last_error": (ctypes.c_char_p, []),
     "qtt_kernel_launches": (ctypes.c_uint64, []),
@@ -55,6 +64,7 @@ SIGNATURES = {
     "qtt_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _P, _P, _P, _P, _I, ctypes.c_size_t, _P]),
     "qtt_batch_run": (_I, [_P, _P]),
     "qtt_batch_status": (_I, [_P, _P]),
+    "qtt_batch_selftest_timeout": (_I, [_P, _D, _P]),
     "qtt_batch_set_variant": (_I, [_P, _I, _P]),
     "qtt_batch_autotune": (_I, [_P, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "qtt_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
@@ -303,6 +313,66 @@ class Operator:
             pass
 
 
+class GeneralOperator:
+    """A QTT matrix with m_k x n_k modes (qtt_gcreate / qtt_gdestroy).
+    cores[k]: array shaped (r_k, m_k, n_k, r_{k+1}); rectangular when
+    prod m != prod n."""
+
+    def __init__(self, cores, stream=None):
+        lib = load_library()
+        _torch()
+        cores = [np.ascontiguousarray(c, dtype=np.float64) for c in cores]
+        d = len(cores)
+        ranks = np.array([1] + [c.shape[3] for c in cores], dtype=np.int32)
+        m = np.array([c.shape[1] for c in cores], dtype=np.int32)
+        n = np.array([c.shape[2] for c in cores], dtype=np.int32)
+        for k, c in enumerate(cores):
+            if c.ndim != 4 or c.shape[0] != ranks[k]:
+                raise QTTError(QTT_ERR_INVALID_ARG, "qtt_gcreate", f"core {k} has shape {c.shape}")
+        flat = np.ascontiguousarray(np.concatenate([c.ravel() for c in cores]))
+        h = ctypes.c_void_p()
+        _check(lib.qtt_gcreate(ctypes.byref(h), d, ranks.ctypes.data_as(_P), m.ctypes.data_as(_P),
+                               n.ctypes.data_as(_P), flat.ctypes.data_as(_P),
+                               _stream_handle(stream)), "qtt_gcreate")
+        self._h = h
+        self.d = d
+        self.ranks = [int(v) for v in ranks]
+        self.m, self.n = [int(v) for v in m], [int(v) for v in n]
+        self.rows = int(lib.qtt_gop_rows(h))
+        self.cols = int(lib.qtt_gop_cols(h))
+
+    def flops(self, nrhs: int = 1, transpose: bool = False) -> float:
+        return load_library().qtt_gop_flops(self._h, 1 if transpose else 0) * nrhs
+
+    def apply(self, x, out=None, transpose: bool = False, stream=None):
+        """y = A x (or A^T x): x a CUDA float64 tensor (len,) or (nrhs, len)."""
+        torch = _torch()
+        nin, nout = (self.rows, self.cols) if transpose else (self.cols, self.rows)
+        nrhs, ldx = _block(x, nin, "qtt_gapply")
+        if out is None:
+            out = torch.empty((nout,) if x.dim() == 1 else (nrhs, nout), dtype=torch.float64,
+                              device=x.device)
+        n2, ldy = _block(out, nout, "qtt_gapply")
+        if n2 != nrhs or x.dtype != torch.float64 or out.dtype != torch.float64:
+            raise QTTError(QTT_ERR_INVALID_ARG, "qtt_gapply", "shape/dtype mismatch")
+        _check(load_library().qtt_gapply(self._h, ctypes.c_void_p(x.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), nrhs, ldx, ldy,
+                                         1 if transpose else 0, _stream_handle(stream)),
+               "qtt_gapply")
+        return out
+
+    def close(self):
+        if self._h is not None:
+            load_library().qtt_gdestroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def solve(K, P, f, kind: str = "gmres", a: float = 1.0, tol: float = 1e-10,
           restart: int = 30, max_iter: int = 300, precond_compute: str = "f64",
           inner_iters: int = 0, out=None, stream=None, raise_on_fail: bool = True):
@@ -361,6 +431,13 @@ class Batch:
 
     def status(self, stream=None):
         _check(load_library().qtt_batch_status(self._h, _stream_handle(stream)), "qtt_batch_status")
+
+    def selftest_timeout(self, seconds, stream=None):
+        """Run the first wave with a withheld dependency (qtt_batch_selftest_timeout);
+        the next status() raises QTT_ERR_TIMEOUT."""
+        _check(load_library().qtt_batch_selftest_timeout(self._h, float(seconds),
+                                                         _stream_handle(stream)),
+               "qtt_batch_selftest_timeout")
 
     def set_variant(self, v, stream=None):
         _check(load_library().qtt_batch_set_variant(self._h, v, _stream_handle(stream)),
@@ -472,6 +549,19 @@ def selftest_wait(seconds: float, stream=None):
     (qtt_selftest_wait); the next sync_status() raises QTT_ERR_TIMEOUT."""
     _check(load_library().qtt_selftest_wait(float(seconds), _stream_handle(stream)),
            "qtt_selftest_wait")
+
+
+def set_scratch_limit(nbytes: int):
+    """Cap the library's scratch at `nbytes` (0 = no cap; qtt_set_scratch_limit)."""
+    _check(load_library().qtt_set_scratch_limit(int(nbytes)), "qtt_set_scratch_limit")
+
+
+def scratch_stats():
+    """{'in_use', 'pool_reserved', 'pool_used'} in bytes (qtt_scratch_stats)."""
+    a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load_library().qtt_scratch_stats(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "qtt_scratch_stats")
+    return {"in_use": a.value, "pool_reserved": b.value, "pool_used": c.value}
 
 
 def sync_status(stream=None):
