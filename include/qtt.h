@@ -240,6 +240,66 @@ int64_t qtt_gop_rows(const qtt_gop *A);
 int64_t qtt_gop_cols(const qtt_gop *A);
 double qtt_gop_flops(const qtt_gop *A, int transpose);
 
+/* ----------------------------------------- whole-core QTT operations */
+/* qtt_tt_round -- TT rounding of a QTT vector or matrix held on the device
+ * (the recompression that keeps the ranks of the compressed product of
+ * Sec. 4.2 bounded; Tables 1-2, "QTT Solve"): left-to-right Householder QR
+ * orthogonalisation, then right-to-left truncated SVDs of the unfoldings,
+ * each keeping the smallest rank whose discarded singular values have 2-norm
+ * <= eps ||t||_F / sqrt(d - 1) -- the threshold of Algorithm 1 -- so that
+ * ||t - round(t)||_F <= eps ||t||_F.  FP64 throughout.
+ *   d, ranks : d cores, ranks[0..d] with ranks[0] = ranks[d] = 1, each in
+ *              [1, 32768]; n: entries per mode, 1..256 (2 for a QTT vector,
+ *              4 for a binary QTT matrix, whose core [r][2][2][r'] is
+ *              [r][4][r'] here).
+ *   cores_in : device FP64, core k as [ranks[k]][n][ranks[k+1]] in C order,
+ *              back to back (not modified).
+ *   eps      : >= 0 (0 drops only exactly-zero singular values).
+ *   ranks_out: host, d + 1 ints, the rounded ranks (never above the input
+ *              ranks).
+ *   cores_out: device FP64 with room for the INPUT cores (the rounded cores,
+ *              same layout, back to back, fit in it); may equal cores_in.
+ * Synchronous: it reads each unfolding's singular values back to choose the
+ * rank, and returns when cores_out is written.  Scratch (a few copies of the
+ * largest core) from the library's pool.  Errors: QTT_ERR_INVALID_ARG,
+ * QTT_ERR_OOM, QTT_ERR_CUDA. */
+qtt_status qtt_tt_round(int d, const int *ranks, int n, const double *cores_in, double eps,
+                        int *ranks_out, double *cores_out, void *stream);
+
+/* qtt_tt_svd -- Algorithm 1 (TT-SVD) on the device: the QTT decomposition
+ * of a dense 2^d x 2^d matrix A (device FP64, row-major, A(i, j) at i 2^d +
+ * j, 1 <= d <= 13).  The tensor's modes are the bit pairs (i_k, j_k),
+ * k = 0 .. d-1, least significant first; each unfolding is split by a
+ * truncated SVD that keeps the smallest rank whose discarded singular values
+ * have 2-norm <= eps ||A||_F / sqrt(d - 1), so ||A - A_tt||_F <= eps
+ * ||A||_F.  The cores come out in qtt_create's layout ([r_k][2 i][2 j]
+ * [r_{k+1}], back to back) in cores_out (device FP64, `capacity` doubles);
+ * ranks_out (host, d + 1) and *n_out (doubles needed) are always set.  If
+ * capacity < *n_out nothing is written and QTT_ERR_INVALID_ARG is returned
+ * (call again with room).  Synchronous, like qtt_tt_round.  Errors:
+ * QTT_ERR_INVALID_ARG, QTT_ERR_OOM, QTT_ERR_CUDA. */
+qtt_status qtt_tt_svd(int d, const double *A, double eps, int *ranks_out, double *cores_out,
+                      int64_t capacity, int64_t *n_out, void *stream);
+
+/* qtt_local_apply -- the left-hand side of the inversion's local linear
+ * system (appendix on local linear systems; Sec. 4.1): with X in QTT form and
+ * every core but W_k fixed, the reduced operator applied to W_k is the
+ * three-core product
+ *   y[b][i][p][B] = sum_{a, g, j, A, C} Psi[a][b][g] G[a][i][j][A] Phi[A][B][C]
+ *                                        W[g][j][p][C]
+ * (a, A: ranks of the operator's core G = G_k; b, g and B, C: ranks of X
+ * before and after core k; i, j, p: mode bits), evaluated as three FP64 GEMMs
+ * with two reorderings.
+ *   ra, ra2 : operator ranks r_k, r_{k+1}; rx, rx2: X's ranks.
+ *   psi     : device, [ra][rx][rx]; G: [ra][2][2][ra2]; phi: [ra2][rx2][rx2].
+ *   W, y    : device, nvec blocks of [rx][2][2][rx2] back to back (y must not
+ *             overlap the inputs).
+ * Asynchronous on `stream`; scratch from the library's pool.  Errors:
+ * QTT_ERR_INVALID_ARG, QTT_ERR_OOM, QTT_ERR_CUDA. */
+qtt_status qtt_local_apply(int ra, int ra2, int rx, int rx2, const double *psi, const double *G,
+                           const double *phi, const double *W, double *y, int64_t nvec,
+                           void *stream);
+
 /* qtt_residual -- r = f - (a x + K x), all FP64, the forward residual of the
  * second-kind system (a I + K) x = f (Sec. 3, eq. (nystrom): A = a I +
  * B K W C), with the subtraction fused into the last core step of the K

@@ -57,6 +57,9 @@ SIGNATURES = {
     "qtt_gop_rows": (_L, [_P]),
     "qtt_gop_cols": (_L, [_P]),
     "qtt_gop_flops": (_D, [_P, _I]),
+    "qtt_tt_round": (_I, [_I, _P, _I, _P, _D, _P, _P, _P]),
+    "qtt_tt_svd": (_I, [_I, _P, _D, _P, _P, _L, ctypes.POINTER(_L), _P]),
+    "qtt_local_apply": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _L, _P]),
     "qtt_status_string": (ctypes.c_char_p, [_I]),
     "qtt_last_error": (ctypes.c_char_p, []),
     "qtt_kernel_launches": (ctypes.c_uint64, []),
@@ -311,6 +314,83 @@ class Operator:
             self.close()
         except Exception:
             pass
+
+
+def _dev_f64(t, what):
+    torch = _torch()
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise QTTError(QTT_ERR_INVALID_ARG, what, "expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def tt_round(ranks, n, cores, eps, out=None, stream=None):
+    """TT rounding on the GPU (qtt_tt_round).  cores: CUDA float64 tensor of
+    the cores back to back, core k [r_k][n][r_{k+1}] (n = 2 for a QTT vector,
+    4 for a binary QTT matrix).  Returns (new ranks, tensor of the rounded
+    cores back to back)."""
+    torch = _torch()
+    r = np.ascontiguousarray(np.asarray(ranks, dtype=np.int32))
+    d = len(r) - 1
+    need = sum(int(r[k]) * n * int(r[k + 1]) for k in range(d))
+    if cores.numel() != need:
+        raise QTTError(QTT_ERR_INVALID_ARG, "qtt_tt_round", f"cores need {need} elements")
+    if out is None:
+        out = torch.empty_like(cores)
+    ro = np.zeros(d + 1, dtype=np.int32)
+    _check(load_library().qtt_tt_round(d, r.ctypes.data_as(_P), int(n),
+                                       _dev_f64(cores, "qtt_tt_round"), float(eps),
+                                       ro.ctypes.data_as(_P), _dev_f64(out, "qtt_tt_round"),
+                                       _stream_handle(stream)), "qtt_tt_round")
+    size = sum(int(ro[k]) * n * int(ro[k + 1]) for k in range(d))
+    return [int(v) for v in ro], out[:size]
+
+
+def tt_svd(A, eps, stream=None):
+    """Algorithm 1 on the GPU (qtt_tt_svd): A a CUDA float64 (2^d, 2^d)
+    tensor.  Returns (ranks, cores back to back as a CUDA tensor, each core
+    [r_k][2 i][2 j][r_{k+1}])."""
+    torch = _torch()
+    N = A.shape[0]
+    d = int(N).bit_length() - 1
+    if A.dim() != 2 or A.shape[1] != N or (1 << d) != N:
+        raise QTTError(QTT_ERR_INVALID_ARG, "qtt_tt_svd", "A must be 2^d x 2^d")
+    lib = load_library()
+    ro = np.zeros(d + 1, dtype=np.int32)
+    need = ctypes.c_int64(0)
+    # first call sizes the output (nothing is written), second fills it
+    cap = 4 * sum(min(4 ** k, 4 ** (d - k)) * min(4 ** (k + 1), 4 ** (d - k - 1)) for k in range(d))
+    cap = min(cap, 1 << 26)
+    out = torch.empty(cap, dtype=torch.float64, device=A.device)
+    st = lib.qtt_tt_svd(d, _dev_f64(A, "qtt_tt_svd"), float(eps), ro.ctypes.data_as(_P),
+                        ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(need),
+                        _stream_handle(stream))
+    if st == QTT_ERR_INVALID_ARG and need.value > cap:
+        out = torch.empty(need.value, dtype=torch.float64, device=A.device)
+        st = lib.qtt_tt_svd(d, _dev_f64(A, "qtt_tt_svd"), float(eps), ro.ctypes.data_as(_P),
+                            ctypes.c_void_p(out.data_ptr()), need.value, ctypes.byref(need),
+                            _stream_handle(stream))
+    _check(st, "qtt_tt_svd")
+    return [int(v) for v in ro], out[:need.value]
+
+
+def local_apply(psi, G, phi, W, out=None, stream=None):
+    """The inversion's local-system product (qtt_local_apply): psi (ra, rx,
+    rx), G (ra, 2, 2, ra2), phi (ra2, rx2, rx2), W (nvec, rx, 2, 2, rx2) or
+    (rx, 2, 2, rx2); CUDA float64.  Returns y shaped like W."""
+    torch = _torch()
+    ra, rx = psi.shape[0], psi.shape[1]
+    ra2, rx2 = phi.shape[0], phi.shape[1]
+    if (psi.shape != (ra, rx, rx) or G.shape != (ra, 2, 2, ra2) or phi.shape != (ra2, rx2, rx2)
+            or W.shape[-4:] != (rx, 2, 2, rx2)):
+        raise QTTError(QTT_ERR_INVALID_ARG, "qtt_local_apply", "inconsistent shapes")
+    nvec = 1 if W.dim() == 4 else W.shape[0]
+    if out is None:
+        out = torch.empty_like(W)
+    _check(load_library().qtt_local_apply(ra, ra2, rx, rx2, _dev_f64(psi, "psi"), _dev_f64(G, "G"),
+                                          _dev_f64(phi, "phi"), _dev_f64(W, "W"),
+                                          _dev_f64(out, "y"), nvec, _stream_handle(stream)),
+           "qtt_local_apply")
+    return out
 
 
 class GeneralOperator:
