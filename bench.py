@@ -262,10 +262,27 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def make_operator(spec):
+def make_operator(spec, reference=False):
+    """The workload's QTT operator.  The 8^3 Laplace volume operator is the
+    dense matrix compressed by Algorithm 1 at eps = 1e-8: on the GPU
+    (qtt_tt_svd) for this library's arm, by the oracle for the reference
+    arm."""
     if spec.get("laplace"):
-        op, _ = inputs.laplace_volume(8, 1e-8)
-        return op
+        A = inputs.laplace_volume_dense(8)
+        if reference:
+            import oracle
+            T = oracle.tt_svd(A, 1e-8)
+            return inputs.QTTData(list(T.ranks), list(T.cores), {"kind": "laplace"})
+        import torch
+        from paper_1511_06029_gb300 import qtt
+        ranks, flat = qtt.tt_svd(torch.from_numpy(A).cuda(), 1e-8)
+        host = flat.cpu().numpy()
+        cores, off = [], 0
+        for k in range(len(ranks) - 1):
+            sz = 4 * ranks[k] * ranks[k + 1]
+            cores.append(host[off:off + sz].reshape(ranks[k], 2, 2, ranks[k + 1]))
+            off += sz
+        return inputs.QTTData(ranks, cores, {"kind": "laplace"})
     return inputs.synthetic_operator(spec["d"], spec["rmax"], spec["seed"])
 
 
@@ -319,7 +336,7 @@ def run_reference_compressed(args, spec):
     """The oracle's compressed product (numpy) on the same operator and QTT
     vector as CompressedRun, whole problem per step."""
     import oracle
-    op = make_operator(spec)
+    op = make_operator(spec, reference=True)
     d = op.d
     br = [min(1 << k, 1 << (d - k), spec["smax"]) for k in range(d + 1)]
     rng = np.random.default_rng(spec["vec_seed"])
@@ -358,7 +375,7 @@ def run_reference(args, spec):
         it = inputs.batched_workload(count=1, seed=spec["seed"])[0]
         op = inputs.synthetic_operator(it["d"], it["rmax"], it["op_seed"])
     else:
-        op = make_operator(spec)
+        op = make_operator(spec, reference=True)
     blk, s = oracle_sample(op, target_s=float(os.environ.get("QTT_REF_STEP_S", "8")))
     x = inputs.gaussian_rhs(blk.N, 1, spec.get("rhs_seed", 1))[0]
     for _ in range(args.warmup):
@@ -798,37 +815,22 @@ RUNNERS = {"apply": ApplyRun, "batched": BatchedRun, "refine": RefineRun,
            "compressed": CompressedRun}
 
 # --------------------------------------------------------------- serving
-def _build_pair(args):
-    d, rmax, seed, eps = args
-    K = inputs.scaled_operator(d, rmax, seed)
-    P = inputs.neumann_preconditioner(K, eps)
-    return d, K, P
-
-
 def _serve_operators(d_range, rmax, seed_base, eps, qtt, log):
-    """K_d and P_d = round(I - K_d + K_d^2, eps) for every d, built on the host
-    in a spawn-started process pool (TT rounding is QR-bound), then uploaded."""
-    import concurrent.futures as cf
-    import multiprocessing as mp
+    """K_d (seeded cores) and P_d = round(I - K_d + K_d^2, eps) for every d,
+    P built on the GPU from K_d (qtt_op_product, qtt_tt_sum, qtt_tt_round)."""
     ds = list(range(d_range[0], d_range[1] + 1))
     t0 = time.perf_counter()
-    env_threads = os.environ.get("OPENBLAS_NUM_THREADS")
-    os.environ["OPENBLAS_NUM_THREADS"] = str(max(1, host_cores() // len(ds)))
-    try:
-        with cf.ProcessPoolExecutor(max_workers=len(ds),
-                                    mp_context=mp.get_context("spawn")) as ex:
-            built = list(ex.map(_build_pair, [(d, rmax, seed_base + d, eps) for d in ds]))
-    finally:
-        if env_threads is None:
-            os.environ.pop("OPENBLAS_NUM_THREADS", None)
-        else:
-            os.environ["OPENBLAS_NUM_THREADS"] = env_threads
-    log(f"built {len(ds)} operator pairs in {time.perf_counter() - t0:.1f} s")
     ops = {}
-    for d, K, P in built:
+    for d in ds:
+        K = inputs.scaled_operator(d, rmax, seed_base + d)
+        K64 = qtt.Operator(K)
+        rp, pcores = qtt.neumann_preconditioner(K64, eps)
+        K64.close()
+        P = inputs.QTTData(rp, pcores, {"kind": "neumann", "eps": eps})
         ops[d] = {"K": qtt.Operator(K, packs=("bf16", "f32", "tf32")), "P64": qtt.Operator(P),
                   "Pbf": qtt.Operator(P, packs=("bf16", "f32", "tf32")), "rP": max(P.ranks),
                   "data": (K, P)}
+    log(f"built {len(ds)} operator pairs on the GPU in {time.perf_counter() - t0:.1f} s")
     return ops
 
 

@@ -281,6 +281,32 @@ qtt_status qtt_tt_round(int d, const int *ranks, int n, const double *cores_in, 
 qtt_status qtt_tt_svd(int d, const double *A, double eps, int *ranks_out, double *cores_out,
                       int64_t capacity, int64_t *n_out, void *stream);
 
+/* qtt_op_product -- C = A B for two QTT matrices of the same d, core by core
+ * (Sec. 4.2: the compressed product, with a QTT matrix in place of the
+ * vector; e.g. K^2 for a Neumann preconditioner or M Y for a product
+ * preconditioner): C_k[a s + b][i][p][a' s' + b'] = sum_j A_k[a][i][j][a']
+ * B_k[b][j][p][b'] (s, s' = B's ranks), each entry fl(fl(A_0 B_0) +
+ * fl(A_1 B_1)).  c_ranks (host, d + 1) receives r_k s_k (each must be <=
+ * 32768); c_cores (device FP64, `capacity` doubles, at least
+ * 4 sum_k r_k s_k r_{k+1} s_{k+1}) receives C's cores in qtt_create's layout.
+ * Asynchronous on `stream`.  Errors: QTT_ERR_INVALID_ARG, QTT_ERR_CUDA. */
+qtt_status qtt_op_product(const qtt_op *A, const qtt_op *B, double *c_cores, int64_t capacity,
+                          int *c_ranks, void *stream);
+
+/* qtt_tt_sum -- sum_t coefs[t] T_t of nterms QTT tensors with d cores and n
+ * entries per mode (2: vectors, 4: binary matrices), by concatenating the
+ * ranks (Sec. 3.3: the ranks of a sum add up): first cores side by side,
+ * middle cores block-diagonal, last cores stacked and scaled by coefs[t].
+ *   ranks[t]  : host, d + 1 ints of term t (ranks[t][0] = ranks[t][d] = 1);
+ *   cores[t]  : device FP64, term t's cores back to back ([r][n][r']);
+ *   ranks_out : host, d + 1 ints, the summed ranks;
+ *   cores_out : device FP64, `capacity` doubles (at least sum_k n R_k
+ *               R_{k+1} for the summed ranks R), must not overlap the terms.
+ * Asynchronous on `stream`.  Errors: QTT_ERR_INVALID_ARG, QTT_ERR_CUDA. */
+qtt_status qtt_tt_sum(int d, int n, int nterms, const int *const *ranks,
+                      const double *const *cores, const double *coefs, int *ranks_out,
+                      double *cores_out, int64_t capacity, void *stream);
+
 /* qtt_local_apply -- the left-hand side of the inversion's local linear
  * system (appendix on local linear systems; Sec. 4.1): with X in QTT form and
  * every core but W_k fixed, the reduced operator applied to W_k is the

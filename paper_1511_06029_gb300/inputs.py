@@ -1,20 +1,20 @@
 """Seeded synthetic inputs for the QTT apply and solves.
 
 This module is the only code that both the CUDA path and the CPU oracle
-consume.  It produces operators (QTT cores) and right-hand sides; it holds
-none of the apply or solve arithmetic under test.  Building the operators does
-use the paper's compression tools (TT-SVD, Algorithm 1; TT rounding) and the
-core-wise product/sum needed to form a preconditioner; those are set-up steps,
-never the hot path, and the tests pin them separately.
+consume.  It produces seeded data -- QTT cores, dense matrices, right-hand
+sides, workload draws -- and holds none of the method's arithmetic: the
+compression of a dense matrix (Algorithm 1), TT rounding and the core-wise
+products and sums that form a preconditioner are done by each side with its
+own code (the library's GPU entry points, or the oracle).
 
 Recipes (all draws from ``numpy.random.default_rng(seed)``, PCG64, which gives
 the same stream on every platform):
 
-* ``laplace_volume`` -- second-kind volume operator A = I + h^3 K on a
-  uniform n x n x n grid, h = 1/n, K(x, y) = 1/(4 pi |x - y|) for x != y and
-  0 on the diagonal (punctured trapezoid rule, Sec. 5.2), points in Morton
-  order (bit 3l + c of the index is bit l of coordinate c), compressed by
-  TT-SVD (Algorithm 1) at accuracy eps.
+* ``laplace_volume_dense`` -- the dense second-kind volume operator
+  A = I + h^3 K on a uniform n x n x n grid, h = 1/n, K(x, y) =
+  1/(4 pi |x - y|) for x != y and 0 on the diagonal (punctured trapezoid
+  rule, Sec. 5.2), points in Morton order (bit 3l + c of the index is bit l
+  of coordinate c); its QTT form comes from Algorithm 1 at eps = 1e-8.
 * ``synthetic_operator`` -- ranks r_k = min(2^k, 2^(d-k), r_max); every core
   but the last is drawn i.i.d. N(0, 1/(4 r_{k-1})), reshaped to a
   (4 r_{k-1}) x r_k matrix, replaced by the Q of its thin QR and its columns
@@ -154,56 +154,6 @@ def laplace_volume_dense(n: int = 8) -> np.ndarray:
     return np.eye(p.shape[0]) + h ** 3 * K
 
 
-def matrix_to_qtt_tensor(A: np.ndarray) -> np.ndarray:
-    """Tensorise a 2^d x 2^d matrix on the product tree (Sec. 3.1): mode k is
-    b_k = 2 i_k + j_k, modes ordered k = 0..d-1 (finest first)."""
-    N = A.shape[0]
-    d = int(round(math.log2(N)))
-    # C-order reshape gives axes (i_{d-1}, ..., i_0, j_{d-1}, ..., j_0)
-    T = A.reshape([2] * (2 * d))
-    perm = []
-    for k in range(d):
-        perm += [d - 1 - k, 2 * d - 1 - k]  # i_k, j_k
-    return np.ascontiguousarray(T.transpose(perm)).reshape([4] * d)
-
-
-def tt_svd(T: np.ndarray, eps: float):
-    """Algorithm 1 (TT decomposition by successive truncated SVDs).  Each
-    unfolding keeps the smallest rank whose discarded singular values have
-    Frobenius norm <= eps ||T||_F / sqrt(d-1) (rank >= 1).  Returns
-    (ranks, cores) with cores shaped (r_k, n_k, r_{k+1})."""
-    dims = T.shape
-    d = len(dims)
-    delta = eps * np.linalg.norm(T.ravel()) / math.sqrt(max(d - 1, 1))
-    ranks = [1]
-    cores = []
-    M = T.reshape(dims[0], -1)
-    for k in range(d - 1):
-        U, S, Vt = np.linalg.svd(M, full_matrices=False)
-        tail = np.sqrt(np.cumsum((S ** 2)[::-1]))[::-1]  # tail[r] = ||S[r:]||
-        r = len(S)
-        for cand in range(1, len(S) + 1):
-            rest = tail[cand] if cand < len(S) else 0.0
-            if rest <= delta:
-                r = cand
-                break
-        cores.append(U[:, :r].reshape(ranks[-1], dims[k], r))
-        ranks.append(r)
-        M = (S[:r, None] * Vt[:r]).reshape(r * dims[k + 1], -1)
-    cores.append(M.reshape(ranks[-1], dims[d - 1], 1))
-    ranks.append(1)
-    return ranks, cores
-
-
-def laplace_volume(n: int = 8, eps: float = 1e-8):
-    """The n^3 Laplace volume operator A = I + h^3 K (Sec. 5.2) compressed by
-    TT-SVD at eps.  Returns (QTTData, dense A)."""
-    A = laplace_volume_dense(n)
-    ranks, cores = tt_svd(matrix_to_qtt_tensor(A), eps)
-    cores = [c.reshape(c.shape[0], 2, 2, c.shape[2]) for c in cores]
-    return QTTData(ranks, cores, {"kind": "laplace", "n": n, "eps": eps}), A
-
-
 # ------------------------------------------ operator norms and preconditioner
 def knorm_table() -> dict:
     """Stored spectral norms ||K||_2 of the synthetic operators used by the
@@ -234,96 +184,6 @@ def scaled_operator(d: int, rmax: int, seed: int, target: float = 0.5,
     out = K.scaled(target / sigma)
     out.meta.update({"knorm_target": target, "knorm_unscaled": sigma})
     return out
-
-
-def _core_product(A: QTTData, B: QTTData) -> QTTData:
-    """Core-wise product A B (ranks multiply); set-up only."""
-    cores = []
-    for a, b in zip(A.cores, B.cores):
-        # c[(p,q), i, j, (s,t)] = sum_l a[p,i,l,s] b[q,l,j,t]
-        c = np.einsum("pils,qljt->pqijst", a, b)
-        pa, qa = a.shape[0], b.shape[0]
-        sa, tb = a.shape[3], b.shape[3]
-        cores.append(c.reshape(pa * qa, 2, 2, sa * tb))
-    ranks = [A.ranks[k] * B.ranks[k] for k in range(A.d + 1)]
-    return QTTData(ranks, cores)
-
-
-def _core_sum(terms) -> QTTData:
-    """sum of operators (list of (coef, QTTData)) by rank concatenation."""
-    d = terms[0][1].d
-    ranks = [1] + [sum(t.ranks[k] for _, t in terms) for k in range(1, d)] + [1]
-    cores = []
-    for k in range(d):
-        c = np.zeros((ranks[k], 2, 2, ranks[k + 1]))
-        ro = co = 0
-        for coef, t in terms:
-            g = t.cores[k] * (coef if k == d - 1 else 1.0)
-            ra, rb = g.shape[0], g.shape[3]
-            r0 = ro if k > 0 else 0
-            c0 = co if k < d - 1 else 0
-            c[r0:r0 + ra, :, :, c0:c0 + rb] += g
-            ro += ra if k > 0 else 0
-            co += rb if k < d - 1 else 0
-        cores.append(c)
-    return QTTData(ranks, cores)
-
-
-def neumann_preconditioner_unrounded(K: QTTData) -> QTTData:
-    """I - K + K^2 as an exact QTT (rank 1 + r + r^2)."""
-    if K.d == 1:
-        I2 = np.eye(2)
-        k = K.cores[0][0, :, :, 0]
-        return QTTData([1, 1], [(I2 - k + k @ k).reshape(1, 2, 2, 1)])
-    K2 = _core_product(K, K)
-    return _core_sum([(1.0, identity(K.d)), (-1.0, K), (1.0, K2)])
-
-
-def tt_round(op: QTTData, eps: float) -> QTTData:
-    """TT rounding (Oseledets): right-to-left QR orthogonalisation, then a
-    left-to-right sweep of truncated SVDs with the Algorithm 1 threshold
-    eps ||A||_F / sqrt(d-1)."""
-    d = op.d
-    cores = [np.asarray(c, dtype=np.float64).reshape(c.shape[0], 4, c.shape[3]).copy()
-             for c in op.cores]
-    ranks = list(op.ranks)
-    # right-to-left orthogonalisation: core k becomes row-orthonormal
-    for k in range(d - 1, 0, -1):
-        ra, n, rb = cores[k].shape
-        M = cores[k].reshape(ra, n * rb)
-        Q, R = np.linalg.qr(M.T)  # M^T = Q R  =>  M = R^T Q^T
-        rnew = Q.shape[1]
-        cores[k] = Q.T.reshape(rnew, n, rb)
-        pa, pn, _ = cores[k - 1].shape
-        cores[k - 1] = (cores[k - 1].reshape(pa * pn, -1) @ R.T).reshape(pa, pn, rnew)
-        ranks[k] = rnew
-    norm = np.linalg.norm(cores[0].ravel())
-    delta = eps * norm / math.sqrt(max(d - 1, 1))
-    for k in range(d - 1):
-        ra, n, rb = cores[k].shape
-        U, S, Vt = np.linalg.svd(cores[k].reshape(ra * n, rb), full_matrices=False)
-        tail = np.sqrt(np.cumsum((S ** 2)[::-1]))[::-1]
-        r = len(S)
-        for cand in range(1, len(S) + 1):
-            rest = tail[cand] if cand < len(S) else 0.0
-            if rest <= delta:
-                r = cand
-                break
-        cores[k] = U[:, :r].reshape(ra, n, r)
-        SV = S[:r, None] * Vt[:r]
-        _, nn, rc = cores[k + 1].shape
-        cores[k + 1] = (SV @ cores[k + 1].reshape(rb, nn * rc)).reshape(r, nn, rc)
-        ranks[k + 1] = r
-    out = [c.reshape(c.shape[0], 2, 2, c.shape[2]) for c in cores]
-    return QTTData(ranks, out, dict(op.meta, rounded_eps=eps))
-
-
-def neumann_preconditioner(K: QTTData, eps: float = 1e-4) -> QTTData:
-    """P = round(I - K + K^2, eps): approximate inverse of I + K for
-    ||K|| < 1 (error operator -K^3 before rounding)."""
-    P = tt_round(neumann_preconditioner_unrounded(K), eps)
-    P.meta.update({"kind": "neumann_preconditioner", "eps": eps})
-    return P
 
 
 # ------------------------------------------------------- workload draws

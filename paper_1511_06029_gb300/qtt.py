@@ -60,6 +60,8 @@ SIGNATURES = {
     "qtt_tt_round": (_I, [_I, _P, _I, _P, _D, _P, _P, _P]),
     "qtt_tt_svd": (_I, [_I, _P, _D, _P, _P, _L, ctypes.POINTER(_L), _P]),
     "qtt_local_apply": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _L, _P]),
+    "qtt_op_product": (_I, [_P, _P, _P, _L, _P, _P]),
+    "qtt_tt_sum": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _L, _P]),
     "qtt_status_string": (ctypes.c_char_p, [_I]),
     "qtt_last_error": (ctypes.c_char_p, []),
     "qtt_kernel_launches": (ctypes.c_uint64, []),
@@ -222,6 +224,11 @@ class Operator:
         self.N = 1 << d
         self.ranks = [int(v) for v in ranks]
         self.packs = tuple(packs)
+        self._flat = flat
+
+    def host_cores_flat(self):
+        """The FP64 cores given at creation, back to back (host copy)."""
+        return self._flat
 
     @property
     def handle(self):
@@ -371,6 +378,64 @@ def tt_svd(A, eps, stream=None):
                             _stream_handle(stream))
     _check(st, "qtt_tt_svd")
     return [int(v) for v in ro], out[:need.value]
+
+
+def op_product(A, B, stream=None):
+    """C = A B core by core on the GPU (qtt_op_product).  Returns (ranks, CUDA
+    float64 tensor of C's cores back to back, [r][2][2][r'] each)."""
+    torch = _torch()
+    if A.d != B.d:
+        raise QTTError(QTT_ERR_INVALID_ARG, "qtt_op_product", "operators differ in d")
+    rc = [a * b for a, b in zip(A.ranks, B.ranks)]
+    n = 4 * sum(rc[k] * rc[k + 1] for k in range(A.d))
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    ro = np.zeros(A.d + 1, dtype=np.int32)
+    _check(load_library().qtt_op_product(A.handle, B.handle, ctypes.c_void_p(out.data_ptr()), n,
+                                         ro.ctypes.data_as(_P), _stream_handle(stream)),
+           "qtt_op_product")
+    return [int(v) for v in ro], out
+
+
+def tt_sum(terms, n, stream=None):
+    """sum_t c_t T_t on the GPU (qtt_tt_sum).  terms: list of (coef, ranks,
+    CUDA float64 cores back to back); n entries per mode.  Returns (ranks,
+    cores)."""
+    torch = _torch()
+    d = len(terms[0][1]) - 1
+    rk = [np.ascontiguousarray(np.asarray(r, dtype=np.int32)) for _, r, _ in terms]
+    R = [1] + [sum(int(r[k]) for r in rk) for k in range(1, d)] + [1]
+    size = sum(n * R[k] * R[k + 1] for k in range(d))
+    out = torch.empty(size, dtype=torch.float64, device="cuda")
+    T = len(terms)
+    rptr = (_P * T)(*[r.ctypes.data_as(_P) for r in rk])
+    cptr = (_P * T)(*[_dev_f64(c, "qtt_tt_sum").value for _, _, c in terms])
+    coef = (ctypes.c_double * T)(*[float(c) for c, _, _ in terms])
+    ro = np.zeros(d + 1, dtype=np.int32)
+    _check(load_library().qtt_tt_sum(d, int(n), T, ctypes.cast(rptr, _P), ctypes.cast(cptr, _P),
+                                     ctypes.cast(coef, _P), ro.ctypes.data_as(_P),
+                                     ctypes.c_void_p(out.data_ptr()), size,
+                                     _stream_handle(stream)), "qtt_tt_sum")
+    return [int(v) for v in ro], out
+
+
+def neumann_preconditioner(K, eps, stream=None):
+    """P = round(I - K + K^2, eps) built on the GPU from the operator K
+    (qtt_op_product, qtt_tt_sum, qtt_tt_round).  Returns (ranks, host list
+    of cores shaped (r, 2, 2, r'))."""
+    torch = _torch()
+    d = K.d
+    r2, k2 = op_product(K, K, stream)
+    kflat = torch.from_numpy(np.ascontiguousarray(K.host_cores_flat())).cuda()
+    ident = torch.from_numpy(np.tile(np.eye(2).ravel(), d)).cuda()
+    rs, s = tt_sum([(1.0, [1] * (d + 1), ident), (-1.0, K.ranks, kflat), (1.0, r2, k2)], 4, stream)
+    rp, p = tt_round(rs, 4, s, eps, stream=stream)
+    host = p.cpu().numpy()
+    cores, off = [], 0
+    for k in range(d):
+        sz = 4 * rp[k] * rp[k + 1]
+        cores.append(host[off:off + sz].reshape(rp[k], 2, 2, rp[k + 1]))
+        off += sz
+    return rp, cores
 
 
 def local_apply(psi, G, phi, W, out=None, stream=None):

@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_1511_06029_gb300 import inputs
-from conftest import rel_l2
+from conftest import rel_l2, laplace_qtt
 
 pytestmark = pytest.mark.gpu
 
@@ -67,7 +67,7 @@ def test_laplace_volume_8cubed(qtt):
     """The 8^3 Laplace volume operator compressed by TT-SVD at 1e-8: GPU vs
     oracle on the same cores to 1e-12, and vs the dense 512 x 512 product
     within the TT-SVD bound eps ||A||_F ||x||."""
-    op, A = inputs.laplace_volume(8, 1e-8)
+    op, A = laplace_qtt(oracle, 8, 1e-8)
     x = inputs.gaussian_rhs(512, 1, 1)
     y = _apply(qtt, op, x)
     assert rel_l2(y, oracle.apply(op, x)) <= TOL_F64

@@ -19,7 +19,7 @@ import pytest
 
 import oracle
 from paper_1511_06029_gb300 import inputs
-from conftest import rel_l2
+from conftest import rel_l2, neumann
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +53,7 @@ def test_refinement_full_size(qtt):
 
 def test_serving_request_full_size(qtt):
     K = inputs.scaled_operator(22, 32, 5022)
-    P = inputs.neumann_preconditioner(K, 1e-4)
+    P = neumann(oracle, K, 1e-4)
     f = inputs.gaussian_rhs(K.N, 1, 6)
     Kg, Pg = qtt.Operator(K), qtt.Operator(P, packs=("bf16",))
     S = qtt.Server(slots=2, kind="gmres", tol=3e-11, precond_compute="bf16")

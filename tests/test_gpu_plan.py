@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_1511_06029_gb300 import inputs
-from conftest import rel_l2
+from conftest import rel_l2, laplace_qtt
 
 pytestmark = pytest.mark.gpu
 
@@ -47,7 +47,7 @@ def test_replay_is_bitwise_the_apply(qtt, compute, dtype, packs):
 def test_small_operator_replays(qtt):
     """The 8^3 volume operator (d = 9), many replays on one stream."""
     import torch
-    data, _ = inputs.laplace_volume(8, 1e-8)
+    data, _ = laplace_qtt(oracle, 8, 1e-8)
     op = qtt.Operator(data)
     x = torch.from_numpy(inputs.gaussian_rhs(data.N, 1, 1)).cuda()
     y = torch.empty_like(x)

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_1511_06029_gb300 import inputs
-from conftest import rel_l2
+from conftest import rel_l2, neumann
 
 pytestmark = pytest.mark.gpu
 
@@ -27,7 +27,7 @@ def operators(qtt):
     ops = {}
     for d in (8, 9, 10):
         K = inputs.scaled_operator(d, 8, 7000 + d)
-        P = inputs.neumann_preconditioner(K, 1e-4)
+        P = neumann(oracle, K, 1e-4)
         ops[d] = (K, P, qtt.Operator(K), qtt.Operator(P, packs=("bf16",)))
     yield ops
     for _, _, Kg, Pg in ops.values():

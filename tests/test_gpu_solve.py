@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from paper_1511_06029_gb300 import inputs
-from conftest import rel_l2
+from conftest import rel_l2, neumann, neumann_unrounded
 
 pytestmark = pytest.mark.gpu
 
@@ -27,7 +27,7 @@ def qtt():
 
 def _problem(d):
     K = inputs.scaled_operator(d, 8, 7000 + d)
-    P = inputs.neumann_preconditioner(K, 1e-4)
+    P = neumann(oracle, K, 1e-4)
     return K, P
 
 
@@ -97,7 +97,7 @@ def test_refine_contraction_pin(qtt):
     number of refinement steps to 1e-12 is at most ceil(12 / -log10 0.125)
     plus the initial apply and one step of slack."""
     K = inputs.scaled_operator(8, 8, 7008)
-    P = inputs.neumann_preconditioner_unrounded(K)
+    P = neumann_unrounded(oracle, K)
     f = inputs.gaussian_rhs(K.N, 1, 15)
     Kg, Pg = qtt.Operator(K), qtt.Operator(P)
     x, info = qtt.solve(Kg, Pg, _gpu(f), kind="refine", tol=1e-12, max_iter=100)

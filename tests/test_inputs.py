@@ -1,12 +1,14 @@
-"""Pins for the seeded input generator (operators built by TT-SVD, TT
-rounding and the synthetic recipe)."""
+"""Pins for the seeded input generator (the synthetic recipe, the Laplace
+volume matrix, workload draws) and for the operators the tests build from it
+with the oracle (Algorithm 1 on the Laplace matrix, the Neumann
+preconditioner)."""
 import math
 
 import numpy as np
 import pytest
 
 from paper_1511_06029_gb300 import inputs
-from conftest import rel_l2
+from conftest import rel_l2, laplace_qtt, neumann_unrounded
 
 
 def test_morton_order_bits():
@@ -32,11 +34,12 @@ def test_laplace_dense_closed_form():
     assert np.allclose(A, A.T)
 
 
-def test_tt_svd_error_bound(oracle_mod):
-    """Algorithm 1 with the eps/sqrt(d-1) threshold: ||A - A_tt||_F <=
-    eps ||A||_F, and hence ||A x - A_tt x|| <= eps ||A||_F ||x||."""
+def test_laplace_qtt_error_bound(oracle_mod):
+    """The 8^3 operator from the oracle's Algorithm 1 with the eps/sqrt(d-1)
+    threshold: ||A - A_tt||_F <= eps ||A||_F, hence ||A x - A_tt x|| <=
+    eps ||A||_F ||x||."""
     eps = 1e-8
-    op, A = inputs.laplace_volume(8, eps)
+    op, A = laplace_qtt(oracle_mod, 8, eps)
     assert op.d == 9 and op.ranks[0] == 1 and op.ranks[-1] == 1
     for k in range(op.d + 1):
         assert op.ranks[k] <= min(4 ** k, 4 ** (op.d - k))
@@ -46,17 +49,6 @@ def test_tt_svd_error_bound(oracle_mod):
     x = inputs.gaussian_rhs(512, 1, 1)[0]
     err = np.linalg.norm(A @ x - oracle_mod.apply(op, x))
     assert err <= eps * nA * np.linalg.norm(x)
-
-
-def test_tt_svd_exact_for_kronecker():
-    """A rank-1 (Kronecker) matrix is recovered with all ranks 1."""
-    rng = np.random.default_rng(3)
-    mats = [rng.standard_normal((2, 2)) for _ in range(5)]
-    K = np.array([[1.0]])
-    for m in mats:
-        K = np.kron(m, K)
-    ranks, cores = inputs.tt_svd(inputs.matrix_to_qtt_tensor(K), 1e-12)
-    assert ranks == [1] * 6
 
 
 def test_synthetic_recipe():
@@ -87,20 +79,20 @@ def test_neumann_preconditioner_exact_and_rounded(oracle_mod):
     DK = oracle_mod.dense(K)
     K = K.scaled(0.5 / np.linalg.norm(DK, 2))
     DK = oracle_mod.dense(K)
-    P = inputs.neumann_preconditioner_unrounded(K)
+    P = neumann_unrounded(oracle_mod, K)
     assert P.ranks[1:-1] == [1 + r + r * r for r in K.ranks[1:-1]]
     DP = oracle_mod.dense(P)
     I = np.eye(1 << d)
     assert np.allclose(DP, I - DK + DK @ DK, atol=1e-14)
     for eps in (1e-4, 1e-8):
-        Pr = inputs.tt_round(P, eps)
+        Pr = oracle_mod.tt_round(P, eps)
         assert max(Pr.ranks) <= max(P.ranks)
         assert np.linalg.norm(oracle_mod.dense(Pr) - DP) <= eps * np.linalg.norm(DP) * (1 + 1e-9)
 
 
 def test_tt_round_lossless_at_tiny_eps(oracle_mod):
     op = inputs.random_cores(6, [1, 3, 5, 5, 4, 2, 1], 9)
-    r = inputs.tt_round(op, 1e-14)
+    r = oracle_mod.tt_round(op, 1e-14)
     assert rel_l2(oracle_mod.dense(r), oracle_mod.dense(op)) <= 1e-12
 
 

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from paper_1511_06029_gb300 import inputs
-from conftest import rel_l2
+from conftest import rel_l2, neumann_unrounded
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -199,7 +199,7 @@ def test_gmres_matches_dense_solve(oracle_mod):
     x, it, rel = oracle_mod.solve_gmres(K, None, f, a=1.0, tol=1e-13, restart=10,
                                         max_iter=400)
     assert rel_l2(x, xs) <= 1e-11 and (rel <= 1e-13).all()
-    P = inputs.neumann_preconditioner_unrounded(K)
+    P = neumann_unrounded(oracle_mod, K)
     x2, it2, rel2 = oracle_mod.solve_gmres(K, P, f, a=1.0, tol=1e-13, restart=30)
     assert rel_l2(x2, xs) <= 1e-11
     assert it2.max() < it.max()
@@ -217,7 +217,7 @@ def test_refine_contracts_like_neumann(oracle_mod):
     1e-13 are bounded by ceil(13 / -log10 ||K^3||) + 1."""
     d = 8
     K = _scaled(oracle_mod, _small_solve_problem(d), 0.5)
-    P = inputs.neumann_preconditioner_unrounded(K)
+    P = neumann_unrounded(oracle_mod, K)
     DK = oracle_mod.dense(K)
     E = np.eye(1 << d) - oracle_mod.dense(P) @ (np.eye(1 << d) + DK)
     assert np.allclose(E, -DK @ DK @ DK, atol=1e-14)
@@ -384,12 +384,35 @@ def test_tt_svd_kronecker_is_rank_one(oracle_mod):
 
 def test_tt_svd_laplace_volume(oracle_mod):
     """The 8^3 Laplace volume matrix at eps = 1e-8: within the bound, and the
-    same ranks as the input generator's own (independent) Algorithm 1 code."""
+    same ranks as an independent Algorithm 1 written here (modes built by an
+    explicit bit transpose, rank chosen by a cumulative tail search)."""
     D = inputs.laplace_volume_dense(8)
     T = oracle_mod.tt_svd(D, 1e-8)
     assert np.linalg.norm(oracle_mod.dense(T) - D) <= 1e-8 * np.linalg.norm(D) * (1 + 1e-9)
-    gen, _ = inputs.laplace_volume(8, 1e-8)
-    assert T.ranks == list(gen.ranks)
+    assert T.ranks == _alg1_ranks(D, 1e-8)
+
+
+def _alg1_ranks(A, eps):
+    """Ranks of Algorithm 1 on the 2^d x 2^d matrix A, computed independently
+    of the oracle: the tensor with modes b_k = 2 i_k + j_k (k = 0 first) by an
+    axis transpose of A's bits, then successive SVDs, each keeping the
+    smallest r with ||S[r:]|| <= eps ||A||_F / sqrt(d - 1)."""
+    N = A.shape[0]
+    d = int(round(np.log2(N)))
+    T = A.reshape([2] * (2 * d))          # axes i_{d-1} .. i_0, j_{d-1} .. j_0
+    perm = []
+    for k in range(d):
+        perm += [d - 1 - k, 2 * d - 1 - k]
+    T = np.ascontiguousarray(T.transpose(perm))
+    delta = eps * np.linalg.norm(A) / np.sqrt(max(d - 1, 1))
+    ranks, M = [1], T.reshape(4, -1)
+    for k in range(d - 1):
+        U, S, Vt = np.linalg.svd(M, full_matrices=False)
+        tail = np.sqrt(np.cumsum((S ** 2)[::-1]))[::-1]
+        r = next(c for c in range(1, len(S) + 1) if (tail[c] if c < len(S) else 0.0) <= delta)
+        ranks.append(r)
+        M = (S[:r, None] * Vt[:r]).reshape(r * 4, -1)
+    return ranks + [1]
 
 
 # ------------------------------------------------ general mode sizes (Sec. 3.1)
