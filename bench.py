@@ -331,7 +331,97 @@ def oracle_baseline(op, target_s=8.0):
                       f"apply ({blk.flops():.3e} flops, {dt:.1f} s), all host threads"}
 
 
+def oracle_refine_sample(data, target_s=8.0):
+    """A bounded sample of the refinement workload for the oracle: the system
+    (I + K_s) x = f on the leading 2^s x 2^s block K_s of K (||K_s||_2 <=
+    ||K||_2 = 0.5), sized so that one refinement solve (about 35 FP64
+    applies at contraction 0.5 per step to 3e-11) takes about target_s."""
+    blk, s = oracle_sample(data, target_s / 35.0, min_d=10)
+    f = inputs.gaussian_rhs(blk.N, 1, 5)[0]
+    return blk, s, f
+
+
+def oracle_refine_solve(blk, f):
+    import oracle
+    return oracle.solve_refine(blk, None, f, a=1.0, tol=3e-11, max_iter=200)
+
+
+def oracle_serve_sample(spec):
+    """A bounded sample of the serving workload for the oracle: one request of
+    the smallest d of the trace (1 right-hand side), K_d and its P =
+    round(I - K + K^2, eps) built by the oracle's own product, sum and
+    rounding."""
+    import oracle
+    d = spec["d_range"][0]
+    K = inputs.scaled_operator(d, spec["rmax"], spec["seed_base"] + d)
+    S = oracle.tt_sum(oracle.tt_sum(inputs.identity(d), K.scaled(-1.0)),
+                      oracle.tt_product(K, K))
+    P = oracle.tt_round(S, spec["eps"])
+    f = inputs.gaussian_rhs(1 << d, 1, 5)[0]
+    return K, P, f, d
+
+
+def oracle_serve_solve(K, P, f, tol):
+    import oracle
+    return oracle.solve_gmres(K, P, f, a=1.0, tol=tol, restart=30, max_iter=300)
+
+
+def solve_baseline(kind, spec, data=None):
+    """cpu_baseline for the solve workloads, in solves/s."""
+    if kind == "refine":
+        blk, s, f = oracle_refine_sample(data)
+        t0 = time.perf_counter()
+        oracle_refine_solve(blk, f)
+        dt = time.perf_counter() - t0
+        sample = (f"refinement x <- x + (f - (I + K_s) x) to 3e-11 on the leading 2^{s} x 2^{s} "
+                  f"block of the d={data.d} operator, 1 RHS, FP64 oracle, all host threads")
+    else:
+        K, P, f, d = oracle_serve_sample(spec)
+        t0 = time.perf_counter()
+        oracle_serve_solve(K, P, f, spec["tol"])
+        dt = time.perf_counter() - t0
+        sample = (f"one request of d = {d} (1 RHS): right-preconditioned GMRES(30) to "
+                  f"{spec['tol']:g} with P = round(I - K + K^2, {spec['eps']:g}), FP64 oracle, "
+                  f"all host threads")
+    return {"value": 1.0 / dt, "unit": "solves/s", "cores": host_cores(), "kind": "oracle",
+            "sample": sample}
+
+
 # --------------------------------------------------------------- reference
+def run_reference_solve(args, spec):
+    """The oracle's solve on a bounded sample of the refine / serve workload,
+    each step one solve, in solves/s."""
+    if spec["kind"] == "refine":
+        data = inputs.scaled_operator(spec["d"], spec["rmax"], spec["seed"])
+        blk, s, f = oracle_refine_sample(data)
+        run = lambda: oracle_refine_solve(blk, f)
+        sample = (f"refinement to 3e-11 on the leading 2^{s} x 2^{s} block of the d={data.d} "
+                  f"operator, 1 RHS per step")
+    else:
+        K, P, f, d = oracle_serve_sample(spec)
+        run = lambda: oracle_serve_solve(K, P, f, spec["tol"])
+        sample = (f"one d = {d} request (1 RHS) per step, GMRES(30) to {spec['tol']:g} with the "
+                  f"oracle's P = round(I - K + K^2, {spec['eps']:g})")
+    for _ in range(args.warmup):
+        run()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run()
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {"metric": "served solves/s", "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": host_cores(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference_compressed(args, spec):
     """The oracle's compressed product (numpy) on the same operator and QTT
     vector as CompressedRun, whole problem per step."""
@@ -371,6 +461,8 @@ def run_reference(args, spec):
     import oracle
     if spec["kind"] == "compressed":
         return run_reference_compressed(args, spec)
+    if spec["kind"] in ("refine", "serve"):
+        return run_reference_solve(args, spec)
     if spec["kind"] == "batched":
         it = inputs.batched_workload(count=1, seed=spec["seed"])[0]
         op = inputs.synthetic_operator(it["d"], it["rmax"], it["op_seed"])
@@ -508,19 +600,23 @@ class ApplyRun:
     def roofline(self, mean_s):
         achieved = self.flops / mean_s / 1e9
         if self.compute == "bf16":
-            # BF16 steps run on the tensor cores and are bound by HBM: report
-            # the bytes the launches must move over the apply's time
-            peak = measured_peaks().get("hbm_gbs") or 6800.0
+            # BF16 contractions run on the tensor cores: the governing
+            # roofline is the BF16 tensor peak (flops 4 N nrhs sum r r' of
+            # the method, no padding counted); the HBM figure of the fused
+            # launches is kept beside it
+            pk = measured_peaks().get("bf16_tflops") or 1900.0
             fb, plan = self.fused_bytes()
             gbs = fb / mean_s / 1e9
-            return {"bound": "hbm",
+            hbm = measured_peaks().get("hbm_gbs") or 6800.0
+            return {"bound": "tensor",
                     "kernel": "whole apply: step_tc2_kernel (TMA + tcgen05 fused pairs), "
                               "step_mma2_kernel pairs, step_mma / step_lp single steps",
-                    "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                    "traffic": None, "achieved_tflops": achieved / 1e3,
+                    "achieved": achieved / 1e3, "peak": pk, "unit": "TFLOP/s",
+                    "frac": achieved / 1e3 / pk, "traffic": None,
+                    "peak_source": "measured BF16 burst (MEASURED_PEAKS.json bf16_tflops)",
+                    "hbm_achieved_gbs": gbs, "hbm_peak_gbs": hbm, "hbm_frac": gbs / hbm,
                     "bytes_per_apply": fb, "unfused_bytes_per_apply": self.algorithmic_bytes(),
-                    "launches_per_apply": len(plan),
-                    "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json)"}
+                    "launches_per_apply": len(plan)}
         if self.compute == "f64":
             peak, src = fp64_peak_gflops(), _peak_source("fp64")
         else:
@@ -718,7 +814,7 @@ class RefineRun:
                 "max_rel_residual": rel}
 
     def cpu_baseline(self):
-        return oracle_baseline(self.data)
+        return solve_baseline("refine", self.spec, self.data)
 
     def close(self):
         self.op.close()
@@ -977,6 +1073,8 @@ def run_serve(args, spec):
               for r in res_p)
     line["roofline"]["achieved"] = f64 / wall_p / 1e9
     line["roofline"]["frac"] = line["roofline"]["achieved"] / fp64_peak_gflops()
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = solve_baseline("serve", spec)
     for o in ops.values():
         for k in ("K", "P64", "Pbf"):
             o[k].close()
