@@ -437,25 +437,34 @@ qtt_status qtt_batch_info(const qtt_batch *B, int *waves, int *variant,
 qtt_status qtt_batch_destroy(qtt_batch *B);
 
 /* ---------------------------------------------------------- solve server */
-/* A solve server admits qtt_solve requests continuously (the paper has no
- * serving layer; each request is one of the solves above).  Requests wait in
- * a FIFO queue; the head is admitted as soon as one of `slots` workers is
- * free and its device-memory estimate fits in what is left of `mem_budget`
- * (0 = 80 % of free memory).  Every worker owns a CUDA stream, so admitted
- * requests run concurrently and their kernels overlap on the device; a
- * finishing request frees its slot and memory and the next ones are admitted
- * at once.  A request's arithmetic depends only on the request, so its
- * result is bitwise the same alone or in any mix.
- *   prm       : solve parameters shared by all requests (kind, a, tol,
+/* A server serves qtt_solve and qtt_apply requests of any d and nrhs by
+ * continuous batching (the paper has no serving layer; each request is one of
+ * the solves or applies above).  Requests wait in a FIFO queue; the head is
+ * admitted while fewer than `slots` requests are active and its device-memory
+ * estimate fits in what is left of `mem_budget` (0 = 80 % of free memory).
+ * One scheduler thread advances every active request by one step per tick:
+ * its preconditioner work on its own stream, then ONE grouped launch per core
+ * step for the forward applies of all active requests (launch L runs core
+ * step L of every request with d > L), then its Gram-Schmidt and norms; one
+ * synchronisation per tick, after which requests that finished leave and
+ * queued ones join.  A request's arithmetic is that of qtt_solve /
+ * qtt_apply on its own buffers, so its result is bitwise the same alone, in
+ * any mix, and through those calls.
+ *   prm       : solve parameters shared by all solve requests (kind, a, tol,
  *               restart, max_iter, precond_compute, inner_iters).
- * qtt_server_submit: f_host / x_host are HOST arrays of nrhs x N doubles
- *   (contiguous), owned by the caller and untouched until the request is
- *   retired by qtt_server_poll; QTT_ERR_OOM if the request alone exceeds the
- *   budget.  *request_id receives the request's id.
+ * qtt_server_submit: a solve of (a I + K) x = f.  f_host / x_host are HOST
+ *   arrays of nrhs x N doubles (contiguous), owned by the caller and
+ *   untouched until the request is retired by qtt_server_poll; QTT_ERR_OOM if
+ *   the request alone exceeds the budget.  *request_id receives its id.
+ * qtt_server_submit_apply: y = A x for nrhs host vectors (x_host, y_host as
+ *   above) with arithmetic `compute` (QTT_F64: grouped with the other
+ *   requests' forward applies; reduced precisions need A's QTT_PACK_* copy
+ *   and run on the request's stream); info reports iters = 1.
  * qtt_server_poll: done = 1 once finished (wait = 1 blocks until then); on
  *   completion fills info (nrhs entries) and the host timestamps (seconds,
  *   one steady clock) of submission, admission and completion, returns the
  *   request's status and retires the id.
+ * qtt_server_ticks: ticks run and grouped launches issued so far.
  * qtt_server_destroy: finishes all submitted requests, then stops. */
 typedef struct qtt_server qtt_server;
 qtt_status qtt_server_create(qtt_server **out, int slots, size_t mem_budget,
@@ -463,12 +472,16 @@ qtt_status qtt_server_create(qtt_server **out, int slots, size_t mem_budget,
 qtt_status qtt_server_submit(qtt_server *S, const qtt_op *K, const qtt_op *P,
                              const double *f_host, double *x_host,
                              int64_t nrhs, int64_t *request_id);
+qtt_status qtt_server_submit_apply(qtt_server *S, const qtt_op *A, const double *x_host,
+                                   double *y_host, int64_t nrhs, qtt_dtype compute,
+                                   int64_t *request_id);
 qtt_status qtt_server_poll(qtt_server *S, int64_t request_id, int wait,
                            int *done, qtt_solve_info *info, double *t_submit,
                            double *t_admit, double *t_finish);
 qtt_status qtt_server_stats(qtt_server *S, int *pending, int *running,
                             size_t *in_use, size_t *peak_in_use,
                             int *peak_running);
+qtt_status qtt_server_ticks(qtt_server *S, uint64_t *ticks, uint64_t *grouped_launches);
 qtt_status qtt_server_destroy(qtt_server *S);
 
 /* ------------------------------------------------------------ diagnostics */

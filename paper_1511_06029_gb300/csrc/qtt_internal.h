@@ -136,6 +136,21 @@ struct StepF64 {
 };
 cudaError_t launch_step_f64(const StepF64 &s, cudaStream_t stream);
 
+// Grouped FP64 steps (the serving loop): one launch runs one step each of
+// several operators.  A descriptor holds the step, whether it takes the
+// split-sum form (f64_step_small, the same choice launch_step_f64 makes),
+// its first CTA and its CTAs per right-hand side; descriptors are ordered by
+// cta0 and the table lives in device memory.
+struct GroupedStepF64 {
+  StepF64 s;
+  int small;
+  int64_t cta0, ctas_per_rhs;
+};
+bool f64_step_small(int64_t N, int rout);
+int64_t f64_step_ctas_per_rhs(const StepF64 &s, bool small);
+cudaError_t launch_step_f64_grouped(const GroupedStepF64 *dev_table, int n, int64_t total_ctas,
+                                    cudaStream_t stream);
+
 // Epilogue request for a whole apply (applies to its last step).
 struct Epilogue {
   bool on = false;

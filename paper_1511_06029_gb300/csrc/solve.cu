@@ -24,6 +24,7 @@
 
 #include "krylov.h"
 #include "qtt_internal.h"
+#include "solve_internal.h"
 
 namespace qtt {
 namespace {
@@ -271,42 +272,12 @@ qtt_status gmres(const Ctx &c, const double *f, double *x, int64_t ld, const qtt
       QTT_CUDA_OK(cudaStreamSynchronize(c.st), "sync");
       ++iters;
       jl = j + 1;
-      bool done = true;
-      for (int64_t r = 0; r < nr; ++r) {
-        double *Hr = H.data() + (size_t)r * (m + 1) * m;
-        double *csr = cs.data() + (size_t)r * m, *snr = sn.data() + (size_t)r * m;
-        double *gr = g.data() + (size_t)r * (m + 1);
-        for (int i = 0; i <= j; ++i) Hr[i * m + j] = hv1[(size_t)i * nr + r] + hv2[(size_t)i * nr + r];
-        Hr[(j + 1) * m + j] = std::sqrt(hs[r]);
-        for (int i = 0; i < j; ++i) {
-          const double a0 = Hr[i * m + j], a1 = Hr[(i + 1) * m + j];
-          Hr[i * m + j] = csr[i] * a0 + snr[i] * a1;
-          Hr[(i + 1) * m + j] = -snr[i] * a0 + csr[i] * a1;
-        }
-        const double a0 = Hr[j * m + j], a1 = Hr[(j + 1) * m + j];
-        const double den = std::sqrt(a0 * a0 + a1 * a1);
-        csr[j] = den == 0.0 ? 1.0 : a0 / den;
-        snr[j] = den == 0.0 ? 0.0 : a1 / den;
-        Hr[j * m + j] = den;
-        Hr[(j + 1) * m + j] = 0.0;
-        gr[j + 1] = -snr[j] * gr[j];
-        gr[j] = csr[j] * gr[j];
-        if (fn[r] > 0.0 && std::fabs(gr[j + 1]) / fn[r] > prm.tol && hs[r] > 0.0) done = false;
-      }
+      const bool done = gmres_host_step(nr, m, j, hv1.data(), hv2.data(), hs.data(), fn, prm.tol,
+                                        H, cs, sn, g);
       if (done) break;
     }
     // y = H^{-1} g per RHS, x += P (V y)
-    for (int64_t r = 0; r < nr; ++r) {
-      const double *Hr = H.data() + (size_t)r * (m + 1) * m;
-      const double *gr = g.data() + (size_t)r * (m + 1);
-      double yy[1024];
-      for (int i = jl - 1; i >= 0; --i) {
-        double s = gr[i];
-        for (int l = i + 1; l < jl; ++l) s -= Hr[i * m + l] * yy[l];
-        yy[i] = Hr[i * m + i] != 0.0 ? s / Hr[i * m + i] : 0.0;
-      }
-      for (int i = 0; i < jl; ++i) y[(size_t)i * nr + r] = yy[i];
-    }
+    gmres_back_solve(nr, m, jl, H, g, y.data());
     QTT_CUDA_OK(cudaMemcpyAsync(ydev, y.data(), sizeof(double) * jl * nr, cudaMemcpyHostToDevice,
                                 c.st), "memcpy");
     // x += Z y (Z = V without a preconditioner)
@@ -494,3 +465,60 @@ extern "C" qtt_status qtt_solve(const qtt_op *K, const qtt_op *P, const double *
                         std::to_string(info[k].iters) + " iterations");
   return QTT_OK;
 }
+
+namespace qtt {
+
+qtt_status solve_apply_M(const SolveCtx &c, int inner, const double *rhs, double *z, double *tmp,
+                         double *tmp2) {
+  return apply_M(Ctx{c.K, c.P, c.a, c.pc, c.N, c.nrhs, c.st}, inner, rhs, z, tmp, tmp2);
+}
+
+qtt_status solve_apply_P(const SolveCtx &c, const double *in, double *out, bool accumulate) {
+  return apply_P(Ctx{c.K, c.P, c.a, c.pc, c.N, c.nrhs, c.st}, in, c.N, out, c.N, accumulate);
+}
+
+bool gmres_host_step(int64_t nr, int m, int j, const double *hv1, const double *hv2,
+                     const double *hs, const std::vector<double> &fn, double tol,
+                     std::vector<double> &H, std::vector<double> &cs, std::vector<double> &sn,
+                     std::vector<double> &g) {
+  bool done = true;
+  for (int64_t r = 0; r < nr; ++r) {
+    double *Hr = H.data() + (size_t)r * (m + 1) * m;
+    double *csr = cs.data() + (size_t)r * m, *snr = sn.data() + (size_t)r * m;
+    double *gr = g.data() + (size_t)r * (m + 1);
+    for (int i = 0; i <= j; ++i) Hr[i * m + j] = hv1[(size_t)i * nr + r] + hv2[(size_t)i * nr + r];
+    Hr[(j + 1) * m + j] = std::sqrt(hs[r]);
+    for (int i = 0; i < j; ++i) {
+      const double a0 = Hr[i * m + j], a1 = Hr[(i + 1) * m + j];
+      Hr[i * m + j] = csr[i] * a0 + snr[i] * a1;
+      Hr[(i + 1) * m + j] = -snr[i] * a0 + csr[i] * a1;
+    }
+    const double a0 = Hr[j * m + j], a1 = Hr[(j + 1) * m + j];
+    const double den = std::sqrt(a0 * a0 + a1 * a1);
+    csr[j] = den == 0.0 ? 1.0 : a0 / den;
+    snr[j] = den == 0.0 ? 0.0 : a1 / den;
+    Hr[j * m + j] = den;
+    Hr[(j + 1) * m + j] = 0.0;
+    gr[j + 1] = -snr[j] * gr[j];
+    gr[j] = csr[j] * gr[j];
+    if (fn[r] > 0.0 && std::fabs(gr[j + 1]) / fn[r] > tol && hs[r] > 0.0) done = false;
+  }
+  return done;
+}
+
+void gmres_back_solve(int64_t nr, int m, int jl, const std::vector<double> &H,
+                      const std::vector<double> &g, double *y) {
+  for (int64_t r = 0; r < nr; ++r) {
+    const double *Hr = H.data() + (size_t)r * (m + 1) * m;
+    const double *gr = g.data() + (size_t)r * (m + 1);
+    double yy[1024];
+    for (int i = jl - 1; i >= 0; --i) {
+      double s = gr[i];
+      for (int l = i + 1; l < jl; ++l) s -= Hr[i * m + l] * yy[l];
+      yy[i] = Hr[i * m + i] != 0.0 ? s / Hr[i * m + i] : 0.0;
+    }
+    for (int i = 0; i < jl; ++i) y[(size_t)i * nr + r] = yy[i];
+  }
+}
+
+}  // namespace qtt

@@ -23,19 +23,22 @@ namespace {
 constexpr int kTN = 4;       // position pairs per thread
 constexpr int kWarpsY = 8;   // output ranks per CTA (one per warp)
 
+// The body of one CTA of the step: `cta` = pair tile * rank blocks + rank
+// block, `by` ranks per block, thread (ty, tx) = (rank in the block, lane),
+// right-hand side c.  Shared by the single-operator kernel and the grouped
+// kernel of the serving loop, so a step's arithmetic is the same in both.
 template <int TN>
-__global__ void __launch_bounds__(32 * kWarpsY)
-step_f64_kernel(StepF64 s) {
-  // blockIdx.x = pair tile * rank blocks + rank block: the CTAs that share a
-  // pair tile (and so its input) run back to back and meet it in L2
-  const int nrb = (s.rout + blockDim.y - 1) / blockDim.y;
-  const int b = (int)(blockIdx.x % nrb) * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void step_f64_tn_body(const StepF64 &s, int64_t cta, int by,
+                                                 int64_t c, int ty, int tx) {
+  // CTAs that share a pair tile (and so its input) run back to back and
+  // meet it in L2
+  const int nrb = (s.rout + by - 1) / by;
+  const int b = (int)(cta % nrb) * by + ty;
   if (b >= s.rout) return;
-  const int64_t c = blockIdx.z;
   const int64_t npairs = s.N >> 1;
   const int64_t bit = (int64_t)1 << s.k;
   const int64_t low = bit - 1;
-  const int64_t q0 = (int64_t)(blockIdx.x / nrb) * (32 * TN) + threadIdx.x;
+  const int64_t q0 = (cta / nrb) * (32 * TN) + tx;
 
   int64_t p0[TN];
   bool ok[TN];
@@ -92,25 +95,31 @@ step_f64_kernel(StepF64 s) {
   }
 }
 
+template <int TN>
+__global__ void __launch_bounds__(32 * kWarpsY)
+step_f64_kernel(StepF64 s) {
+  step_f64_tn_body<TN>(s, blockIdx.x, blockDim.y, blockIdx.z, threadIdx.y, threadIdx.x);
+}
+
 // Small steps (few pair tiles, e.g. the 8^3 volume operator with N = 512):
 // the same contraction with the sum over (a, j) split among KS warps, so a
 // CTA of 8 warps covers 8 / KS output ranks of 32 pairs and the grid has
 // KS times more CTAs with KS times shorter FMA chains.  The KS partial sums
 // meet in shared memory and are added in a fixed order (deterministic).
+// One CTA of the split-sum form (every thread of the CTA calls it: it holds
+// a CTA-wide barrier); part is the CTA's shared scratch.
 template <int KS>
-__global__ void __launch_bounds__(32 * kWarpsY)
-step_f64_small_kernel(StepF64 s) {
+__device__ __forceinline__ void step_f64_small_body(const StepF64 &s, int64_t cta, int64_t c,
+                                                    int warp, int lane,
+                                                    double (*part)[2][32]) {
   constexpr int RPC = kWarpsY / KS;  // output ranks per CTA
-  __shared__ double part[kWarpsY][2][32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nrg = (s.rout + RPC - 1) / RPC;
-  const int b = (int)(blockIdx.x % nrg) * RPC + warp / KS;
+  const int b = (int)(cta % nrg) * RPC + warp / KS;
   const int split = warp % KS;
-  const int64_t c = blockIdx.z;
   const int64_t npairs = s.N >> 1;
   const int64_t bit = (int64_t)1 << s.k;
   const int64_t low = bit - 1;
-  const int64_t q = (int64_t)(blockIdx.x / nrg) * 32 + lane;
+  const int64_t q = (cta / nrg) * 32 + lane;
   const bool ok = q < npairs && b < s.rout;
   const int64_t p0 = ((q & ~low) << 1) | (q & low);
   double acc0 = 0.0, acc1 = 0.0;
@@ -155,6 +164,38 @@ step_f64_small_kernel(StepF64 s) {
     out[p0] = acc0;
     out[p0 + bit] = acc1;
   }
+}
+
+template <int KS>
+__global__ void __launch_bounds__(32 * kWarpsY)
+step_f64_small_kernel(StepF64 s) {
+  __shared__ double part[kWarpsY][2][32];
+  step_f64_small_body<KS>(s, blockIdx.x, blockIdx.z, threadIdx.x >> 5, threadIdx.x & 31, part);
+}
+
+// Grouped steps: one launch runs, for each descriptor, one step of one
+// operator (its own sizes, buffers and epilogue).  CTA blockIdx.x belongs to
+// the descriptor whose range [cta0, cta0 + ctas) holds it; inside that range
+// it is CTA (cta, c) of the single-operator launch, with the same body and
+// the same form (split-sum or pairs-per-lane) that launch would take.
+__global__ void __launch_bounds__(32 * kWarpsY)
+step_f64_grouped_kernel(const GroupedStepF64 *g, int n) {
+  __shared__ double part[kWarpsY][2][32];
+  int lo = 0, hi = n - 1;
+  const int64_t bx = blockIdx.x;
+  while (lo < hi) {  // last descriptor with cta0 <= bx
+    const int mid = (lo + hi + 1) >> 1;
+    if (g[mid].cta0 <= bx) lo = mid;
+    else hi = mid - 1;
+  }
+  const GroupedStepF64 &d = g[lo];
+  const int64_t local = bx - d.cta0;
+  const int64_t c = local / d.ctas_per_rhs, cta = local - c * d.ctas_per_rhs;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (d.small)
+    step_f64_small_body<4>(d.s, cta, c, warp, lane, part);
+  else
+    step_f64_tn_body<kTN>(d.s, cta, kWarpsY, c, warp, lane);
 }
 
 }  // namespace
@@ -206,23 +247,42 @@ cudaError_t launch_tn(const StepF64 &s, cudaStream_t stream) {
 
 }  // namespace
 
-cudaError_t launch_step_f64(const StepF64 &s, cudaStream_t stream) {
-  // Small steps (the 8^3 volume operator has N = 512) would give a few CTAs
-  // with 4 pairs per lane and leave most SMs idle: the split-sum kernel then
-  // gives 16x the CTAs (one pair per lane, the (a, j) sum over 4 warps).
+// Small steps (the 8^3 volume operator has N = 512) would give a few CTAs
+// with 4 pairs per lane and leave most SMs idle: the split-sum kernel then
+// gives 16x the CTAs (one pair per lane, the (a, j) sum over 4 warps).  The
+// choice depends on one right-hand side's work only (not on nrhs): the two
+// forms sum in different orders, and a right-hand side must get the same
+// bits whatever else shares its launch (chunked applies, batched solves, the
+// server's grouped steps).
+bool f64_step_small(int64_t N, int rout) {
   static const int sms = [] {
     int dev = 0, n = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     return n;
   }();
-  // The choice depends on one right-hand side's work only (not on nrhs): the
-  // two kernels sum in different orders, and a right-hand side must get the
-  // same bits whatever else shares its launch (chunked applies, batched
-  // solves, the server's requests).
-  const int64_t ctas_per_rhs = ((s.N >> 1) + 127) / 128 * ((s.rout + kWarpsY - 1) / kWarpsY);
-  if (ctas_per_rhs < 2 * sms) return launch_small(s, stream);
+  const int64_t ctas_per_rhs = ((N >> 1) + 127) / 128 * ((rout + kWarpsY - 1) / kWarpsY);
+  return ctas_per_rhs < 2 * sms;
+}
+
+cudaError_t launch_step_f64(const StepF64 &s, cudaStream_t stream) {
+  if (f64_step_small(s.N, s.rout)) return launch_small(s, stream);
   return launch_tn<kTN>(s, stream);
+}
+
+int64_t f64_step_ctas_per_rhs(const StepF64 &s, bool small) {
+  const int64_t npairs = s.N >> 1;
+  if (small) return (npairs + 31) / 32 * ((s.rout + 1) / 2);
+  return (npairs + 32 * kTN - 1) / (32 * kTN) * ((s.rout + kWarpsY - 1) / kWarpsY);
+}
+
+cudaError_t launch_step_f64_grouped(const GroupedStepF64 *dev_table, int n, int64_t total_ctas,
+                                    cudaStream_t stream) {
+  if (n <= 0 || total_ctas <= 0) return cudaSuccess;
+  if (total_ctas > 0x7fffffffLL) return cudaErrorInvalidValue;
+  step_f64_grouped_kernel<<<(unsigned)total_ctas, 32 * kWarpsY, 0, stream>>>(dev_table, n);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 }  // namespace qtt

@@ -83,6 +83,8 @@ SIGNATURES = {
                               ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
                               ctypes.POINTER(_I)]),
     "qtt_server_destroy": (_I, [_P]),
+    "qtt_server_submit_apply": (_I, [_P, _P, _P, _P, _L, _I, ctypes.POINTER(_L)]),
+    "qtt_server_ticks": (_I, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 
@@ -617,9 +619,10 @@ class Batch:
 
 
 class Server:
-    """Continuous-admission solve server (qtt_server_*).  submit() takes host
-    numpy arrays (nrhs, N) float64; the result lands in the returned x array
-    when poll()/wait() reports the request done."""
+    """Continuous-batching solve and apply server (qtt_server_*).  submit()
+    and submit_apply() take host numpy arrays (nrhs, N) float64; the result
+    lands in the returned array when poll()/wait() reports the request
+    done."""
 
     def __init__(self, slots=4, mem_budget=0, kind="gmres", a=1.0, tol=1e-10, restart=30,
                  max_iter=300, precond_compute="bf16", inner_iters=0):
@@ -643,6 +646,24 @@ class Server:
             "qtt_server_submit")
         self._live[rid.value] = (f, x)
         return rid.value
+
+    def submit_apply(self, A, x, compute="f64"):
+        """y = A x as a served request (host arrays (nrhs, N) float64)."""
+        x = np.ascontiguousarray(np.atleast_2d(np.asarray(x, dtype=np.float64)))
+        y = np.empty_like(x)
+        rid = ctypes.c_int64()
+        _check(load_library().qtt_server_submit_apply(
+            self._h, A.handle, x.ctypes.data_as(_P), y.ctypes.data_as(_P), x.shape[0],
+            DTYPES[compute], ctypes.byref(rid)), "qtt_server_submit_apply")
+        self._live[rid.value] = (x, y)
+        return rid.value
+
+    def ticks(self):
+        """(ticks run, grouped launches issued) so far (qtt_server_ticks)."""
+        t, g = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load_library().qtt_server_ticks(self._h, ctypes.byref(t), ctypes.byref(g)),
+               "qtt_server_ticks")
+        return t.value, g.value
 
     def poll(self, rid, wait=False):
         """None while running; else (x, info, (t_submit, t_admit, t_finish))."""

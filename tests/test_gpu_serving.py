@@ -108,3 +108,70 @@ def test_poll_before_done_and_unknown_id(qtt, operators):
         qtt._check(qtt.load_library().qtt_server_poll(S._h, rid, 0, ctypes.byref(done), None,
                                                       None, None, None), "poll")
     S.close()
+
+
+def test_served_solves_are_bitwise_qtt_solve(qtt, operators):
+    """The tick scheduler runs qtt_solve's arithmetic: a GMRES request with a
+    BF16 preconditioner and one inner step, and a refinement request, give
+    bitwise the x that qtt_solve gives for the same inputs."""
+    import torch
+    for kind, pc, inner in (("gmres", "bf16", 1), ("refine", "f64", 0)):
+        for d in (9, 10):
+            K, P, Kg, Pg = operators[d]
+            f = inputs.gaussian_rhs(1 << d, 2, 40 + d)
+            S = qtt.Server(slots=2, kind=kind, tol=GPU_TOL, precond_compute=pc,
+                           inner_iters=inner)
+            Kp = qtt.Operator(K, packs=("bf16",)) if inner else Kg
+            x, info, _ = S.wait(S.submit(Kp, Pg, f))
+            S.close()
+            xs, infos = qtt.solve(Kp, Pg, torch.from_numpy(f).cuda(), kind=kind, tol=GPU_TOL,
+                                  precond_compute=pc, inner_iters=inner)
+            assert np.array_equal(x, xs.cpu().numpy()), (kind, d)
+            assert [i[0] for i in info] == [i[0] for i in infos]
+            if inner:
+                Kp.close()
+
+
+def test_apply_requests_share_grouped_launches(qtt, operators):
+    """Six FP64 apply requests of d = 8, 9, 10 submitted together: each is
+    bitwise qtt_apply's, and their 54 core steps ran in far fewer grouped
+    launches (one launch per core step index, shared by every request that
+    has that step).  Then applies, a BF16 apply and solves in one mix: the
+    FP64 applies bitwise, the BF16 apply within the BF16 bound of the
+    oracle, the solves converged."""
+    import torch
+    S = qtt.Server(slots=8, kind="gmres", tol=GPU_TOL, precond_compute="bf16")
+    ds = (8, 9, 10, 10, 9, 8)
+    xs = [inputs.gaussian_rhs(1 << d, 1 + i % 3, 300 + i) for i, d in enumerate(ds)]
+    ids = [S.submit_apply(operators[d][2], x) for d, x in zip(ds, xs)]
+    ys = [S.wait(i)[0] for i in ids]
+    ticks, grouped = S.ticks()
+    S.close()
+    for d, x, y in zip(ds, xs, ys):
+        assert np.array_equal(y, operators[d][2].apply(torch.from_numpy(x).cuda()).cpu().numpy())
+    assert grouped < sum(ds) and ticks <= len(ds)
+
+    S = qtt.Server(slots=8, kind="gmres", tol=GPU_TOL, precond_compute="bf16")
+    jobs = []
+    for i, d in enumerate(ds):
+        jobs.append(("apply", d, xs[i], S.submit_apply(operators[d][2], xs[i])))
+    for d in (9, 10):
+        f = inputs.gaussian_rhs(1 << d, 2, 400 + d)
+        jobs.append(("solve", d, f, S.submit(operators[d][2], operators[d][3], f)))
+    xb = inputs.gaussian_rhs(1 << 10, 2, 500)
+    Kb = qtt.Operator(operators[10][0], packs=("bf16",))
+    jobs.append(("apply_bf16", 10, xb, S.submit_apply(Kb, xb, compute="bf16")))
+    out = [(kind, d, x, S.wait(rid)) for kind, d, x, rid in jobs]
+    S.close()
+    for kind, d, x, (y, info, _) in out:
+        K, P, Kg, Pg = operators[d]
+        if kind == "apply":
+            ref = Kg.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+            assert np.array_equal(y, ref)
+        elif kind == "apply_bf16":
+            assert rel_l2(y, oracle.apply(K, x)) <= 3 * np.sqrt(d) * 2.0 ** -8
+        else:
+            assert all(s == qtt.QTT_OK and r <= GPU_TOL for _, r, s in info)
+            xo, _, _ = oracle.solve_gmres(K, P, x, a=1.0, tol=1e-13, restart=30)
+            assert rel_l2(y, xo) <= 1e-10
+    Kb.close()
