@@ -505,6 +505,12 @@ class ApplyRun:
         tdt = getattr(torch, IO[self.compute])
         packs = () if self.compute == "f64" else (self.compute,)
         self.op = qtt.Operator(self.data, packs=packs, stream=stream)
+        # the fusion plan for this operator, arithmetic and nrhs, chosen by the
+        # library's tuner before the timed region (FP64 has a single plan)
+        self.plan, self.tuned_s = None, None
+        if self.compute != "f64":
+            self.plan, self.tuned_s = self.op.autotune(self.nrhs, self.compute, reps=2,
+                                                       stream=stream)
         self.x_host = inputs.gaussian_rhs(self.data.N, self.nrhs, spec["rhs_seed"] + 1000 * rank)
         self.x = torch.from_numpy(self.x_host).to("cuda").to(tdt)
         self.y = torch.empty_like(self.x)
@@ -644,6 +650,7 @@ class ApplyRun:
         return {"workload": self.spec["name"], "d": d.d, "N": d.N, "rmax": max(d.ranks),
                 "nrhs_per_gpu": self.nrhs, "sum_r_r": d.sigma,
                 "flops_per_step_per_gpu": self.flops, "compute": self.compute,
+                "autotuned_plan": self.plan, "autotuned_s_per_apply": self.tuned_s,
                 "l2": f"not flushed: each step streams 2 x {inter / 1e9:.2f} GB of "
                       f"intermediates through the 129 MB L2" if inter > 129e6 else
                       "inputs smaller than L2 (latency-bound case)"}

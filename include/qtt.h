@@ -125,6 +125,36 @@ qtt_status qtt_apply(const qtt_op *A, const void *x, void *y, int64_t nrhs,
                      int64_t ld, qtt_dtype io_dtype, qtt_dtype compute,
                      void *stream);
 
+/* ------------------------------------------------------------ fusion plan */
+/* How an apply in each arithmetic runs -- which steps are merged into one
+ * launch and on which kernels -- is a per-operator plan; the paper has no
+ * counterpart (its Algorithm 2 runs one step at a time).  Plan codes:
+ * fusion + 2 pairs + 8 groups2 + 16 staged, where
+ *   fusion  (1): merge steps -- the first and last 2-3 low-rank steps in one
+ *                launch each, middle steps in fused pairs (merge depth 2);
+ *                0: one launch per step;
+ *   pairs   (0-2): fused-pair family for BF16: 2 tcgen05 (TMA + TMEM),
+ *                1 mma.sync, 0 no pairs;
+ *   groups2 (1): tcgen05 pairs with two epilogue groups (else as many as
+ *                fit beside three input stages);
+ *   staged  (1): FP32/TF32 single steps on the shared-memory staged kernel.
+ * The untuned plan is 1 + 4 + 16 = 21.
+ * qtt_apply_autotune: times every candidate plan for `compute` on this
+ *   operator with nrhs right-hand sides (one warm-up, then `reps` applies
+ *   each, on `stream`; the arithmetic does not depend on the values, so the
+ *   vectors are zeros from the library's scratch) and keeps the fastest for
+ *   later qtt_apply calls in that arithmetic; *plan and *seconds (per apply)
+ *   receive the choice.  Synchronises `stream`.
+ * qtt_apply_set_plan / qtt_apply_get_plan: set or read the plan of one
+ *   arithmetic (e.g. a choice cached from an earlier process).
+ * Every plan computes the same product; plans differ in rounding only where
+ * the arithmetic itself differs (the fused BF16 pairs keep the unfused
+ * rounding points).  Errors: QTT_ERR_INVALID_ARG, QTT_ERR_OOM, QTT_ERR_CUDA. */
+qtt_status qtt_apply_autotune(qtt_op *A, int64_t nrhs, qtt_dtype compute, int reps, void *stream,
+                              int *plan, double *seconds);
+qtt_status qtt_apply_set_plan(qtt_op *A, qtt_dtype compute, int plan);
+qtt_status qtt_apply_get_plan(const qtt_op *A, qtt_dtype compute, int *plan);
+
 /* qtt_apply_noalloc -- y = A x in FP64 without allocating any memory.  The
  * paper has no counterpart: this exists for callers that cannot allocate
  * device memory at the time they apply an operator -- for instance a process

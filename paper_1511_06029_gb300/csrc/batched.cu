@@ -470,16 +470,31 @@ qtt_status build_plan(qtt_batch *B, cudaStream_t st) {
   free_waves(B);
   const int TN = B->variant;
   const int PC = 32 * TN;
-  // greedy waves in input order under the memory budget
+  // Waves hold operators of one rank class (largest rank <= 16, <= 24,
+  // <= 32, <= 48), so that each wave's kernel is sized -- shared memory,
+  // hence CTAs per SM -- for its own class; within a class, greedy waves in
+  // input order under the memory budget.
+  auto rank_class = [](const qtt_op *A) {
+    int r = 1;
+    for (int k = 0; k <= A->d; ++k) r = std::max(r, A->ranks[k]);
+    return r <= 16 ? 0 : r <= 24 ? 1 : r <= 32 ? 2 : 3;
+  };
+  std::vector<int> order(B->ops.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return rank_class(B->ops[a]) < rank_class(B->ops[b]);
+  });
   std::vector<std::vector<int>> groups;
   size_t cur = 0, maxw = 0;
-  for (int i = 0; i < (int)B->ops.size(); ++i) {
+  int cls = -1;
+  for (int i : order) {
     const size_t need = op_scratch_bytes(B->ops[i], B->nrhs[i]);
     if (need > B->budget)
       return fail(QTT_ERR_OOM, "batch: one operator's scratch exceeds the memory budget");
-    if (groups.empty() || cur + need > B->budget) {
+    if (groups.empty() || cur + need > B->budget || rank_class(B->ops[i]) != cls) {
       groups.emplace_back();
       cur = 0;
+      cls = rank_class(B->ops[i]);
     }
     groups.back().push_back(i);
     cur += need;
@@ -499,12 +514,12 @@ qtt_status build_plan(qtt_batch *B, cudaStream_t st) {
   if (qtt_status as = persistent_alloc(reinterpret_cast<void **>(&B->d_next),
                                        sizeof(unsigned long long) * std::max<size_t>(1, groups.size()), st))
     return as;
-  // every wave's kernel is sized for the largest rank of the batch
-  int max_rank_all = 1;
-  for (const qtt_op *A : B->ops)
-    for (int k = 0; k <= A->d; ++k) max_rank_all = std::max(max_rank_all, A->ranks[k]);
-  const int max_k_wave = 2 * max_rank_all;
   for (auto &g : groups) {
+    // the wave's kernel is sized for the largest rank of its own operators
+    int max_rank_wave = 1;
+    for (int i : g)
+      for (int k = 0; k <= B->ops[i]->d; ++k) max_rank_wave = std::max(max_rank_wave, B->ops[i]->ranks[k]);
+    const int max_k_wave = 2 * max_rank_wave;
     WaveDev wv;
     wv.ops = g;
     std::vector<BOp> hops;
@@ -588,26 +603,38 @@ qtt_status build_plan(qtt_batch *B, cudaStream_t st) {
 
 template <int TN, int NS>
 qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
-  int max_rin = 1;
-  for (auto &w : B->waves) max_rin = std::max(max_rin, w.max_rin);
   const int PC = 32 * TN;
-  const int max_k = 2 * max_rin;
-  const int rpad_max = (max_rin + 3) / 4 * 4;
-  const int core_floats = (max_k * 2 * rpad_max + 15) / 16 * 16;
-  const size_t smem = sizeof(float) * ((size_t)core_floats + (size_t)NS * max_k * PC);
   // raised once to the largest footprint (rank kMaxRank), shared by all threads
   static cudaError_t attr = cudaFuncSetAttribute(
       batch_kernel<TN, 6, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
       (int)(sizeof(float) * ((size_t)(2 * kMaxRank * 2 * kMaxRank) +
                              (size_t)NS * (2 * kMaxRank) * PC)));
   QTT_CUDA_TRY(attr);
-  int per_sm = 0, dev = 0, sms = 0;
-  QTT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<TN, 6, NS>, kThreads, smem));
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int clk_khz = 2000000;
   cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
-  B->grid = std::max(1, per_sm) * sms;
+  // each wave sized for its own largest rank: shared memory and so the CTAs
+  // resident per SM
+  auto sizing = [&](const WaveDev &w, int *max_k, int *core_floats, size_t *smem, int *grid) {
+    *max_k = 2 * w.max_rin;
+    const int rpad_max = (w.max_rin + 3) / 4 * 4;
+    *core_floats = (*max_k * 2 * rpad_max + 15) / 16 * 16;
+    *smem = sizeof(float) * ((size_t)*core_floats + (size_t)NS * *max_k * PC);
+    int per_sm = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, batch_kernel<TN, 6, NS>, kThreads, *smem);
+    *grid = std::max(1, per_sm) * sms;
+    return e;
+  };
+  B->grid = 0;
+  for (const auto &w : B->waves) {
+    int mk, cf, g;
+    size_t sm;
+    QTT_CUDA_TRY(sizing(w, &mk, &cf, &sm, &g));
+    B->grid = std::max(B->grid, g);
+  }
   const bool selftest = B->selftest_start >= 0;
   for (size_t wi = 0; wi < (selftest ? (size_t)1 : B->waves.size()); ++wi) {
     auto &w = B->waves[wi];
@@ -631,9 +658,12 @@ qtt_status launch_waves_t(qtt_batch *B, cudaStream_t st) {
     bw.status = B->d_status;
     bw.tf32 = B->compute == QTT_TF32;
     bw.wait_budget = selftest ? B->selftest_budget : (long long)clk_khz * 1000LL * 4;  // ~4 s
+    int max_k, core_floats, grid;
+    size_t smem;
+    QTT_CUDA_TRY(sizing(w, &max_k, &core_floats, &smem, &grid));
     bw.max_k = max_k;
     bw.core_floats = core_floats;
-    batch_kernel<TN, 6, NS><<<B->grid, kThreads, smem, st>>>(bw);
+    batch_kernel<TN, 6, NS><<<grid, kThreads, smem, st>>>(bw);
     count_launches(1);
     QTT_CUDA_TRY(cudaGetLastError());
   }

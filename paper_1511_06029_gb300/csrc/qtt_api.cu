@@ -396,6 +396,8 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
     buf[1] = buf[0] + (size_t)A->rmax_inner * (size_t)N * (size_t)chunk * esz;
   }
   const size_t xsz = dtype_size(xt), ysz = dtype_size(yt);
+  const ApplyPlan &pl = A->plan[compute];
+  const bool fuse = use_fusion() && pl.fusion;
   const bool tc = compute == QTT_BF16 && use_tensor_cores() && A->mma_bf16;
   for (int64_t c0 = 0; c0 < nrhs; c0 += chunk) {
     const int64_t nc = std::min<int64_t>(chunk, nrhs - c0);
@@ -403,8 +405,8 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
     int k0 = 0;
     const int mi = mode == LP_F32 ? 0 : mode == LP_TF32 ? 1 : 2;
     const std::vector<float> &hcores = A->head[mi];
-    const int hm = use_fusion() && !hcores.empty() ? head_steps(A->ranks.data(), d) : 0;
-    const int tm = use_fusion() && !A->tail[mi].empty() ? tail_steps(A->ranks.data(), d, hm) : 0;
+    const int hm = fuse && !hcores.empty() ? head_steps(A->ranks.data(), d) : 0;
+    const int tm = fuse && !A->tail[mi].empty() ? tail_steps(A->ranks.data(), d, hm) : 0;
     const int kend = d - tm;  // steps k0 .. kend-1 here, kend .. d-1 in the tail kernel
     if (hm) {
       // steps 0 .. hm-1 in one launch; y_hm lands in scratch half 0
@@ -429,9 +431,9 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
       k0 = hm;
     }
     for (int k = k0; k < kend; ++k) {
-      const bool pair =
-          tc && use_fusion() && k + 2 < d && k + 1 < kend && A->mp[k] && A->mp[k + 1];
-      const bool tc5 = pair && use_tcgen05() &&
+      const bool pair = tc && fuse && pl.pairs > 0 && k + 2 < d && k + 1 < kend && A->mp[k] &&
+                        A->mp[k + 1];
+      const bool tc5 = pair && use_tcgen05() && pl.pairs == 2 &&
                        tc2_steps_eligible(k, A->ranks[k], A->ranks[k + 1], A->ranks[k + 2], N);
       const bool mma2 =
           pair && mma2_steps_eligible(k, A->ranks[k], A->ranks[k + 1], A->ranks[k + 2], N);
@@ -453,6 +455,7 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
         m.Mp2 = A->mp[k + 1];
         m.N = N;
         m.nrhs = nc;
+        m.groups_cap = pl.groups_cap;
         cudaError_t e = cudaErrorNotSupported;
         if (tc5) e = launch_step_tc2_bf16(m, st);
         if (e == cudaErrorNotSupported && mma2) e = launch_step_mma2_bf16(m, st);
@@ -525,7 +528,7 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
         m.N = N;
         m.nrhs = nc;
         e = launch_step_mma_bf16(m, st);
-      } else if (use_staged_f32() && f32s_step_eligible(p)) {
+      } else if (use_staged_f32() && pl.staged && f32s_step_eligible(p)) {
         e = launch_step_f32s(p, st);
       } else {
         e = launch_step_lp(p, st);
@@ -925,6 +928,101 @@ qtt_status qtt_residual(const qtt_op *K, double a, const double *f, const double
   e.s_u = -a;
   e.s_acc = -1.0;
   return apply_f64(K, x, r, nrhs, ld, static_cast<cudaStream_t>(stream), e);
+}
+
+qtt_status qtt_apply_set_plan(qtt_op *A, qtt_dtype compute, int plan) {
+  if (!A || !valid_dtype(compute)) return fail(QTT_ERR_INVALID_ARG, "qtt_apply_set_plan: bad operator or compute");
+  ApplyPlan p;
+  if (!decode_plan(plan, &p)) return fail(QTT_ERR_INVALID_ARG, "qtt_apply_set_plan: unknown plan code");
+  A->plan[compute] = p;
+  return QTT_OK;
+}
+
+qtt_status qtt_apply_get_plan(const qtt_op *A, qtt_dtype compute, int *plan) {
+  if (!A || !plan || !valid_dtype(compute))
+    return fail(QTT_ERR_INVALID_ARG, "qtt_apply_get_plan: bad argument");
+  *plan = encode_plan(A->plan[compute]);
+  return QTT_OK;
+}
+
+qtt_status qtt_apply_autotune(qtt_op *A, int64_t nrhs, qtt_dtype compute, int reps, void *stream,
+                              int *plan, double *seconds) {
+  if (!A || nrhs < 1 || !valid_dtype(compute))
+    return fail(QTT_ERR_INVALID_ARG, "qtt_apply_autotune: bad operator, nrhs or compute");
+  if (qtt_status ds = check_device(A, "qtt_apply_autotune")) return ds;
+  if (reps < 1) reps = 1;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // candidate plans for this arithmetic (the default first)
+  std::vector<ApplyPlan> cands;
+  ApplyPlan p0;
+  cands.push_back(p0);
+  if (compute == QTT_BF16) {
+    ApplyPlan p = p0;
+    p.groups_cap = 2;
+    cands.push_back(p);          // tcgen05 pairs, two epilogue groups
+    p = p0;
+    p.pairs = 1;
+    cands.push_back(p);          // mma.sync pairs
+    p = p0;
+    p.pairs = 0;
+    cands.push_back(p);          // head/tail merged, single middle steps
+    p = p0;
+    p.fusion = false;
+    cands.push_back(p);          // one launch per step
+  } else if (compute == QTT_F32 || compute == QTT_TF32) {
+    ApplyPlan p = p0;
+    p.staged = false;
+    cands.push_back(p);
+    p = p0;
+    p.fusion = false;
+    cands.push_back(p);
+    p.staged = false;
+    cands.push_back(p);
+  }
+  const qtt_dtype io = compute == QTT_F64 ? QTT_F64 : compute == QTT_BF16 ? QTT_BF16 : QTT_F32;
+  const int64_t N = (int64_t)1 << A->d;
+  const size_t bytes = (size_t)N * (size_t)nrhs * dtype_size(io);
+  void *x = nullptr, *y = nullptr;
+  qtt_status s = scratch_alloc(&x, bytes, st);
+  if (s == QTT_OK) s = scratch_alloc(&y, bytes, st);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (s == QTT_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    s = fail(QTT_ERR_CUDA, "qtt_apply_autotune: events");
+  if (s == QTT_OK && cudaMemsetAsync(x, 0, bytes, st) != cudaSuccess)
+    s = fail(QTT_ERR_CUDA, "qtt_apply_autotune: clear x");
+  const ApplyPlan keep = A->plan[compute];
+  double best_t = 1e300;
+  ApplyPlan best = keep;
+  for (size_t c = 0; c < cands.size() && s == QTT_OK; ++c) {
+    A->plan[compute] = cands[c];
+    // timing does not depend on the values (the arithmetic is data-independent)
+    qtt_status t = qtt_apply(A, x, y, nrhs, N, io, compute, st);  // warm-up
+    if (t != QTT_OK) continue;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && t == QTT_OK; ++r) t = qtt_apply(A, x, y, nrhs, N, io, compute, st);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      s = cuda_fail(cudaGetLastError(), "qtt_apply_autotune: sync");
+      break;
+    }
+    if (t != QTT_OK) continue;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double sec = ms / 1e3 / reps;
+    if (sec < best_t) {
+      best_t = sec;
+      best = cands[c];
+    }
+  }
+  A->plan[compute] = s == QTT_OK ? best : keep;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  scratch_free(x, st);
+  scratch_free(y, st);
+  if (s != QTT_OK) return s;
+  if (plan) *plan = encode_plan(best);
+  if (seconds) *seconds = best_t;
+  return QTT_OK;
 }
 
 qtt_status qtt_set_scratch_limit(size_t bytes) {

@@ -51,6 +51,27 @@ void release_after(const std::vector<void *> &ptrs, const std::vector<cudaEvent_
 
 struct qtt_op;
 namespace qtt {
+// How an apply in a given arithmetic runs (the fusion plan).  Chosen per
+// operator and arithmetic by qtt_apply_autotune (or set by the caller);
+// the defaults are the rules the library uses untuned.
+struct ApplyPlan {
+  bool fusion = true;   // merge steps: head/tail kernels (2-3 steps) and fused pairs (2 steps)
+  int pairs = 2;        // fused-pair kernel family: 2 tcgen05, 1 mma.sync, 0 none
+  int groups_cap = 0;   // tcgen05 pairs: 0 = as many epilogue groups as fit, 2 = two
+  bool staged = true;   // FP32/TF32 single steps on the staged (shared-memory) kernel
+};
+// plan code = fusion + 2 pairs + 8 (groups_cap == 2) + 16 staged
+inline int encode_plan(const ApplyPlan &p) {
+  return (p.fusion ? 1 : 0) + 2 * p.pairs + (p.groups_cap == 2 ? 8 : 0) + (p.staged ? 16 : 0);
+}
+inline bool decode_plan(int code, ApplyPlan *p) {
+  if (code < 0 || code > 31 || ((code >> 1) & 3) == 3) return false;
+  p->fusion = (code & 1) != 0;
+  p->pairs = (code >> 1) & 3;
+  p->groups_cap = (code & 8) ? 2 : 0;
+  p->staged = (code & 16) != 0;
+  return true;
+}
 // Record that work just queued on `stream` reads A (one event per stream,
 // re-recorded at each use; nothing is recorded while the stream is being
 // captured into a graph).  qtt_destroy releases A after these events.
@@ -97,6 +118,8 @@ struct qtt_op {
   // The same for the last three cores (d-3, d-2, d-1 as slots 0, 1, 2), for
   // the tail kernel.
   std::vector<float> tail[3];
+  // Fusion plan per arithmetic (index = qtt_dtype).
+  qtt::ApplyPlan plan[4];
   // Streams that have queued work reading the operator, each with an event
   // recorded after its latest use (see qtt::note_use).
   mutable std::mutex use_mu;

@@ -37,6 +37,7 @@ struct StepMMA2 {
   const __nv_bfloat16 *A2;   // M_{k+1} as [Mp2][Mp1] (its K padding equals M_k's row padding)
   int k, r0, r1, r2, Mp1, Kp1, Mp2;
   int64_t N, nrhs;
+  int groups_cap = 0;        // tcgen05 pairs: 0 = as many epilogue groups as fit, 2 = two
 };
 
 bool mma2_steps_eligible(int k, int r0, int r1, int r2, int64_t N);

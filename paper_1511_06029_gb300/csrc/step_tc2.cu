@@ -730,7 +730,7 @@ cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st) {
   // their tiles leave room for at least three ring stages -- the small-rank
   // pairs, whose time per chunk is set by the MMA -> epilogue -> MMA chain
   // rather than by bytes; else two.  As many ring stages as fit.
-  int G = 4, S = four_groups_allowed() ? stages_for(s, 4) : 0;
+  int G = 4, S = four_groups_allowed() && s.groups_cap != 2 ? stages_for(s, 4) : 0;
   if (S < 3) {
     G = 2;
     S = stages_for(s, 2);

@@ -58,6 +58,9 @@ SIGNATURES = {
     "qtt_gop_cols": (_L, [_P]),
     "qtt_gop_flops": (_D, [_P, _I]),
     "qtt_tt_round": (_I, [_I, _P, _I, _P, _D, _P, _P, _P]),
+    "qtt_apply_autotune": (_I, [_P, _L, _I, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "qtt_apply_set_plan": (_I, [_P, _I, _I]),
+    "qtt_apply_get_plan": (_I, [_P, _I, ctypes.POINTER(_I)]),
     "qtt_tt_svd": (_I, [_I, _P, _D, _P, _P, _L, ctypes.POINTER(_L), _P]),
     "qtt_local_apply": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _L, _P]),
     "qtt_op_product": (_I, [_P, _P, _P, _L, _P, _P]),
@@ -291,6 +294,49 @@ class Operator:
                                 ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
                "qtt_apply_tt")
         return [a * int(b) for a, b in zip(self.ranks, br)], out
+
+    def autotune(self, nrhs: int, compute: str = "bf16", reps: int = 2, cache=None, stream=None):
+        """Pick the fastest fusion plan for applies of nrhs right-hand sides in
+        `compute` (qtt_apply_autotune).  With `cache` (a JSON path; default
+        $QTT_PLAN_CACHE when set) a plan found earlier for the same d, ranks,
+        nrhs and arithmetic is reused instead of timed, and a new choice is
+        stored.  Returns (plan code, seconds per apply or None if cached)."""
+        import json
+        import zlib
+        cache = cache or os.environ.get("QTT_PLAN_CACHE")
+        key = (f"d{self.d}_r{zlib.crc32(np.asarray(self.ranks, dtype=np.int32).tobytes()):08x}"
+               f"_n{int(nrhs)}_{compute}")
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as fh:
+                table = json.load(fh)
+        if key in table:
+            _check(load_library().qtt_apply_set_plan(self.handle, DTYPES[compute],
+                                                     int(table[key]["plan"])),
+                   "qtt_apply_set_plan")
+            return int(table[key]["plan"]), None
+        plan, sec = ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(load_library().qtt_apply_autotune(self.handle, int(nrhs), DTYPES[compute], int(reps),
+                                                 _stream_handle(stream), ctypes.byref(plan),
+                                                 ctypes.byref(sec)), "qtt_apply_autotune")
+        if cache:
+            table[key] = {"plan": plan.value, "seconds": sec.value}
+            tmp = cache + f".tmp{os.getpid()}"
+            os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+            with open(tmp, "w") as fh:
+                json.dump(table, fh, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return plan.value, sec.value
+
+    def set_plan(self, compute: str, plan: int):
+        _check(load_library().qtt_apply_set_plan(self.handle, DTYPES[compute], int(plan)),
+               "qtt_apply_set_plan")
+
+    def get_plan(self, compute: str) -> int:
+        v = ctypes.c_int(0)
+        _check(load_library().qtt_apply_get_plan(self.handle, DTYPES[compute], ctypes.byref(v)),
+               "qtt_apply_get_plan")
+        return v.value
 
     def plan(self, x, out, compute: str = "f64"):
         """Record y = A x for these two tensors as a CUDA graph (qtt_plan_create);
