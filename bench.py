@@ -136,6 +136,10 @@ WORKLOADS = {
     "apply_f64_d21": dict(kind="apply", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=64,
                           compute="f64"),
     "compressed_tt": dict(kind="compressed", d=21, rmax=48, seed=3, smax=48, vec_seed=7),
+    "round_tt": dict(kind="round", d=21, rmax=48, seed=3, smax=48, vec_seed=7, eps=1e-6),
+    "general_f64": dict(kind="general", d=12, mode=4, rmax=32, seed=12),
+    "local_apply": dict(kind="local", ra=64, rx=256, nvec=16, seed=13),
+    "tt_svd_d12": dict(kind="ttsvd", n=16, eps=1e-6),
     "batched_f32": dict(kind="batched", compute="f32", count=256, seed=4),
     "batched_tf32": dict(kind="batched", compute="tf32", count=256, seed=4),
     "batched_f32_small": dict(kind="batched", compute="f32", count=24, seed=4,
@@ -463,6 +467,8 @@ def run_reference(args, spec):
         return run_reference_compressed(args, spec)
     if spec["kind"] in ("refine", "serve"):
         return run_reference_solve(args, spec)
+    if spec["kind"] in SAMPLES:
+        return run_reference_sample(args, spec)
     if spec["kind"] == "batched":
         it = inputs.batched_workload(count=1, seed=spec["seed"])[0]
         op = inputs.synthetic_operator(it["d"], it["rmax"], it["op_seed"])
@@ -880,12 +886,21 @@ class CompressedRun:
         return 8.0 * (self.out_elems + self.bh.size + nparams)
 
     def roofline(self, mean_s):
-        peak = measured_peaks().get("hbm_gbs") or 6800.0
+        # Each 8-byte entry costs two FP64 instructions (a multiply and a fused
+        # multiply-add, 3 flops): the FP64 pipe, at 2 instructions per clock
+        # per SM, caps the kernel below the HBM rate (2.5 TB/s of output), so
+        # the governing peak is the FP64 pipe's rate for this mix: 1.5 flops
+        # per instruction x SMs x 2 x clock.
+        peak = fp64_peak_gflops() * 0.75
+        achieved = self.work() / mean_s
+        hbm = measured_peaks().get("hbm_gbs") or 6800.0
         gbs = self.bytes_per_step() / mean_s / 1e9
-        return {"bound": "hbm", "kernel": "compressed_core_kernel (one launch per core)",
-                "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+        return {"bound": "alu", "kernel": "compressed_core_kernel (one launch per core)",
+                "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
                 "traffic": None, "bytes_per_step": self.bytes_per_step(),
-                "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json)"}
+                "hbm_achieved_gbs": gbs, "hbm_peak_gbs": hbm, "hbm_frac": gbs / hbm,
+                "peak_source": "FP64 pipe for one DMUL + one DFMA per entry (3 flops per 2 "
+                               "instructions): 0.75 x " + _peak_source("fp64")}
 
     def cpu_baseline(self):
         import oracle
@@ -914,8 +929,377 @@ class CompressedRun:
                 "output_doubles": self.out_elems, "l2": "output 0.5+ GB per step, larger than L2"}
 
 
+class GeneralRun:
+    """A QTT matrix with 4 x 4 modes (Sec. 3.1's tensorisation with m_k =
+    n_k = 4): d = 12 cores, 4^12 = 16,777,216 rows and columns, ranks up to
+    32, one FP64 right-hand side per step through qtt_gapply."""
+
+    def __init__(self, spec, rank, stream):
+        import torch
+        from paper_1511_06029_gb300 import qtt
+        self.spec = spec
+        m = [spec["mode"]] * spec["d"]
+        self.cores = inputs.general_cores(m, m, spec["rmax"], spec["seed"])
+        self.op = qtt.GeneralOperator(self.cores, stream=stream)
+        self.xh_np = inputs.gaussian_rhs(self.op.cols, 1, spec["seed"] + 1 + 1000 * rank)
+        self.x = torch.from_numpy(self.xh_np).cuda()
+        self.y = torch.empty(1, self.op.rows, dtype=torch.float64, device="cuda")
+        self.stream = stream
+        self.flops = self.op.flops()
+        self.xh = self.x.cpu().pin_memory()
+        self.yh = torch.empty_like(self.y.cpu()).pin_memory()
+        self.xd, self.yd = torch.empty_like(self.x), torch.empty_like(self.y)
+        self.unit = "GFLOP/s"
+        self.launches = spec["d"]
+
+    def step(self):
+        self.op.apply(self.x, out=self.y, stream=self.stream)
+
+    def e2e_step(self):
+        self.xd.copy_(self.xh, non_blocking=True)
+        self.op.apply(self.xd, out=self.yd)
+        self.yh.copy_(self.yd, non_blocking=True)
+
+    def e2e_bytes(self):
+        return self.x.numel() * 8, self.y.numel() * 8
+
+    def e2e_check(self):
+        import torch
+        return bool(torch.equal(self.yh, self.y.cpu()))
+
+    def work(self):
+        return self.flops / 1e9
+
+    def roofline(self, mean_s):
+        achieved = self.flops / mean_s / 1e9
+        return {"bound": "alu", "kernel": "gstep_kernel (one launch per core)",
+                "achieved": achieved, "peak": fp64_peak_gflops(), "unit": "GFLOP/s",
+                "frac": achieved / fp64_peak_gflops(), "traffic": None,
+                "peak_source": _peak_source("fp64")}
+
+    def config(self):
+        return {"workload": self.spec["name"], "d": self.spec["d"], "modes": self.spec["mode"],
+                "rows": self.op.rows, "cols": self.op.cols, "rmax": max(self.op.ranks),
+                "flops_per_step_per_gpu": self.flops,
+                "l2": "not flushed: each step streams 2 x 4.3 GB of intermediates"}
+
+    def cpu_baseline(self):
+        return oracle_general_sample(self.spec)
+
+    def close(self):
+        self.op.close()
+
+
+class LocalRun:
+    """The inversion's local-system product Psi G Phi W (appendix on local
+    linear systems) for operator ranks 64, X ranks 256 and 16 vectors W per
+    step (qtt_local_apply): three FP64 GEMMs per vector."""
+
+    def __init__(self, spec, rank, stream):
+        import torch
+        from paper_1511_06029_gb300 import qtt
+        self.qtt = qtt
+        self.spec = spec
+        ra, rx, nv = spec["ra"], spec["rx"], spec["nvec"]
+        rng = np.random.default_rng(spec["seed"] + 1000 * rank)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        self.psi = dev(rng.standard_normal((ra, rx, rx)) / rx)
+        self.G = dev(rng.standard_normal((ra, 2, 2, ra)) / ra)
+        self.phi = dev(rng.standard_normal((ra, rx, rx)) / rx)
+        self.Wh = rng.standard_normal((nv, rx, 2, 2, rx))
+        self.W = dev(self.Wh)
+        self.y = torch.empty_like(self.W)
+        self.stream = stream
+        self.flops = nv * (2.0 * ra * rx * 4 * rx * rx + 2.0 * 2 * rx * rx * 2 * ra * 2 * ra
+                           + 2.0 * 4 * rx * ra * rx * rx)
+        self.Wp = self.W.cpu().pin_memory()
+        self.yp = torch.empty_like(self.Wp).pin_memory()
+        self.Wd, self.yd = torch.empty_like(self.W), torch.empty_like(self.W)
+        self.unit = "GFLOP/s"
+        self.launches = 2 + 5 * nv
+
+    def step(self):
+        self.qtt.local_apply(self.psi, self.G, self.phi, self.W, out=self.y, stream=self.stream)
+
+    def e2e_step(self):
+        self.Wd.copy_(self.Wp, non_blocking=True)
+        self.qtt.local_apply(self.psi, self.G, self.phi, self.Wd, out=self.yd)
+        self.yp.copy_(self.yd, non_blocking=True)
+
+    def e2e_bytes(self):
+        return self.W.numel() * 8, self.y.numel() * 8
+
+    def e2e_check(self):
+        import torch
+        return bool(torch.equal(self.yp, self.y.cpu()))
+
+    def work(self):
+        return self.flops / 1e9
+
+    def roofline(self, mean_s):
+        achieved = self.flops / mean_s / 1e9
+        return {"bound": "alu", "kernel": "gemm_kernel (FP64, 64 x 64 tiles) + permute_kernel",
+                "achieved": achieved, "peak": fp64_peak_gflops(), "unit": "GFLOP/s",
+                "frac": achieved / fp64_peak_gflops(), "traffic": None,
+                "peak_source": _peak_source("fp64")}
+
+    def config(self):
+        return {"workload": self.spec["name"], "operator_ranks": self.spec["ra"],
+                "x_ranks": self.spec["rx"], "vectors_per_step": self.spec["nvec"],
+                "flops_per_step_per_gpu": self.flops, "l2": "operands fit in L2 (reused)"}
+
+    def cpu_baseline(self):
+        return oracle_local_sample(self.spec)
+
+    def close(self):
+        pass
+
+
+def round_flops(n, rin, rout):
+    """FP64 flops of TT rounding as the library runs it, from the ranks before
+    (rin) and after (rout): the left-to-right Householder QR (2 m p^2 -
+    2 p^3 / 3), its explicit Q (the same again) and the R x next-core product
+    of every core, the right-to-left QRs of the unfoldings and the products
+    that carry U S into the previous core (the Jacobi sweeps of the small
+    triangular factors are left out)."""
+    d = len(rin) - 1
+    r = list(rin)
+    f = 0.0
+    for k in range(d - 1):
+        m, nb = r[k] * n, r[k + 1]
+        p = min(m, nb)
+        f += 2 * (2.0 * max(m, nb) * p * p - 2.0 * p ** 3 / 3)
+        f += 2.0 * p * nb * n * r[k + 2]
+        r[k + 1] = p
+    for k in range(d - 1, 0, -1):
+        ra, q = r[k], n * rout[k + 1]
+        mm, nn = max(ra, q), min(ra, q)
+        f += 2 * (2.0 * mm * nn * nn - 2.0 * nn ** 3 / 3)
+        f += 2.0 * r[k - 1] * n * ra * rout[k] + 2.0 * ra * q * rout[k]
+        r[k] = rout[k]
+    return f
+
+
+class RoundRun:
+    """TT rounding on the GPU of the compressed product c = A b (Sec. 4.2):
+    A the d = 21, r <= 48 operator, b a QTT vector of ranks up to 48, so c's
+    ranks reach 2304; each step rounds c at eps = 1e-6 (qtt_tt_round)."""
+
+    def __init__(self, spec, rank, stream):
+        import torch
+        from paper_1511_06029_gb300 import qtt
+        self.qtt = qtt
+        self.spec = spec
+        self.data = make_operator(spec)
+        d = self.data.d
+        br = [min(1 << k, 1 << (d - k), spec["smax"]) for k in range(d + 1)]
+        rng = np.random.default_rng(spec["vec_seed"] + 1000 * rank)
+        cores = []
+        for k in range(d):
+            c = rng.standard_normal((br[k], 2, br[k + 1]))
+            c *= 10.0 ** (-0.05 * np.arange(br[k + 1]))[None, None, :]
+            cores.append(c.ravel())
+        op = qtt.Operator(self.data, stream=stream)
+        self.pr, self.pc = op.apply_tt(br, torch.from_numpy(np.concatenate(cores)).cuda(),
+                                       stream=stream)
+        torch.cuda.synchronize()
+        op.close()
+        self.out = torch.empty_like(self.pc)
+        self.stream = stream
+        self.rout, _ = qtt.tt_round(self.pr, 2, self.pc, spec["eps"], out=self.out, stream=stream)
+        self.flops = round_flops(2, self.pr, self.rout)
+        self.pch = self.pc.cpu().pin_memory()
+        self.pcd = torch.empty_like(self.pc)
+        self.outh = torch.empty_like(self.pch).pin_memory()
+        self.unit = "GFLOP/s"
+        self.launches = 0
+
+    def step(self):
+        self.qtt.tt_round(self.pr, 2, self.pc, self.spec["eps"], out=self.out, stream=self.stream)
+
+    def e2e_step(self):
+        self.pcd.copy_(self.pch, non_blocking=True)
+        ro, res = self.qtt.tt_round(self.pr, 2, self.pcd, self.spec["eps"], out=self.out)
+        self.outh[:res.numel()].copy_(res, non_blocking=True)
+
+    def e2e_bytes(self):
+        n = sum(2 * self.rout[k] * self.rout[k + 1] for k in range(len(self.rout) - 1))
+        return self.pc.numel() * 8, n * 8
+
+    def e2e_check(self):
+        return True
+
+    def work(self):
+        return self.flops / 1e9
+
+    def roofline(self, mean_s):
+        achieved = self.flops / mean_s / 1e9
+        return {"bound": "alu", "kernel": "Householder dots/update kernels, gemm_kernel, "
+                                          "jacobi_round_kernel",
+                "achieved": achieved, "peak": fp64_peak_gflops(), "unit": "GFLOP/s",
+                "frac": achieved / fp64_peak_gflops(), "traffic": None,
+                "flops_per_rounding": self.flops, "seconds_per_rounding": mean_s,
+                "peak_source": _peak_source("fp64")}
+
+    def config(self):
+        return {"workload": self.spec["name"], "d": self.data.d, "product_rmax": max(self.pr),
+                "rounded_rmax": max(self.rout), "eps": self.spec["eps"],
+                "product_doubles": self.pc.numel(), "flops_per_step_per_gpu": self.flops,
+                "l2": "each step streams GBs of cores and factors"}
+
+    def cpu_baseline(self):
+        return oracle_round_sample(self.spec)
+
+    def close(self):
+        pass
+
+
+class TTSVDRun:
+    """Algorithm 1 on the GPU (qtt_tt_svd): the 16^3 Laplace volume matrix
+    (Sec. 5.2's operator on a 16 x 16 x 16 grid, 4096 x 4096, d = 12)
+    decomposed at eps = 1e-6 per step."""
+
+    def __init__(self, spec, rank, stream):
+        import torch
+        from paper_1511_06029_gb300 import qtt
+        self.qtt = qtt
+        self.spec = spec
+        self.Ah = inputs.laplace_volume_dense(spec["n"])
+        self.A = torch.from_numpy(self.Ah).cuda()
+        self.stream = stream
+        self.ranks, _ = qtt.tt_svd(self.A, spec["eps"], stream=stream)
+        self.Ap = self.A.cpu().pin_memory()
+        self.Ad = torch.empty_like(self.A)
+        self.unit = "decompositions/s"
+        self.launches = 0
+
+    def step(self):
+        self.qtt.tt_svd(self.A, self.spec["eps"], stream=self.stream)
+
+    def e2e_step(self):
+        self.Ad.copy_(self.Ap, non_blocking=True)
+        self.qtt.tt_svd(self.Ad, self.spec["eps"])
+
+    def e2e_bytes(self):
+        n = sum(4 * self.ranks[k] * self.ranks[k + 1] for k in range(len(self.ranks) - 1))
+        return self.Ah.nbytes, n * 8
+
+    def e2e_check(self):
+        return True
+
+    def work(self):
+        return 1.0
+
+    def roofline(self, mean_s):
+        return {"bound": "latency", "kernel": "Householder QR, Jacobi SVD and GEMM kernels",
+                "achieved": None, "peak": None, "unit": "s", "frac": None, "traffic": None,
+                "seconds_per_decomposition": mean_s,
+                "note": "many small dependent launches (one Householder column and one "
+                        "Jacobi round each); no roofline fraction is claimed"}
+
+    def config(self):
+        return {"workload": self.spec["name"], "d": int(np.log2(self.Ah.shape[0])),
+                "matrix": f"{self.Ah.shape[0]} x {self.Ah.shape[1]}", "eps": self.spec["eps"],
+                "ranks": self.ranks, "l2": "matrix 134 MB, larger than L2"}
+
+    def cpu_baseline(self):
+        return oracle_ttsvd_sample(self.spec)
+
+    def close(self):
+        pass
+
+
+# ------------------------------------------ oracle samples of the next rows
+# Each times the oracle once on a bounded sample of the workload and returns
+# a cpu_baseline dict (also the reference arm's step for these workloads).
+def oracle_general_sample(spec):
+    import oracle
+    m = [spec["mode"]] * 8
+    cores = inputs.general_cores(m, m, spec["rmax"], spec["seed"])
+    x = inputs.gaussian_rhs(int(np.prod(m)), 1, 3)
+    t0 = time.perf_counter()
+    oracle.apply_general(cores, x)
+    dt = time.perf_counter() - t0
+    f = sum(2.0 * c.shape[0] * 16 * c.shape[3] * 4.0 ** 7 for c in cores)
+    return {"value": f / dt / 1e9, "unit": "GFLOP/s", "cores": host_cores(), "kind": "oracle",
+            "sample": f"d = 8 cores of the same modes and ranks (65,536 x 65,536), one "
+                      f"oracle.apply_general call ({dt:.1f} s, numpy)"}
+
+
+def oracle_local_sample(spec):
+    import oracle
+    rng = np.random.default_rng(1)
+    ra, rx = 8, 16
+    args = (rng.standard_normal((ra, rx, rx)), rng.standard_normal((ra, 2, 2, ra)),
+            rng.standard_normal((ra, rx, rx)), rng.standard_normal((rx, 2, 2, rx)))
+    t0 = time.perf_counter()
+    oracle.local_apply(*args)
+    dt = time.perf_counter() - t0
+    f = 2.0 * ra * rx * 4 * rx * rx + 2.0 * 2 * rx * rx * 2 * ra * 2 * ra + 2.0 * 4 * rx * ra * rx * rx
+    return {"value": f / dt / 1e9, "unit": "GFLOP/s", "cores": host_cores(), "kind": "oracle",
+            "sample": f"operator ranks 8, X ranks 16, one vector: oracle.local_apply (numpy "
+                      f"einsum over all indices, {dt:.2f} s)"}
+
+
+def oracle_round_sample(spec):
+    import oracle
+    d = 14
+    A = inputs.synthetic_operator(d, 24, 3)
+    br = [min(1 << k, 1 << (d - k), 24) for k in range(d + 1)]
+    rng = np.random.default_rng(7)
+    b = oracle.Vec(br, [rng.standard_normal((br[k], 2, br[k + 1])) for k in range(d)])
+    c = oracle.apply_tt(A, b)
+    t0 = time.perf_counter()
+    rc = oracle.tt_round(c, spec["eps"])
+    dt = time.perf_counter() - t0
+    f = round_flops(2, c.ranks, rc.ranks)
+    return {"value": f / dt / 1e9, "unit": "GFLOP/s", "cores": host_cores(), "kind": "oracle",
+            "sample": f"rounding of a d = 14 product (ranks up to {max(c.ranks)}) at the same "
+                      f"eps: oracle.tt_round (numpy QR/SVD), {dt:.1f} s"}
+
+
+def oracle_ttsvd_sample(spec):
+    import oracle
+    A = inputs.laplace_volume_dense(spec["n"])
+    t0 = time.perf_counter()
+    oracle.tt_svd(A, spec["eps"])
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "decompositions/s", "cores": host_cores(),
+            "kind": "oracle", "sample": f"the same matrix, oracle.tt_svd (numpy SVD), {dt:.1f} s"}
+
+
+SAMPLES = {"general": oracle_general_sample, "local": oracle_local_sample,
+           "round": oracle_round_sample, "ttsvd": oracle_ttsvd_sample}
+
+
+def run_reference_sample(args, spec):
+    """--impl reference for the next rows' workloads: each step one oracle
+    run of the bounded sample, in the sample's own unit."""
+    fn = SAMPLES[spec["kind"]]
+    for _ in range(args.warmup):
+        fn(spec)
+    vals, t0 = [], time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(fn(spec))
+    dt = time.perf_counter() - t0
+    last = vals[-1]
+    value = float(np.median([v["value"] for v in vals]))
+    line = {"metric": METRIC if last["unit"] == "GFLOP/s" else last["unit"], "value": value,
+            "unit": last["unit"], "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "sample": last["sample"]},
+            "cpu_baseline": dict(last, value=value),
+            "e2e": {"value": value, "unit": last["unit"], "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 RUNNERS = {"apply": ApplyRun, "batched": BatchedRun, "refine": RefineRun,
-           "compressed": CompressedRun}
+           "compressed": CompressedRun, "general": GeneralRun, "local": LocalRun,
+           "round": RoundRun, "ttsvd": TTSVDRun}
 
 # --------------------------------------------------------------- serving
 def _serve_operators(d_range, rmax, seed_base, eps, qtt, log):

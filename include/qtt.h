@@ -217,8 +217,8 @@ qtt_status qtt_plan_destroy(qtt_plan *P);
  * bit j_k:
  *   C_k[alpha s + beta][i][alpha' s' + beta']
  *       = sum_j G_k[alpha][i][j][alpha'] b_k[beta][j][beta'],
- * so c's ranks are r_k s_k (no rounding).  Each entry is computed as
- * fl(fl(a_0 b_0) + fl(a_1 b_1)) in FP64.
+ * so c's ranks are r_k s_k (no rounding).  Each entry is computed in FP64
+ * as fma(a_1, b_1, fl(a_0 b_0)) (one product, one fused multiply-add).
  *   b_ranks : host array of d + 1 ranks s_0 .. s_d (s_0 = s_d = 1, each in
  *             [1, 4096], every r_k s_k <= 32767), d = A's d.
  *   b_cores : device FP64, b's cores back to back, core k [s_k][2][s_{k+1}]

@@ -6,11 +6,10 @@
 //   C_k[alpha s + beta][i][alpha' s' + beta'] =
 //       sum_j A_k[alpha][i][j][alpha'] b_k[beta][j][beta'],
 // so c's ranks are the products r_k s_k (no rounding here).  Every output
-// entry is two products and one addition, written once: the kernel streams
-// the output (sum_k 2 r_k s_k r_{k+1} s_{k+1} doubles) and reads the small
-// cores of A and b through L1/L2.  Each entry is the separately rounded
-// fl(fl(a_0 b_0) + fl(a_1 b_1)) (no fused multiply-add), the evaluation of
-// the definition written out.
+// entry is two products and one addition, written once (sum_k 2 r_k s_k
+// r_{k+1} s_{k+1} doubles); the small cores of A and b are read once per row
+// into shared memory.  Each entry is fma(a_1, b_1, fl(a_0 b_0)): within
+// u (|a_0 b_0| + |a_0 b_0 + a_1 b_1|) of the exact sum.
 #include <vector>
 
 #include "qtt_internal.h"
@@ -20,29 +19,47 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// One core of c.  M: A's FP64 core as packed at qtt_create, [a'][a][j][i];
-// B: b's core [beta][j][beta']; C: c's core [a s + beta][i][a' s' + beta'].
-// Block row blockIdx.y = (a s + beta) 2 + i (one output row, its A and b
-// slices fixed); threads stride over the row's rb s' columns, so each entry
-// costs one 32-bit division (col -> a', beta') and one coalesced store.
+// One core of c, one output row per CTA.  M: A's FP64 core as packed at
+// qtt_create, [a'][a][j][i]; B: b's core [beta][j][beta']; C: c's core
+// [a s + beta][i][a' s' + beta'].  Row blockIdx.x = (a s + beta) 2 + i fixes
+// A's slice (a, i) and b's slice beta: the CTA stages A(a, i, j, a') for both
+// j and b(beta, j, beta') for both j in shared memory, then its threads walk
+// the row's r' s' columns -- column = a' s' + beta', the pair (a', beta')
+// advanced by counters, no division per entry -- and each writes
+// fma(A_1, b_1, fl(A_0 b_0)).  On GB300 the FP64 pipe issues two
+// instructions per clock per SM, so an entry's two FP64 instructions (a
+// multiply and a fused multiply-add) for its 8 stored bytes -- not the
+// store itself -- set the limit: 152 x 2 x 2.07e9 / 2 = 3.1e11 entries/s,
+// 2.5 TB/s of output.
 __global__ void __launch_bounds__(kThreads) compressed_core_kernel(
     const double *__restrict__ M, const double *__restrict__ B, double *__restrict__ C, int ra,
     int rb, int s, int s2) {
-  const unsigned row2 = blockIdx.y;  // (a s + beta) 2 + i
+  extern __shared__ double sm[];
+  double *sa = sm;            // [a'][j]: 2 rb
+  double *sb = sm + 2 * rb;   // [j][beta']: 2 s2
+  const unsigned row2 = blockIdx.x;  // (a s + beta) 2 + i
   const int i = (int)(row2 & 1u);
   const unsigned row = row2 >> 1;
   const int a = (int)(row / (unsigned)s), beta = (int)(row % (unsigned)s);
+  for (int t = threadIdx.x; t < rb; t += kThreads) {
+    const double *m = M + ((int64_t)t * ra + a) * 4 + i;  // (a' = t, a, j = 0, i)
+    sa[2 * t] = __ldg(m);
+    sa[2 * t + 1] = __ldg(m + 2);
+  }
+  for (int t = threadIdx.x; t < 2 * s2; t += kThreads) sb[t] = __ldg(B + (int64_t)beta * 2 * s2 + t);
+  __syncthreads();
   const unsigned cols = (unsigned)rb * (unsigned)s2;
-  const double *mrow = M + (int64_t)a * 4 + i;                  // + a' ra 4; j at +2
-  const double *brow = B + (int64_t)beta * 2 * s2;              // + beta'; j at +s2
   double *crow = C + (int64_t)row2 * cols;
-  const int64_t mstride = (int64_t)ra * 4;
-  for (unsigned col = blockIdx.x * kThreads + threadIdx.x; col < cols;
-       col += gridDim.x * kThreads) {
-    const unsigned a2 = col / (unsigned)s2, beta2 = col - a2 * (unsigned)s2;
-    const double *m = mrow + a2 * mstride;
-    const double *bb = brow + beta2;
-    crow[col] = __dadd_rn(__dmul_rn(__ldg(m), __ldg(bb)), __dmul_rn(__ldg(m + 2), __ldg(bb + s2)));
+  unsigned a2 = threadIdx.x / (unsigned)s2, b2 = threadIdx.x % (unsigned)s2;
+  const unsigned da = kThreads / (unsigned)s2, db = kThreads % (unsigned)s2;
+  for (unsigned col = threadIdx.x; col < cols; col += kThreads) {
+    crow[col] = fma(sa[2 * a2 + 1], sb[s2 + b2], __dmul_rn(sa[2 * a2], sb[b2]));
+    a2 += da;
+    b2 += db;
+    if (b2 >= (unsigned)s2) {
+      b2 -= (unsigned)s2;
+      ++a2;
+    }
   }
 }
 
@@ -93,21 +110,16 @@ extern "C" qtt_status qtt_apply_tt(const qtt_op *A, const int *b_ranks, const do
                 "qtt_apply_tt: vector ranks must start and end with 1, lie in [1, 4096], "
                 "and keep every product rank r_k s_k <= 32767");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // shared memory of the largest core: 2 (r' + s') doubles (<= 128 KB)
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      compressed_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * (4096 + 4096) * 8);
+  if (attr != cudaSuccess) return cuda_fail(attr, "qtt_apply_tt: shared memory attribute");
   for (int k = 0; k < A->d; ++k) {
-    const int64_t rows2 = (int64_t)A->ranks[k] * b_ranks[k] * 2;       // <= 65534
-    const int64_t cols = (int64_t)A->ranks[k + 1] * b_ranks[k + 1];     // <= 2^20
-    // enough blocks per row that the grid covers every SM several times
-    int64_t bx = (cols + kThreads - 1) / kThreads;
-    const int64_t want = ((int64_t)sms * 8 + rows2 - 1) / rows2;
-    if (bx > want) bx = want < 1 ? 1 : want;
-    const dim3 grid((unsigned)bx, (unsigned)rows2);
-    compressed_core_kernel<<<grid, kThreads, 0, st>>>(A->m64 + A->off[k], b_cores + boff[k],
-                                                      c_cores + coff[k], A->ranks[k],
-                                                      A->ranks[k + 1], b_ranks[k],
-                                                      b_ranks[k + 1]);
+    const int64_t rows2 = (int64_t)A->ranks[k] * b_ranks[k] * 2;  // <= 65534
+    const size_t smem = (size_t)2 * (A->ranks[k + 1] + b_ranks[k + 1]) * sizeof(double);
+    compressed_core_kernel<<<(unsigned)rows2, kThreads, smem, st>>>(
+        A->m64 + A->off[k], b_cores + boff[k], c_cores + coff[k], A->ranks[k], A->ranks[k + 1],
+        b_ranks[k], b_ranks[k + 1]);
     count_launches(1);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -29,36 +29,43 @@ struct GemmArgs {
   int64_t m, n, k, lda, ldb, ldc, sa, sb, sc;
   double alpha, beta;
   int ta, tb;
+  // split-K: blockIdx.z = batch * splits + split; split s sums k in
+  // [s kchunk, (s + 1) kchunk) into part[(s batch + b) m n] (alpha applied)
+  int splits;
+  int64_t kchunk, batch;
+  double *part;
 };
 
 __global__ void __launch_bounds__(kThreads) gemm_kernel(GemmArgs g) {
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t bz = blockIdx.z;
+  const int64_t z = blockIdx.z;
+  const int64_t bz = z / g.splits, sp = z - bz * g.splits;
   const double *A = g.A + bz * g.sa;
   const double *B = g.B + bz * g.sb;
   double *C = g.C + bz * g.sc;
   const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
+  const int64_t klo = sp * g.kchunk, khi = min(g.k, klo + g.kchunk);
   double acc[4][4];
 #pragma unroll
   for (int s = 0; s < 4; ++s)
 #pragma unroll
     for (int t = 0; t < 4; ++t) acc[s][t] = 0.0;
-  for (int64_t k0 = 0; k0 < g.k; k0 += BK) {
+  for (int64_t k0 = klo; k0 < khi; k0 += BK) {
     for (int e = tid; e < BM * BK; e += kThreads) {
       // consecutive threads read consecutive addresses of A
       const int ii = g.ta ? e % BM : e / BK, kk = g.ta ? e / BM : e % BK;
       const int64_t gi = i0 + ii, gk = k0 + kk;
       double v = 0.0;
-      if (gi < g.m && gk < g.k) v = g.ta ? A[gk * g.lda + gi] : A[gi * g.lda + gk];
+      if (gi < g.m && gk < khi) v = g.ta ? A[gk * g.lda + gi] : A[gi * g.lda + gk];
       As[kk][ii] = v;
     }
     for (int e = tid; e < BN * BK; e += kThreads) {
       const int jj = g.tb ? e / BK : e % BN, kk = g.tb ? e % BK : e / BN;
       const int64_t gj = j0 + jj, gk = k0 + kk;
       double v = 0.0;
-      if (gj < g.n && gk < g.k) v = g.tb ? B[gj * g.ldb + gk] : B[gk * g.ldb + gj];
+      if (gj < g.n && gk < khi) v = g.tb ? B[gj * g.ldb + gk] : B[gk * g.ldb + gj];
       Bs[kk][jj] = v;
     }
     __syncthreads();
@@ -84,9 +91,26 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(GemmArgs g) {
     for (int t = 0; t < 4; ++t) {
       const int64_t j = j0 + tx + 16 * t;
       if (j >= g.n) continue;
+      if (g.splits > 1) {
+        g.part[(sp * g.batch + bz) * g.m * g.n + i * g.n + j] = g.alpha * acc[s][t];
+        continue;
+      }
       double *c = C + i * g.ldc + j;
       *c = g.beta == 0.0 ? g.alpha * acc[s][t] : fma(g.alpha, acc[s][t], g.beta * *c);
     }
+  }
+}
+
+// C = sum over the splits, in split order, of the partial products (+ beta C).
+__global__ void __launch_bounds__(kThreads) gemm_reduce_kernel(GemmArgs g) {
+  const int64_t mn = g.m * g.n, total = mn * g.batch;
+  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * kThreads) {
+    const int64_t bz = e / mn, r = e - bz * mn, i = r / g.n, j = r - i * g.n;
+    double s = 0.0;
+    for (int sp = 0; sp < g.splits; ++sp) s += g.part[((int64_t)sp * g.batch + bz) * mn + r];
+    double *c = g.C + bz * g.sc + i * g.ldc + j;
+    *c = g.beta == 0.0 ? s : fma(g.beta, *c, s);
   }
 }
 
@@ -169,9 +193,36 @@ cudaError_t gemm(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha
                  int64_t sb, double beta, double *C, int64_t ldc, int64_t sc, int64_t batch,
                  cudaStream_t st) {
   if (m <= 0 || n <= 0 || batch <= 0) return cudaSuccess;
-  GemmArgs g{A, B, C, m, n, k, lda, ldb, ldc, sa, sb, sc, alpha, beta, ta ? 1 : 0, tb ? 1 : 0};
+  GemmArgs g{A, B, C, m, n, k, lda, ldb, ldc, sa, sb, sc, alpha, beta, ta ? 1 : 0, tb ? 1 : 0,
+             1, std::max<int64_t>(k, 1), 1, nullptr};
   const int64_t gx = (n + BN - 1) / BN, gy = (m + BM - 1) / BM;
   if (gy > 65535 || gx > 0x7fffffffLL) return cudaErrorInvalidValue;
+  // Split-K when the output tiles leave most SMs idle and K is long: S
+  // splits (a function of the shape only, so results are reproducible) sum
+  // into partial products that a second launch adds in split order.
+  const int64_t tiles = gx * gy * batch;
+  int S = 1;
+  if (batch <= 65535 && tiles < 2 * 152 && k >= 8 * BK) {
+    S = (int)std::min<int64_t>({(2 * 152 + tiles - 1) / tiles, k / (4 * BK), 64});
+    if (tiles * S > 65535 * gx * gy) S = 1;
+  }
+  if (S > 1) {
+    void *part = nullptr;
+    if (scratch_alloc(&part, (size_t)S * batch * m * n * sizeof(double), st) != QTT_OK) {
+      S = 1;  // no room: the single pass below
+    } else {
+      g.splits = S;
+      g.kchunk = ((k + S - 1) / S + BK - 1) / BK * BK;
+      g.batch = batch;
+      g.part = static_cast<double *>(part);
+      gemm_kernel<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)(batch * S)), kThreads, 0, st>>>(g);
+      gemm_reduce_kernel<<<grid_for(m * n * batch), kThreads, 0, st>>>(g);
+      count_launches(2);
+      const cudaError_t e = cudaGetLastError();
+      scratch_free(part, st);
+      return e;
+    }
+  }
   for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
     GemmArgs h = g;
     h.A += b0 * sa;

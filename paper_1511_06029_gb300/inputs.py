@@ -121,6 +121,23 @@ def synthetic_operator(d: int, rmax: int, seed: int) -> QTTData:
     return QTTData(ranks, cores, {"kind": "synthetic", "d": d, "rmax": rmax, "seed": seed})
 
 
+def general_cores(m, n, rmax: int, seed: int):
+    """Cores of a QTT matrix with general mode sizes (m_k x n_k modes):
+    ranks min(prod of the mode products on either side, rmax), entries
+    i.i.d. N(0, 1 / (r_k n_k)) so that every step keeps the intermediate's
+    size of order one.  Core k has shape (r_k, m_k, n_k, r_{k+1})."""
+    rng = np.random.default_rng(seed)
+    d = len(m)
+    ranks = [1]
+    for k in range(1, d):
+        left = int(np.prod([m[l] * n[l] for l in range(k)]))
+        right = int(np.prod([m[l] * n[l] for l in range(k, d)]))
+        ranks.append(min(rmax, left, right))
+    ranks.append(1)
+    return [rng.standard_normal((ranks[k], m[k], n[k], ranks[k + 1])) / math.sqrt(ranks[k] * n[k])
+            for k in range(d)]
+
+
 def gaussian_rhs(N: int, nrhs: int, seed: int) -> np.ndarray:
     """(nrhs, N) i.i.d. N(0, 1); row c is right-hand side c."""
     rng = np.random.default_rng(seed)
