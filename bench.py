@@ -110,7 +110,9 @@ METRIC = "QTT-apply GFLOP/s"
 # capture of the same command, averaged over one apply's launches; valid for
 # the kernel source it was taken on (see the named profile).
 NCU_TRAFFIC = {
-    "apply_f64": {"bytes_per_launch": 144.41e9 / 24,
+    # measured on d = 22 (31.09 GB = 0.971 of its algorithmic bytes), scaled
+    # to d = 24 by the algorithmic bytes (145.23 GB per apply, 24 launches)
+    "apply_f64": {"bytes_per_launch": 145.23e9 * 0.971 / 24,
                   "source": "profiles/step_f64_kernel_apply_f64_d24_launches.md"},
 }
 
