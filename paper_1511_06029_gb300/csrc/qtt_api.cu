@@ -431,6 +431,36 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
       k0 = hm;
     }
     for (int k = k0; k < kend; ++k) {
+      // TF32: steps k and k+1 on the tcgen05 tensor cores (kind::tf32)
+      if (compute == QTT_TF32 && fuse && pl.pairs == 2 && A->mma_tf32 && use_tensor_cores() &&
+          use_tcgen05() && k >= 1 && k + 2 < d && k + 1 < kend && A->toff[k] >= 0 &&
+          A->toff[k + 1] >= 0 &&
+          tc2f_steps_eligible(k, A->ranks[k], A->ranks[k + 1], A->ranks[k + 2], N)) {
+        StepTF2 t;
+        t.in = reinterpret_cast<const float *>(buf[src]);
+        t.in_rhs_stride = (int64_t)A->ranks[k] * N;
+        t.out = reinterpret_cast<float *>(buf[src ^ 1]);
+        t.out_rhs_stride = (int64_t)A->ranks[k + 2] * N;
+        t.A1 = A->mma_tf32 + A->toff[k];
+        t.A2 = A->mma_tf32 + A->toff[k + 1];
+        t.k = k;
+        t.r0 = A->ranks[k];
+        t.r1 = A->ranks[k + 1];
+        t.r2 = A->ranks[k + 2];
+        t.N = N;
+        t.nrhs = nc;
+        const cudaError_t e = launch_step_tc2_tf32(t, st);
+        if (e == cudaSuccess) {
+          src ^= 1;
+          ++k;
+          continue;
+        }
+        if (e != cudaErrorNotSupported) {
+          scratch_free(scratch, st);
+          return cuda_fail(e, "TF32 tensor-core step launch");
+        }
+        cudaGetLastError();  // nothing was launched: the steps run one by one
+      }
       const bool pair = tc && fuse && pl.pairs > 0 && k + 2 < d && k + 1 < kend && A->mp[k] &&
                         A->mp[k + 1];
       const bool tc5 = pair && use_tcgen05() && pl.pairs == 2 &&
@@ -741,6 +771,31 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores
       std::vector<float> t(lp);
       for (float &v : t) v = host_tf32_rne(v);
       e2 = upload(reinterpret_cast<void **>(&A->mtf32), t.data(), t.size() * sizeof(float));
+      // tensor-core layout [128][2 r_k], rows 2b+i, columns 2a+j (the same
+      // TF32 values as the packed copy)
+      A->toff.assign(d, -1);
+      int64_t to = 0;
+      for (int k = 0; k < d; ++k) {
+        if ((ranks[k] != 16 && ranks[k] != 32) || ranks[k + 1] > 32) continue;
+        A->toff[k] = to;
+        to += (int64_t)128 * 2 * ranks[k];
+      }
+      if (e2 == cudaSuccess && to > 0) {
+        std::vector<float> m((size_t)to, 0.0f);
+        for (int k = 0; k < d; ++k) {
+          if (A->toff[k] < 0) continue;
+          const int ra = ranks[k], rb = ranks[k + 1], K = 2 * ra;
+          const double *G = cores + A->off[k];
+          float *M = m.data() + A->toff[k];
+          for (int a = 0; a < ra; ++a)
+            for (int i = 0; i < 2; ++i)
+              for (int j = 0; j < 2; ++j)
+                for (int b = 0; b < rb; ++b)
+                  M[(size_t)(2 * b + i) * K + 2 * a + j] =
+                      host_tf32_rne((float)G[(((size_t)a * 2 + i) * 2 + j) * rb + b]);
+        }
+        e2 = upload(reinterpret_cast<void **>(&A->mma_tf32), m.data(), m.size() * sizeof(float));
+      }
     }
     if (e2 == cudaSuccess && (precision_mask & QTT_PACK_BF16)) {
       std::vector<__nv_bfloat16> h(lp.size());
@@ -799,7 +854,7 @@ qtt_status qtt_destroy(qtt_op *A) {
     for (auto &u : A->uses) evs.push_back(u.second);
     A->uses.clear();
   }
-  release_after({A->m64, A->m32, A->mtf32, A->mbf16, A->mma_bf16}, evs);
+  release_after({A->m64, A->m32, A->mtf32, A->mbf16, A->mma_bf16, A->mma_tf32}, evs);
   for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
   if (cur >= 0 && cur != A->device) cudaSetDevice(cur);
   delete A;
@@ -971,6 +1026,11 @@ qtt_status qtt_apply_autotune(qtt_op *A, int64_t nrhs, qtt_dtype compute, int re
     cands.push_back(p);          // one launch per step
   } else if (compute == QTT_F32 || compute == QTT_TF32) {
     ApplyPlan p = p0;
+    if (compute == QTT_TF32) {
+      p.pairs = 0;
+      cands.push_back(p);        // no tcgen05 pairs: every middle step on the FP32 pipe
+      p = p0;
+    }
     p.staged = false;
     cands.push_back(p);
     p = p0;
@@ -1059,8 +1119,10 @@ qtt_status qtt_sync_status(void *stream) {
   if (e != cudaSuccess) return cuda_fail(e, "qtt_sync_status");
   int h = 0;
   e = tc_status_take(&h);
+  int hf = 0;
+  if (e == cudaSuccess) e = tcf_status_take(&hf);
   if (e != cudaSuccess) return cuda_fail(e, "qtt_sync_status: device status word");
-  if (h != 0)
+  if (h != 0 || hf != 0)
     return fail(QTT_ERR_TIMEOUT, "tensor-core kernel: an mbarrier wait ran out of its budget");
   return QTT_OK;
 }

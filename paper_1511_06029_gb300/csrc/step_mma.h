@@ -50,6 +50,25 @@ cudaError_t launch_step_mma2_bf16(const StepMMA2 &s, cudaStream_t st);
 constexpr int kTc2MaxRank = 56;
 bool tc2_steps_eligible(int k, int r0, int r1, int r2, int64_t N);
 cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st);
+// Two consecutive TF32 steps on the tcgen05 tensor cores (step_tc2f.cu,
+// kind::tf32): FP32 planar buffers holding TF32-rounded values; cores as
+// [128][2 r_in] TF32 matrices (rows 2 r_out + i, columns 2 a + j, rows past
+// 2 r_out zero).  cudaErrorNotSupported (nothing launched) when the shapes
+// do not fit.
+struct StepTF2 {
+  const float *in;           // y_k, planar [rhs][a][position]
+  int64_t in_rhs_stride;
+  float *out;                // y_{k+2}
+  int64_t out_rhs_stride;
+  const float *A1;           // M_k as [128][2 r0]
+  const float *A2;           // M_{k+1} as [128][2 r1]
+  int k, r0, r1, r2;
+  int64_t N, nrhs;
+};
+bool tc2f_steps_eligible(int k, int r0, int r1, int r2, int64_t N);
+cudaError_t launch_step_tc2_tf32(const StepTF2 &s, cudaStream_t st);
+cudaError_t tcf_status_take(int *status);
+
 // Device status word of the tcgen05 kernels (QTT_ERR_TIMEOUT after a bounded
 // wait gave up); returns it and clears it.
 cudaError_t tc_status_take(int *status);

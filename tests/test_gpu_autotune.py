@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 
 BF16_PLANS = [21, 29, 19, 17, 20]  # default, two groups, mma.sync pairs, no pairs, no fusion
 F32_PLANS = [21, 5, 20, 4]         # default, unstaged, no fusion, neither
+TF32_PLANS = [21, 17, 5, 20, 4]    # default (tcgen05 pairs), no pairs, unstaged, no fusion, neither
 
 
 @pytest.fixture(scope="module")
@@ -27,7 +28,7 @@ def qtt():
 
 @pytest.mark.parametrize("compute,plans,tol", [("bf16", BF16_PLANS, 4 * 2.0 ** -8),
                                                ("f32", F32_PLANS, 4 * 2.0 ** -24),
-                                               ("tf32", F32_PLANS, 4 * 2.0 ** -11)])
+                                               ("tf32", TF32_PLANS, 4 * 2.0 ** -11)])
 def test_every_plan_computes_the_product(qtt, compute, plans, tol):
     import torch
     data = inputs.synthetic_operator(16, 32, 2)
