@@ -15,7 +15,10 @@ Workloads (a "step" is one pass of the hot path over one batch of input):
                   (qtt_plan_*, one CUDA graph launch).
   apply_f32_d24 / apply_tf32_d24 / apply_bf16_d24
                   the default operator and RHS with FP32 / TF32 / BF16 operands
-                  and FP32 accumulation (FP32 pipe).
+                  and FP32 accumulation (FP32 steps on the FP32 pipe; TF32 and
+                  BF16 middle steps in pairs on the tcgen05 tensor cores).
+  apply_f32_d22 / apply_tf32_d22
+                  the same family at d = 22 (profiler captures).
   apply_bf16_d21  d = 21, r_max = 48, 64 BF16 right-hand sides, BF16 operands,
                   FP32 accumulation.
   apply_bf16_d20_8
@@ -129,6 +132,8 @@ WORKLOADS = {
                            compute="tf32"),
     "apply_f32_d22": dict(kind="apply", d=22, rmax=32, seed=2, rhs_seed=3, nrhs=1,
                           compute="f32"),
+    "apply_tf32_d22": dict(kind="apply", d=22, rmax=32, seed=2, rhs_seed=3, nrhs=1,
+                           compute="tf32"),
     "apply_bf16_d24": dict(kind="apply", d=24, rmax=32, seed=2, rhs_seed=3, nrhs=1,
                            compute="bf16"),
     "apply_bf16_d21": dict(kind="apply", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=64,
@@ -168,6 +173,7 @@ WORKLOADS = {
     "refine_f64_d21_2": dict(kind="refine", d=21, rmax=48, seed=3, rhs_seed=4, nrhs=2,
                              pc="f64", inner=6),
 }
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates
 IO = {"f64": "float64", "f32": "float32", "tf32": "float32", "bf16": "bfloat16"}
 KERNEL = {"f64": "step_f64_kernel", "f32": "step_lp_kernel<F32>",
           "tf32": "step_lp_kernel<TF32>", "bf16": "step_lp_kernel<BF16>"}
@@ -594,10 +600,17 @@ class ApplyRun:
         kend = d.d - (t if t >= 2 else 0)
         while k < kend:
             fits = k + 2 < d.d and k + 1 < kend
-            tc2 = k >= 4 and d.N >= 256 and r[k] % 8 == 0 and \
-                all(8 <= r[k + i] <= 56 for i in range(3)) if fits else False
-            mma2 = k >= 3 and all(16 <= r[k + i] <= 48 for i in range(3)) \
-                and (d.N >> 2) % 8 == 0 if fits else False
+            if self.compute == "tf32":
+                # TF32 pairs: k >= 5, N >= 512, 2^(k+2) < N, r_k and r_{k+1}
+                # in {16, 32}, r_{k+2} <= 32
+                tc2 = fits and k >= 5 and d.N >= 512 and (1 << (k + 2)) < d.N and \
+                    r[k] in (16, 32) and r[k + 1] in (16, 32) and r[k + 2] <= 32
+                mma2 = False
+            else:
+                tc2 = k >= 4 and d.N >= 256 and r[k] % 8 == 0 and \
+                    all(8 <= r[k + i] <= 56 for i in range(3)) if fits else False
+                mma2 = k >= 3 and all(16 <= r[k + i] <= 48 for i in range(3)) \
+                    and (d.N >> 2) % 8 == 0 if fits else False
             if tc2 or mma2:
                 b += r[k] + r[k + 2]
                 ks.append((k, k + 1))
@@ -609,7 +622,13 @@ class ApplyRun:
         if kend < d.d:
             b += r[kend] + r[d.d]
             ks.append(tuple(range(kend, d.d)))
-        return b * d.N * self.nrhs * 2, ks
+        return b * d.N * self.nrhs * (4 if self.compute == "tf32" else 2), ks
+
+    def tf32_pairs_on(self):
+        """The tuned TF32 plan runs tcgen05 pairs (plan code: fusion bit 0,
+        pairs in bits 1-2)."""
+        p = self.plan if self.plan is not None else 21
+        return self.compute == "tf32" and (p & 1) == 1 and ((p >> 1) & 3) == 2
 
     def roofline(self, mean_s):
         achieved = self.flops / mean_s / 1e9
@@ -631,6 +650,24 @@ class ApplyRun:
                     "hbm_achieved_gbs": gbs, "hbm_peak_gbs": hbm, "hbm_frac": gbs / hbm,
                     "bytes_per_apply": fb, "unfused_bytes_per_apply": self.algorithmic_bytes(),
                     "launches_per_apply": len(plan)}
+        if self.tf32_pairs_on():
+            # the middle steps run as kind::tf32 MMAs: the TF32 tensor peak
+            # (measured BF16 burst x the nominal TF32/BF16 ratio 1.1/2.25)
+            # governs; the HBM figure of the fused launches is kept beside it
+            pk = (measured_peaks().get("bf16_tflops") or 1900.0) * TF32_PER_BF16
+            fb, plan = self.fused_bytes()
+            gbs = fb / mean_s / 1e9
+            hbm = measured_peaks().get("hbm_gbs") or 6800.0
+            return {"bound": "tensor",
+                    "kernel": "whole apply: step_tc2f_kernel (TMA + tcgen05 kind::tf32 pairs), "
+                              "step_f32s / step_lp single steps, head and tail kernels",
+                    "achieved": achieved / 1e3, "peak": pk, "unit": "TFLOP/s",
+                    "frac": achieved / 1e3 / pk, "traffic": None,
+                    "peak_source": "measured BF16 burst (MEASURED_PEAKS.json bf16_tflops) x "
+                                   "1.1/2.25 (nominal dense TF32/BF16)",
+                    "hbm_achieved_gbs": gbs, "hbm_peak_gbs": hbm, "hbm_frac": gbs / hbm,
+                    "bytes_per_apply": fb, "unfused_bytes_per_apply": self.algorithmic_bytes(),
+                    "launches_per_apply": len(plan)}
         if self.compute == "f64":
             peak, src = fp64_peak_gflops(), _peak_source("fp64")
         else:
@@ -646,7 +683,7 @@ class ApplyRun:
         if self.compute in ("bf16", "tf32"):
             pk = measured_peaks().get("bf16_tflops")
             if pk:
-                tc = pk * 1e3 * (0.5 if self.compute == "tf32" else 1.0)
+                tc = pk * 1e3 * (TF32_PER_BF16 if self.compute == "tf32" else 1.0)
                 r["frac_of_tensor_peak"] = achieved / tc
                 r["tensor_peak_gflops"] = tc
         return r
@@ -732,7 +769,7 @@ class BatchedRun:
              "peak_source": "FP32 pipe, 152 SMs x 128 FMA/clk x 2.07 GHz"}
         pk = measured_peaks().get("bf16_tflops")
         if pk and self.compute == "tf32":
-            r["frac_of_tensor_peak"] = achieved / (pk * 1e3 * 0.5)
+            r["frac_of_tensor_peak"] = achieved / (pk * 1e3 * TF32_PER_BF16)
         return r
 
     def config(self):
