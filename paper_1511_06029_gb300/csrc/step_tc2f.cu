@@ -35,10 +35,11 @@
 //               TMEM columns (D1, then D2 of the same chunk): D1 -> T, D2 ->
 //               O -> TMA stores
 //   warp 2      one lane issues the TMA loads into a ring of S stages
-//   warp 3      allocates TMEM; one lane issues the MMAs: MMA1 of chunk n,
-//               then MMA2 of chunk n - 2 (the lag lets the T write of a
-//               chunk overlap the next MMA1)
-//   warps 6-7, 10-15   transpose stage -> Bk (two Bk buffers)
+//   warp 3      allocates TMEM; one lane issues MMA1 of every chunk
+//   warp 12     one lane issues MMA2 of every chunk (two issuing warps: the
+//               two MMAs of different chunks never wait behind each other's
+//               dependencies, and their issue overlaps)
+//   warps 6-7, 10-11, 13-15   transpose stage -> Bk (two Bk buffers)
 // Every wait is bounded (a clock budget, then a shared abort flag: every role
 // leaves its loop, the CTA drains its copies, frees its TMEM and records
 // QTT_ERR_TIMEOUT in this file's status word, read by qtt_sync_status).
@@ -59,11 +60,12 @@ using namespace tcx;
 constexpr int kGroups = 3;
 constexpr int kGroupThreads = 64;
 constexpr int kProducerWarp = 2;
-constexpr int kMmaWarp = 3;
-constexpr int kXWarps = 8;                  // transposer warps 6, 7, 10-15
+constexpr int kMmaWarp = 3;                 // MMA1
+constexpr int kMma2Warp = 12;               // MMA2
+constexpr int kXWarps = 7;                  // transposer warps 6, 7, 10, 11, 13-15
+constexpr int kXItems = 10;                 // ceil(64 / 7) Bk pieces per lane and chunk
 constexpr int kXThreads = 32 * kXWarps;
 constexpr int kThreads = 512;
-constexpr int kLag = 2;                     // MMA2 of chunk n - kLag follows MMA1 of chunk n
 constexpr int kQ = 64;                      // quads per chunk: two runs of 32
 constexpr int kCols = 2 * kQ;               // N of both MMAs
 constexpr uint32_t kTmemCols = 512;         // D of three groups (384), M_k and M_{k+1} (128)
@@ -296,17 +298,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           wait_bar(su32(&B.full[m % S]), (unsigned)(m / S) & 1u, &never);
       }
     }
-  } else if (warp == kMmaWarp) {
+  } else if (warp == kMmaWarp || warp == kMma2Warp) {
     // ------------------------------------------------------------ MMA issue
+    // B operands K-major, 128-byte swizzle: a K step of 8 TF32 moves 32 bytes
+    // inside a 128-byte atom; atoms of 32 K are 128 x 128 bytes apart.  A
+    // operands: TMEM columns kTmemA1/A2 + 8 ks.
     if (lane == 0) {
-      // B operands K-major, 128-byte swizzle: a K step of 8 TF32 moves 32
-      // bytes inside a 128-byte atom; atoms of 32 K are 128 x 128 bytes apart.
-      // A operands: TMEM columns kTmemA1/A2 + 8 ks.
       const uint64_t tK = smem_desc(0, 16, 1024, 2);
-      const int nk1 = Kp1 / 8, nk2 = Kp2 / 8;
-      for (int n = 0;; ++n) {
-        if (n < mine) {
-          // D of this group was last read by the O write of chunk n - 4
+      if (warp == kMmaWarp) {
+        const int nk1 = Kp1 / 8;
+        for (int n = 0; n < mine; ++n) {
+          // D of this group was last read by the O write of chunk n - 3
           const int g = n % kGroups, b = n % kNbk;
           if (!wait_bar(su32(&B.bkready[b]), (unsigned)(n / kNbk) & 1u, abort)) break;
           if (n >= kGroups &&
@@ -317,13 +319,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           const unsigned bkb = base32 + P.bk[b];
           for (int ks = 0; ks < nk1; ++ks) {
             const unsigned bb = bkb + (unsigned)((ks >> 2) * kCols * 128 + (ks & 3) * 32);
-            mma_tf32_ts(d, tmem + kTmemA1 + 8u * (uint32_t)ks, tK | ((bb >> 4) & 0x3FFFu), ks > 0);
+            mma_tf32_ts(d, tmem + kTmemA1 + 8u * (uint32_t)ks, tK | ((bb >> 4) & 0x3FFFu),
+                        ks > 0);
           }
           mma_commit(su32(&B.bkfree[b]));
           mma_commit(su32(&B.d1full[g]));
         }
-        const int m = n - kLag;
-        if (m >= 0 && m < mine) {
+      } else {
+        const int nk2 = Kp2 / 8;
+        for (int m = 0; m < mine; ++m) {
           // D1 of chunk m has been read (T written): D2 overwrites it
           const int gm = m % kGroups;
           if (!wait_bar(su32(&B.tready[gm]), (unsigned)(m / kGroups) & 1u, abort)) break;
@@ -332,24 +336,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           const unsigned tb = base32 + P.to[gm];
           for (int ks = 0; ks < nk2; ++ks) {
             const unsigned bb = tb + (unsigned)((ks >> 2) * kCols * 128 + (ks & 3) * 32);
-            mma_tf32_ts(d, tmem + kTmemA2 + 8u * (uint32_t)ks, tK | ((bb >> 4) & 0x3FFFu), ks > 0);
+            mma_tf32_ts(d, tmem + kTmemA2 + 8u * (uint32_t)ks, tK | ((bb >> 4) & 0x3FFFu),
+                        ks > 0);
           }
           mma_commit(su32(&B.d2full[gm]));
         }
-        if (m >= mine - 1) break;
       }
     }
-  } else if (wq >= 2 || warp >= 12) {
+  } else if (wq >= 2 || warp >= 13) {
     // ------------------------------------------------------------ transposer
     // box h, row R = j1 (2 r0) + kr (kr = 2a + j0), 32 positions x; Bk row
     // n = 64 j1 + 32 h + x, K index kr.  Lane x of transposer warp xw gathers
-    // the four K values of the 16-byte Bk pieces jp = xw, xw + 8, ... (jp =
+    // the four K values of the 16-byte Bk pieces jp = xw, xw + 7, ... (jp =
     // (2 h + j1) npiece + piece): rows R .. R+3 at position x (a warp reads
     // whole 128-byte stage rows), one 16-byte store (eight consecutive Bk
     // rows of a warp land in eight distinct bank groups under the swizzle).
     // R is a multiple of 4, so row R + e has swizzle phase (R & 4) | e.  All
     // loads of a chunk are issued before its stores.
-    const int xw = warp < 12 ? ((warp >> 2) - 1) * 2 + (warp & 1) : warp - 8;  // 0..7
+    const int xw = warp < 12 ? ((warp >> 2) - 1) * 2 + (warp & 1) : warp - 9;  // 0..6
     const int lnp = Kp1 == 64 ? 4 : 3;                  // log2(npiece), npiece = Kp1 / 4
     const int njp = 4 << lnp;
     const unsigned xc = (unsigned)lane >> 2;
@@ -366,9 +370,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (n >= kNbk && !wait_bar(su32(&B.bkfree[b]), (unsigned)(n / kNbk - 1) & 1u, abort)) break;
       const unsigned char *stg = base + P.s0 + (unsigned)st * P.stage + ldx;
       unsigned char *bk = base + P.bk[b] + stx;
-      float4 v[8];
+      float4 v[kXItems];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
+      for (int t = 0; t < kXItems; ++t) {
         const int jp = xw + kXWarps * t;
         if (jp < njp) {
           const unsigned hj = (unsigned)jp >> lnp, pc = (unsigned)jp & ((1u << lnp) - 1u);
@@ -382,7 +386,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
+      for (int t = 0; t < kXItems; ++t) {
         const int jp = xw + kXWarps * t;
         if (jp < njp) {
           // n = 64 j1 + 32 h + x: (pc / 8) 16384 + j1 8192 + h 4096 + x 128 + swizzled piece
