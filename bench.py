@@ -601,10 +601,10 @@ class ApplyRun:
         while k < kend:
             fits = k + 2 < d.d and k + 1 < kend
             if self.compute == "tf32":
-                # TF32 pairs: k >= 5, N >= 512, 2^(k+2) < N, r_k and r_{k+1}
-                # in {16, 32}, r_{k+2} <= 32
-                tc2 = fits and k >= 5 and d.N >= 512 and (1 << (k + 2)) < d.N and \
-                    r[k] in (16, 32) and r[k + 1] in (16, 32) and r[k + 2] <= 32
+                # TF32 pairs: k >= 3, N >= 1024, 2^(k+2) < N, r_k and r_{k+1}
+                # in {8, 16, 32}, r_{k+2} <= 32
+                tc2 = fits and k >= 3 and d.N >= 1024 and (1 << (k + 2)) < d.N and \
+                    r[k] in (8, 16, 32) and r[k + 1] in (8, 16, 32) and r[k + 2] <= 32
                 mma2 = False
             else:
                 tc2 = k >= 4 and d.N >= 256 and r[k] % 8 == 0 and \

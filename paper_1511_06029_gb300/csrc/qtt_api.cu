@@ -434,7 +434,7 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
       // TF32: steps k and k+1 on the tcgen05 tensor cores (kind::tf32)
       if (compute == QTT_TF32 && fuse && pl.pairs == 2 && A->mma_tf32 && use_tensor_cores() &&
           use_tcgen05() && k >= 1 && k + 2 < d && k + 1 < kend && A->toff[k] >= 0 &&
-          A->toff[k + 1] >= 0 &&
+          A->t2off[k + 1] >= 0 &&
           tc2f_steps_eligible(k, A->ranks[k], A->ranks[k + 1], A->ranks[k + 2], N)) {
         StepTF2 t;
         t.in = reinterpret_cast<const float *>(buf[src]);
@@ -442,7 +442,7 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
         t.out = reinterpret_cast<float *>(buf[src ^ 1]);
         t.out_rhs_stride = (int64_t)A->ranks[k + 2] * N;
         t.A1 = A->mma_tf32 + A->toff[k];
-        t.A2 = A->mma_tf32 + A->toff[k + 1];
+        t.A2 = A->mma_tf32 + A->t2off[k + 1];
         t.k = k;
         t.r0 = A->ranks[k];
         t.r1 = A->ranks[k + 1];
@@ -774,11 +774,14 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores
       // tensor-core layout [128][2 r_k], rows 2b+i, columns 2a+j (the same
       // TF32 values as the packed copy)
       A->toff.assign(d, -1);
+      A->t2off.assign(d, -1);
       int64_t to = 0;
       for (int k = 0; k < d; ++k) {
-        if ((ranks[k] != 16 && ranks[k] != 32) || ranks[k + 1] > 32) continue;
+        if ((ranks[k] != 8 && ranks[k] != 16 && ranks[k] != 32) || ranks[k + 1] > 32) continue;
         A->toff[k] = to;
         to += (int64_t)128 * 2 * ranks[k];
+        A->t2off[k] = to;
+        to += (int64_t)64 * 2 * ranks[k];
       }
       if (e2 == cudaSuccess && to > 0) {
         std::vector<float> m((size_t)to, 0.0f);
@@ -787,12 +790,16 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores
           const int ra = ranks[k], rb = ranks[k + 1], K = 2 * ra;
           const double *G = cores + A->off[k];
           float *M = m.data() + A->toff[k];
+          float *M2 = m.data() + A->t2off[k];
           for (int a = 0; a < ra; ++a)
             for (int i = 0; i < 2; ++i)
               for (int j = 0; j < 2; ++j)
-                for (int b = 0; b < rb; ++b)
-                  M[(size_t)(2 * b + i) * K + 2 * a + j] =
+                for (int b = 0; b < rb; ++b) {
+                  const float v =
                       host_tf32_rne((float)G[(((size_t)a * 2 + i) * 2 + j) * rb + b]);
+                  M[(size_t)(2 * b + i) * K + 2 * a + j] = v;
+                  M2[(size_t)(2 * b + i) * K + j * ra + a] = v;
+                }
         }
         e2 = upload(reinterpret_cast<void **>(&A->mma_tf32), m.data(), m.size() * sizeof(float));
       }

@@ -107,12 +107,13 @@ struct qtt_op {
   __nv_bfloat16 *mma_bf16 = nullptr;
   std::vector<int64_t> moff;
   std::vector<int> mp, kp;
-  // TF32 tensor-core copy for the tcgen05 pair kernel: core k as [128][2 r_k]
-  // (rows 2b+i, zero past 2 r_{k+1}; columns 2a+j), TF32-rounded, at element
-  // offset toff[k]; only for r_k in {16, 32} and r_{k+1} <= 32 (toff[k] = -1
-  // otherwise).
+  // TF32 tensor-core copies for the tcgen05 pair kernel, TF32-rounded: core k
+  // as the first step of a pair, [128][2 r_k] (rows 2b+i, zero past
+  // 2 r_{k+1}; columns 2a+j) at element offset toff[k], and as the second,
+  // [64][2 r_k] (rows 2b+i, zero past 2 r_{k+1}; columns j r_k + a) at
+  // t2off[k]; only for r_k in {8, 16, 32} and r_{k+1} <= 32 (-1 otherwise).
   float *mma_tf32 = nullptr;
-  std::vector<int64_t> toff;
+  std::vector<int64_t> toff, t2off;
   // Reduced-precision packing [a][j][b padded to rpad[k+1]][i]:
   std::vector<int> rpad;        // padded output rank per core (index k+1)
   std::vector<int64_t> offlp;   // element offset of core k

@@ -51,17 +51,18 @@ constexpr int kTc2MaxRank = 56;
 bool tc2_steps_eligible(int k, int r0, int r1, int r2, int64_t N);
 cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st);
 // Two consecutive TF32 steps on the tcgen05 tensor cores (step_tc2f.cu,
-// kind::tf32): FP32 planar buffers holding TF32-rounded values; cores as
-// [128][2 r_in] TF32 matrices (rows 2 r_out + i, columns 2 a + j, rows past
-// 2 r_out zero).  cudaErrorNotSupported (nothing launched) when the shapes
-// do not fit.
+// kind::tf32): FP32 planar buffers holding TF32-rounded values.  Cores as
+// TF32 matrices: A1 = M_k as [128][2 r_k] (rows 2b + i, columns 2a + j, rows
+// past 2 r_{k+1} zero), A2 = M_{k+1} as [64][2 r_{k+1}] (rows 2c + i,
+// columns j r_{k+1} + b, rows past 2 r_{k+2} zero).  cudaErrorNotSupported
+// (nothing launched) when the shapes do not fit.
 struct StepTF2 {
   const float *in;           // y_k, planar [rhs][a][position]
   int64_t in_rhs_stride;
   float *out;                // y_{k+2}
   int64_t out_rhs_stride;
-  const float *A1;           // M_k as [128][2 r0]
-  const float *A2;           // M_{k+1} as [128][2 r1]
+  const float *A1;           // M_k as [128][2 r0], columns 2a + j
+  const float *A2;           // M_{k+1} as [64][2 r1], columns j r1 + b
   int k, r0, r1, r2;
   int64_t N, nrhs;
 };

@@ -122,6 +122,10 @@ __device__ __forceinline__ void bulk_commit() {
 __device__ __forceinline__ void bulk_wait_read0() {
   asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
 }
+// All but the most recent bulk group have read their shared memory.
+__device__ __forceinline__ void bulk_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+}
 // Barrier of the epilogue warps that also ORs a flag over them: the abort
 // decision stays uniform, so no epilogue thread is left at a barrier.
 // (Named barrier 1 + g belongs to epilogue group g of NT threads.)

@@ -6,9 +6,11 @@ operands are TF32 (unit roundoff 2^-11) and every stored intermediate is
 rounded to TF32, so the relative error is at most about sqrt(d) 2^-11 --
 the launch count shows that the pairs ran (fewer launches than the plan
 without pairs), and the result agrees with the FP32-pipe TF32 sweep within
-the same bound.  The cases cover ranks 16 and 32 in both MMAs, an output
-rank that is not a multiple of anything (5), a single chunk per CTA and
-many chunks per CTA (the stage ring and both epilogue groups wrap)."""
+the same bound.  The cases cover ranks 8, 16 and 32 in both MMAs, pairs
+starting at bits 3 and 4 (unswizzled boxes over several high-bit rows) and
+at 5 and above, an output rank that is not a multiple of anything (5), a
+single chunk per CTA and many chunks per CTA (the stage ring and both
+epilogue groups wrap)."""
 import math
 
 import numpy as np
@@ -27,6 +29,7 @@ CASES = [
     ("profile", 16, 32, 3),
     ("ranks", [1, 2, 4, 8, 16, 16, 32, 5, 4, 2, 1], None, 2),
     ("ranks", [1, 2, 4, 8, 16, 32, 16, 32, 16, 32, 8, 4, 2, 1], None, 1),
+    ("ranks", [1, 2, 4, 8, 8, 16, 8, 32, 8, 4, 2, 1], None, 2),
 ]
 
 
@@ -103,4 +106,44 @@ def test_tf32_pairs_linearity(qtt):
     y1, _ = _apply(qtt, op, x, PLAN_PAIRS)
     y2, _ = _apply(qtt, op, 2 * x, PLAN_PAIRS)
     assert np.array_equal(y2, 2 * y1)
+    op.close()
+
+
+def _sparse_sign_cores(ranks, heavy, seed):
+    """Cores with entries in {-1, 0, 1}: for each output (b, i), one nonzero
+    (a, j) at a random place (any a, so off the rank diagonal), or three for
+    the cores in `heavy`.  |y| grows at most 3x per heavy core and not at all
+    elsewhere, so with x in {-1, 0, 1} every intermediate is an integer below
+    3^len(heavy) -- exact in TF32 (11 significant bits) -- and every FP32 sum
+    of such integers is exact."""
+    rng = np.random.default_rng(seed)
+    cores = []
+    for k in range(len(ranks) - 1):
+        ra, rb = ranks[k], ranks[k + 1]
+        G = np.zeros((ra, 2, 2, rb))
+        for b in range(rb):
+            for i in range(2):
+                for _ in range(3 if k in heavy else 1):
+                    G[rng.integers(ra), i, rng.integers(2), b] = rng.choice([-1.0, 1.0])
+        cores.append(G)
+    return inputs.QTTData(list(ranks), cores, {"kind": "sparse-sign"})
+
+
+def test_tf32_pairs_integer_exact(qtt):
+    """The pair kernel reproduces the oracle bit for bit when every value it
+    rounds is a small integer: d = 12, ranks up to 32 (pairs (5, 6) and
+    (7, 8) on the tensor cores), three signed nonzeros per output in those
+    four cores."""
+    import torch
+    ranks = inputs.rank_profile(12, 32)
+    data = _sparse_sign_cores(ranks, heavy={5, 6, 7, 8}, seed=3)
+    x = np.random.default_rng(4).integers(-1, 2, size=(3, data.N)).astype(np.float64)
+    ref = oracle.apply(data, x)
+    assert np.abs(ref).max() < 2 ** 11 and np.abs(ref).max() >= 2
+    op = qtt.Operator(data, packs=("tf32",))
+    xd = torch.from_numpy(x.astype(np.float32)).cuda()
+    y_tc, n_tc = _apply(qtt, op, xd, PLAN_PAIRS)
+    _, n_fp = _apply(qtt, op, xd, PLAN_NO_PAIRS)
+    assert n_tc < n_fp
+    assert np.array_equal(y_tc, ref)
     op.close()
