@@ -602,9 +602,9 @@ class ApplyRun:
             fits = k + 2 < d.d and k + 1 < kend
             if self.compute == "tf32":
                 # TF32 pairs: k >= 3, N >= 1024, 2^(k+2) < N, r_k and r_{k+1}
-                # in {8, 16, 32}, r_{k+2} <= 32
+                # in 8..32, r_{k+2} <= 32
                 tc2 = fits and k >= 3 and d.N >= 1024 and (1 << (k + 2)) < d.N and \
-                    r[k] in (8, 16, 32) and r[k + 1] in (8, 16, 32) and r[k + 2] <= 32
+                    8 <= r[k] <= 32 and 8 <= r[k + 1] <= 32 and r[k + 2] <= 32
                 mma2 = False
             else:
                 tc2 = k >= 4 and d.N >= 256 and r[k] % 8 == 0 and \
@@ -763,7 +763,11 @@ class BatchedRun:
 
     def roofline(self, mean_s):
         achieved = self.flops / mean_s / 1e9
-        r = {"bound": "alu", "kernel": f"batch_kernel<{self.variant % 100}>", "achieved": achieved,
+        kern = f"batch_kernel<{self.variant % 100}>"
+        if self.info.get("tensor_ops"):
+            kern += (f" waves + {self.info['tensor_ops']} operators on step_tc2f_kernel "
+                     "(tcgen05 TF32 pairs)")
+        r = {"bound": "alu", "kernel": kern, "achieved": achieved,
              "peak": fp32_peak_gflops(), "unit": "GFLOP/s",
              "frac": achieved / fp32_peak_gflops(), "traffic": None,
              "peak_source": "FP32 pipe, 152 SMs x 128 FMA/clk x 2.07 GHz"}
@@ -779,6 +783,7 @@ class BatchedRun:
                 "total_rhs": sum(it["nrhs"] for it in self.items),
                 "flops_per_step_per_gpu": self.flops, "compute": self.compute,
                 "waves": self.info["waves"], "grid": self.info["grid"],
+                "tensor_core_operators": self.info.get("tensor_ops", 0),
                 "autotuned_pairs_per_lane": self.variant % 100,
                 "autotuned_chunks_per_item": (self.variant // 100) % 100,
                 "autotuned_ring_depth": self.variant // 10000,

@@ -433,6 +433,9 @@ struct qtt_batch {
   cudaGraphExec_t exec = nullptr;
   double flops = 0.0;
   int grid = 0;
+  // TF32 batches: operators whose apply runs step pairs on the tcgen05 tensor
+  // cores go through that apply after the waves, not into a wave
+  std::vector<int> tc_ops;
 };
 
 namespace qtt {
@@ -479,8 +482,14 @@ qtt_status build_plan(qtt_batch *B, cudaStream_t st) {
     for (int k = 0; k <= A->d; ++k) r = std::max(r, A->ranks[k]);
     return r <= 16 ? 0 : r <= 24 ? 1 : r <= 32 ? 2 : 3;
   };
-  std::vector<int> order(B->ops.size());
-  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::vector<int> order;
+  B->tc_ops.clear();
+  for (size_t i = 0; i < B->ops.size(); ++i) {
+    if (B->compute == QTT_TF32 && tf32_tc_pairs(B->ops[i]) > 0)
+      B->tc_ops.push_back((int)i);
+    else
+      order.push_back((int)i);
+  }
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return rank_class(B->ops[a]) < rank_class(B->ops[b]);
   });
@@ -775,6 +784,11 @@ qtt_status qtt_batch_run(qtt_batch *B, void *stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaGraphLaunch(B->exec, st);
   if (e != cudaSuccess) return cuda_fail(e, "qtt_batch_run: graph launch");
+  for (int i : B->tc_ops) {
+    const qtt_status s = apply_lp(B->ops[i], QTT_TF32, B->x[i], QTT_F32, B->y[i], QTT_F32,
+                                  B->nrhs[i], B->ld[i], st, LpEpilogue{});
+    if (s != QTT_OK) return s;
+  }
   // the run reads every operator and the batch's own buffers
   for (const qtt_op *A : B->ops) note_use(A, st);
   if (!B->last_run) {
@@ -875,6 +889,12 @@ qtt_status qtt_batch_autotune(qtt_batch *B, int reps, void *stream, int *chosen,
   if (chosen) *chosen = best;
   if (seconds_per_run) *seconds_per_run = best_t;
   return s;
+}
+
+qtt_status qtt_batch_tensor_ops(const qtt_batch *B, int *count) {
+  if (!B || !count) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_tensor_ops: no batch");
+  *count = (int)B->tc_ops.size();
+  return QTT_OK;
 }
 
 qtt_status qtt_batch_info(const qtt_batch *B, int *waves, int *variant, int *grid,

@@ -354,8 +354,34 @@ static bool use_tcgen05() {
   return on;
 }
 
+// Steps k and k+1 of a TF32 apply run as one tcgen05 pair (the middle
+// steps k0 .. kend-1 are the ones outside the head and tail kernels).
+static bool tf32_pair_at(const qtt_op *A, int k, int kend, int64_t N) {
+  const int d = A->d;
+  return A->mma_tf32 && use_tensor_cores() && use_tcgen05() && k >= 1 && k + 2 < d &&
+         k + 1 < kend && A->toff[k] >= 0 && A->t2off[k + 1] >= 0 &&
+         tc2f_steps_eligible(k, A->ranks[k], A->ranks[k + 1], A->ranks[k + 2], N);
+}
+
 static size_t dtype_size(qtt_dtype t) {
   return t == QTT_F64 ? 8 : (t == QTT_BF16 ? 2 : 4);
+}
+
+int tf32_tc_pairs(const qtt_op *A) {
+  const ApplyPlan &pl = A->plan[QTT_TF32];
+  if (!A->mtf32 || !A->mma_tf32 || !use_fusion() || !pl.fusion || pl.pairs != 2) return 0;
+  const int d = A->d;
+  const int64_t N = (int64_t)1 << d;
+  const int hm = !A->head[1].empty() ? head_steps(A->ranks.data(), d) : 0;
+  const int tm = !A->tail[1].empty() ? tail_steps(A->ranks.data(), d, hm) : 0;
+  const int kend = d - tm;
+  int n = 0;
+  for (int k = hm; k < kend; ++k)
+    if (tf32_pair_at(A, k, kend, N)) {
+      ++n;
+      ++k;
+    }
+  return n;
 }
 
 qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype xt, void *y,
@@ -432,10 +458,7 @@ qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype
     }
     for (int k = k0; k < kend; ++k) {
       // TF32: steps k and k+1 on the tcgen05 tensor cores (kind::tf32)
-      if (compute == QTT_TF32 && fuse && pl.pairs == 2 && A->mma_tf32 && use_tensor_cores() &&
-          use_tcgen05() && k >= 1 && k + 2 < d && k + 1 < kend && A->toff[k] >= 0 &&
-          A->t2off[k + 1] >= 0 &&
-          tc2f_steps_eligible(k, A->ranks[k], A->ranks[k + 1], A->ranks[k + 2], N)) {
+      if (compute == QTT_TF32 && fuse && pl.pairs == 2 && tf32_pair_at(A, k, kend, N)) {
         StepTF2 t;
         t.in = reinterpret_cast<const float *>(buf[src]);
         t.in_rhs_stride = (int64_t)A->ranks[k] * N;
@@ -776,18 +799,23 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores
       A->toff.assign(d, -1);
       A->t2off.assign(d, -1);
       int64_t to = 0;
+      // first-step copy [128][K1], K1 = 2 r_k rounded up to 8, columns 2a + j;
+      // second-step copy [64][K2], K2 = 2 r_k rounded up to 4 per half,
+      // columns j (r_k rounded up to 4) + a; padding zero
       for (int k = 0; k < d; ++k) {
-        if ((ranks[k] != 8 && ranks[k] != 16 && ranks[k] != 32) || ranks[k + 1] > 32) continue;
+        if (ranks[k] < 8 || ranks[k] > 32 || ranks[k + 1] > 32) continue;
+        const int k1 = (2 * ranks[k] + 7) / 8 * 8, k2 = 2 * ((ranks[k] + 3) / 4 * 4);
         A->toff[k] = to;
-        to += (int64_t)128 * 2 * ranks[k];
+        to += (int64_t)128 * k1;
         A->t2off[k] = to;
-        to += (int64_t)64 * 2 * ranks[k];
+        to += (int64_t)64 * k2;
       }
       if (e2 == cudaSuccess && to > 0) {
         std::vector<float> m((size_t)to, 0.0f);
         for (int k = 0; k < d; ++k) {
           if (A->toff[k] < 0) continue;
-          const int ra = ranks[k], rb = ranks[k + 1], K = 2 * ra;
+          const int ra = ranks[k], rb = ranks[k + 1];
+          const int k1 = (2 * ra + 7) / 8 * 8, rap = (ra + 3) / 4 * 4, k2 = 2 * rap;
           const double *G = cores + A->off[k];
           float *M = m.data() + A->toff[k];
           float *M2 = m.data() + A->t2off[k];
@@ -797,8 +825,8 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores
                 for (int b = 0; b < rb; ++b) {
                   const float v =
                       host_tf32_rne((float)G[(((size_t)a * 2 + i) * 2 + j) * rb + b]);
-                  M[(size_t)(2 * b + i) * K + 2 * a + j] = v;
-                  M2[(size_t)(2 * b + i) * K + j * ra + a] = v;
+                  M[(size_t)(2 * b + i) * k1 + 2 * a + j] = v;
+                  M2[(size_t)(2 * b + i) * k2 + j * rap + a] = v;
                 }
         }
         e2 = upload(reinterpret_cast<void **>(&A->mma_tf32), m.data(), m.size() * sizeof(float));

@@ -108,10 +108,11 @@ struct qtt_op {
   std::vector<int64_t> moff;
   std::vector<int> mp, kp;
   // TF32 tensor-core copies for the tcgen05 pair kernel, TF32-rounded: core k
-  // as the first step of a pair, [128][2 r_k] (rows 2b+i, zero past
-  // 2 r_{k+1}; columns 2a+j) at element offset toff[k], and as the second,
-  // [64][2 r_k] (rows 2b+i, zero past 2 r_{k+1}; columns j r_k + a) at
-  // t2off[k]; only for r_k in {8, 16, 32} and r_{k+1} <= 32 (-1 otherwise).
+  // as the first step of a pair, [128][2 r_k rounded up to 8] (rows 2b+i,
+  // zero past 2 r_{k+1}; columns 2a+j) at element offset toff[k], and as the
+  // second, [64][2 r'] with r' = r_k rounded up to 4 (rows 2b+i, zero past
+  // 2 r_{k+1}; columns j r' + a) at t2off[k]; only for 8 <= r_k <= 32 and
+  // r_{k+1} <= 32 (-1 otherwise).
   float *mma_tf32 = nullptr;
   std::vector<int64_t> toff, t2off;
   // Reduced-precision packing [a][j][b padded to rpad[k+1]][i]:
@@ -200,6 +201,10 @@ struct LpEpilogue {
 qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype xt, void *y,
                     qtt_dtype yt, int64_t nrhs, int64_t ld, cudaStream_t st,
                     const LpEpilogue &epi);
+// Number of step pairs a TF32 apply of A runs on the tcgen05 tensor cores
+// under its current plan (0 when none: no TF32 tensor-core copy, fusion or
+// pairs off, or no eligible pair).
+int tf32_tc_pairs(const qtt_op *A);
 
 // FP64 apply of A to nrhs vectors (ld = leading dimension of x and y) with
 // an optional epilogue; scratch from the pool.  Host-side, asynchronous.

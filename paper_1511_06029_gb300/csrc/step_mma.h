@@ -52,17 +52,18 @@ bool tc2_steps_eligible(int k, int r0, int r1, int r2, int64_t N);
 cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st);
 // Two consecutive TF32 steps on the tcgen05 tensor cores (step_tc2f.cu,
 // kind::tf32): FP32 planar buffers holding TF32-rounded values.  Cores as
-// TF32 matrices: A1 = M_k as [128][2 r_k] (rows 2b + i, columns 2a + j, rows
-// past 2 r_{k+1} zero), A2 = M_{k+1} as [64][2 r_{k+1}] (rows 2c + i,
-// columns j r_{k+1} + b, rows past 2 r_{k+2} zero).  cudaErrorNotSupported
-// (nothing launched) when the shapes do not fit.
+// TF32 matrices: A1 = M_k as [128][K1] (K1 = 2 r_k rounded up to 8; rows
+// 2b + i, columns 2a + j; rows past 2 r_{k+1} zero), A2 = M_{k+1} as
+// [64][2 r'] (r' = r_{k+1} rounded up to 4; rows 2c + i, columns j r' + b;
+// rows past 2 r_{k+2} zero).  cudaErrorNotSupported (nothing launched) when
+// the shapes do not fit.
 struct StepTF2 {
   const float *in;           // y_k, planar [rhs][a][position]
   int64_t in_rhs_stride;
   float *out;                // y_{k+2}
   int64_t out_rhs_stride;
-  const float *A1;           // M_k as [128][2 r0], columns 2a + j
-  const float *A2;           // M_{k+1} as [64][2 r1], columns j r1 + b
+  const float *A1;           // M_k as [128][K1], columns 2a + j
+  const float *A2;           // M_{k+1} as [64][2 r'], columns j r' + b
   int k, r0, r1, r2;
   int64_t N, nrhs;
 };

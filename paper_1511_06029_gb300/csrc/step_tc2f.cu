@@ -26,17 +26,20 @@
 //   D1^T     (TMEM) lane m, column 2b + i_k
 //   T        (shared memory, A of MMA2, D1 rounded to TF32 -- where the
 //            unfused sweep rounds the stored y_{k+1}): row
-//            n = 64 i_k + 32 h + x, K = j_{k+1} r_{k+1} + b, so that each
+//            n = 64 i_k + 32 h + x, K = j_{k+1} r1p + b, so that each
 //            thread stores runs of four consecutive K (16 bytes)
 //   B2       (shared memory, B of MMA2): M_{k+1} as rows 2c + i_{k+1},
-//            K = j_{k+1} r_{k+1} + b
+//            K = j_{k+1} r1p + b
 //   D2^T     (TMEM) lane n, column 2c + i_{k+1}
 //   y_{k+2}  (HBM) D2^T rounded to TF32, written by the thread of lane n:
 //            for each (c, i_{k+1}) the 32 lanes of a warp store 32
 //            consecutive positions of one plane (128 bytes)
-// Ranks 8, 16 or 32 in and between the steps (K of both MMAs a multiple of
-// 16), r_{k+2} <= 32.  MMA1 is M = 128, N = 2 r_{k+1}, K = 2 r_k; MMA2 is M = 128,
-// N = 2 r_{k+2} rounded up to 16, K = 2 r_{k+1}; K = 8 per instruction.
+// Ranks 8 to 32 in and between the steps, r_{k+2} <= 32.  MMA1 is M = 128,
+// N = 2 r_{k+1} and K = 2 r_k, MMA2 is M = 128, N = 2 r_{k+2} and
+// K = 2 r1p (r1p = r_{k+1} rounded up to 4, so that T's two halves start on
+// 16-byte pieces); N is rounded up to 16 and K to 8 (the MMA's multiples),
+// the padding rows and columns of the core tiles are zero and the padding
+// columns of X are written as zeros.  K = 8 per instruction.
 //
 // Warp roles (a warp reaches the TMEM lanes 32 (w mod 4) .. + 31), connected
 // by mbarriers:
@@ -181,31 +184,34 @@ struct Bars {
 };
 static_assert(sizeof(Bars) <= kBarBytes, "mbarrier block");
 
-// Shared-memory plan (byte offsets from a 1024-aligned base): B1 (2 r1 rows x
-// Kp1) and B2 (N2 rows x Kp2) K-major, per group a T buffer (128 rows x Kp2,
+// Shared-memory plan (byte offsets from a 1024-aligned base): B1 (N1 rows x
+// K1) and B2 (N2 rows x K2) K-major, per group a T buffer (128 rows x K2,
 // K-major), the stage ring (two boxes of 4 r0 rows of 128 bytes).
 struct PlanF {
-  unsigned b1, b2, t[kGroups], box, s0, stage, end;
-  int n1, n2;
+  unsigned b1, b2, t[kGroups], box, boxs, s0, stage, end;
+  int n1, n2, k1, r1p, k2;
 };
 __host__ __device__ inline unsigned kmaj_bytes(int rows, int Kp) {
   return (unsigned)((Kp + 31) / 32) * (unsigned)rows * 128u;
 }
 __host__ __device__ inline PlanF make_plan_f(const StepTF2 &s, int S) {
   PlanF p;
-  const int Kp1 = 2 * s.r0, Kp2 = 2 * s.r1;
-  p.n1 = 2 * s.r1;
+  p.k1 = (2 * s.r0 + 7) / 8 * 8;
+  p.r1p = (s.r1 + 3) / 4 * 4;
+  p.k2 = 2 * p.r1p;
+  p.n1 = (2 * s.r1 + 15) / 16 * 16;
   p.n2 = (2 * s.r2 + 15) / 16 * 16;
   p.b1 = up1k(kBarBytes);
-  p.b2 = up1k(p.b1 + kmaj_bytes(p.n1, Kp1));
-  unsigned o = up1k(p.b2 + kmaj_bytes(p.n2, Kp2));
+  p.b2 = up1k(p.b1 + kmaj_bytes(p.n1, p.k1));
+  unsigned o = up1k(p.b2 + kmaj_bytes(p.n2, p.k2));
   for (int g = 0; g < kGroups; ++g) {
     p.t[g] = o;
-    o = up1k(o + kmaj_bytes(128, Kp2));
+    o = up1k(o + kmaj_bytes(128, p.k2));
   }
   p.s0 = o;
   p.box = (unsigned)(4 * s.r0) * 128u;
-  p.stage = up1k(2 * p.box);
+  p.boxs = up1k(p.box);
+  p.stage = 2 * p.boxs;
   p.end = p.s0 + (unsigned)S * p.stage;
   return p;
 }
@@ -219,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const unsigned base32 = su32(base);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int wq = warp & 3;
-  const int Kp1 = 2 * s.r0, Kp2 = 2 * s.r1;
+  const int Kp1 = P.k1, Kp2 = P.k2;  // padded K of the two MMAs
 
   if (warp == kMma1Warp) {
     asm volatile(
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int64_t q = cw.w * kQ + 32 * h;
-          tma_load5(base32 + P.s0 + (unsigned)st * P.stage + (unsigned)h * P.box, &tin,
+          tma_load5(base32 + P.s0 + (unsigned)st * P.stage + (unsigned)h * P.boxs, &tin,
                     (int)(q & lowmask), 0, (int)(cw.c * s.r0), 0, (int)(q >> s.k), fb);
         }
         if (++st == S) {
@@ -358,15 +364,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ stage -> X
     // warp q = w - 4 owns TMEM lanes 32 q .. + 31 = positions (j1, h) =
     // (q / 2, q % 2), t = lane: column kr of X is row R = j1 2 r0 + kr of box
-    // h at position t.  k >= 5: a warp reads whole 128-byte rows; 2 r0 is a
-    // multiple of 8, so row R has swizzle phase kr % 8.  k = 3, 4: position
-    // t is (hi, x) = (t / 2^k, t % 2^k), at ((hi 4 r0 + R) 2^k + x) floats.
+    // h at position t (columns 2 r0 .. 63 are written as zeros).  k >= 5: a
+    // warp reads whole 128-byte rows, row R at swizzle phase R % 8.
+    // k = 3, 4: position t is (hi, x) = (t / 2^k, t % 2^k), at
+    // ((hi 4 r0 + R) 2^k + x) floats.
     const int j1 = wq >> 1, h = wq & 1;
+    const int kin = 2 * s.r0;
     const bool swz = s.k >= 5;
     const unsigned xc = (unsigned)lane >> 2, xl = (unsigned)(lane & 3) * 4u;
+    const unsigned rot = (unsigned)(j1 * kin);
     unsigned pre[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) pre[c] = ((xc ^ (unsigned)c) << 4) + xl;
+    for (int c = 0; c < 8; ++c) pre[c] = ((xc ^ (((unsigned)c + rot) & 7u)) << 4) + xl;
     const unsigned rstride = 4u << s.k;  // k = 3, 4: bytes per row
     const unsigned plain =
         ((((unsigned)lane >> s.k) * 4u * (unsigned)s.r0) << s.k) * 4u +
@@ -378,25 +387,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int b = n % kNx;
       if (!wait_bar(su32(&B.full[st]), ph, abort)) break;
       if (n >= kNx && !wait_bar(su32(&B.xfree[b]), (unsigned)(n / kNx - 1) & 1u, abort)) break;
-      const unsigned char *box = base + P.s0 + (unsigned)st * P.stage + (unsigned)h * P.box;
+      const unsigned char *box = base + P.s0 + (unsigned)st * P.stage + (unsigned)h * P.boxs;
       float v[64];
       if (swz) {
-        const unsigned char *rows = box + (unsigned)(j1 * Kp1) * 128u;
+        const unsigned char *rows = box + rot * 128u;
 #pragma unroll
         for (int kr = 0; kr < 64; ++kr)
-          if (kr < Kp1) v[kr] = *reinterpret_cast<const float *>(rows + kr * 128 + pre[kr & 7]);
+          v[kr] = kr < kin ? *reinterpret_cast<const float *>(rows + kr * 128 + pre[kr & 7]) : 0.f;
       } else {
-        const unsigned char *rows = box + plain + (unsigned)(j1 * Kp1) * rstride;
+        const unsigned char *rows = box + plain + rot * rstride;
 #pragma unroll
         for (int kr = 0; kr < 64; ++kr)
-          if (kr < Kp1) v[kr] = *reinterpret_cast<const float *>(rows + (unsigned)kr * rstride);
+          v[kr] = kr < kin ? *reinterpret_cast<const float *>(rows + (unsigned)kr * rstride) : 0.f;
       }
       mbar_arrive(su32(&B.empty[st]));  // the stage has been read
-      if (Kp1 == 16) {
+      if (Kp1 <= 16) {
         tmem_st16(tl + (uint32_t)(b * 64), v);
       } else {
         tmem_st32(tl + (uint32_t)(b * 64), v);
-        if (Kp1 == 64) tmem_st32(tl + (uint32_t)(b * 64 + 32), v + 32);
+        if (Kp1 > 32) tmem_st32(tl + (uint32_t)(b * 64 + 32), v + 32);
       }
       asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
       tc_fence_before();
@@ -417,9 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t d2 = d1 + 64u;
     const unsigned x7 = (unsigned)lane & 7u;
     unsigned char *T = base + P.t[g];
-    // T: K = j1 r1 + 4p lies in atom (j1 r1) / 32, piece ((j1 r1) / 4 + p) % 8
-    const unsigned tatom = (unsigned)(qhi * s.r1 >> 5) * 16384u;
-    const unsigned tp0 = (unsigned)(qhi * s.r1 >> 2) & 7u;
+    const unsigned tk0 = (unsigned)(qhi * P.r1p);  // this thread's half of T's K
     const int64_t bit1 = (int64_t)1 << (s.k + 1);
     ChunkWalk cw(blockIdx.x + (int64_t)g * NG, (int64_t)kGroups * NG, cpr);
     for (int n = g; n < mine; n += kGroups, cw.next()) {
@@ -427,24 +434,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (epi_any<kGroupThreads>(!wait_bar(su32(&B.d1full[g]), par, abort), g)) break;
       tc_fence_after();
       {
-        // D1^T column 2b + i -> T row 64 i + 32 h + x, K = j1 r1 + b: four
+        // D1^T column 2b + i -> T row 64 i + 32 h + x, K = j1 r1p + b: four
         // consecutive b per 16-byte piece, at (K / 32) 16384 + row 128 +
-        // ((K / 4 % 8) ^ (row % 8)) 16.  T was last read by MMA2 of chunk
+        // ((K / 4 % 8) ^ (row % 8)) 16 (columns b >= r1 of D1^T are zero: the
+        // core tile's padding rows).  T was last read by MMA2 of chunk
         // n - 2, complete before this group's y write of that chunk began.
         float v[64];
         tmem_ld64(d1, v);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-          unsigned char *trow = T + (unsigned)(64 * i + 32 * qh + lane) * 128u + tatom;
+          unsigned char *trow = T + (unsigned)(64 * i + 32 * qh + lane) * 128u;
 #pragma unroll
           for (int p = 0; p < 8; ++p) {
-            if (4 * p < s.r1) {
+            if (4 * p < P.r1p) {
+              const unsigned kk = tk0 + 4u * (unsigned)p;
               float4 w;
               w.x = tf32_rne(v[8 * p + i]);
               w.y = tf32_rne(v[8 * p + 2 + i]);
               w.z = tf32_rne(v[8 * p + 4 + i]);
               w.w = tf32_rne(v[8 * p + 6 + i]);
-              *reinterpret_cast<float4 *>(trow + ((((tp0 + (unsigned)p) & 7u) ^ x7) << 4)) = w;
+              *reinterpret_cast<float4 *>(trow + (kk >> 5) * 16384u +
+                                          ((((kk >> 2) & 7u) ^ x7) << 4)) = w;
             }
           }
         }
@@ -523,11 +533,10 @@ int stages_for_f(const StepTF2 &s) {
 
 bool tc2f_steps_eligible(int k, int r0, int r1, int r2, int64_t N) {
   // k >= 3: rows of at least 8 positions (32 bytes); whole chunks of 64
-  // quads; the K of both MMAs (2 r0, 2 r1) 16, 32 or 64; r2 <= 32 so that N
-  // of MMA2 is at most 64
-  auto ok = [](int r) { return r == 8 || r == 16 || r == 32; };
-  return k >= 3 && N >= 1024 && ((int64_t)1 << (k + 2)) < N && ok(r0) && ok(r1) && r2 >= 1 &&
-         r2 <= kMaxRank;
+  // quads; ranks 8..32 in and between the steps (K and N of the MMAs at most
+  // 64, at least 16 rows of useful work), r2 <= 32
+  return k >= 3 && N >= 1024 && ((int64_t)1 << (k + 2)) < N && r0 >= 8 && r0 <= kMaxRank &&
+         r1 >= 8 && r1 <= kMaxRank && r2 >= 1 && r2 <= kMaxRank;
 }
 
 cudaError_t launch_step_tc2_tf32(const StepTF2 &s, cudaStream_t st) {

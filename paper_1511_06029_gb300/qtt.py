@@ -77,6 +77,7 @@ SIGNATURES = {
     "qtt_batch_autotune": (_I, [_P, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "qtt_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                             ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_size_t)]),
+    "qtt_batch_tensor_ops": (_I, [_P, ctypes.POINTER(_I)]),
     "qtt_batch_destroy": (_I, [_P]),
     "qtt_server_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _P]),
     "qtt_server_submit": (_I, [_P, _P, _P, _P, _P, _L, ctypes.POINTER(_L)]),
@@ -649,8 +650,11 @@ class Batch:
         _check(load_library().qtt_batch_info(self._h, ctypes.byref(w), ctypes.byref(v),
                                              ctypes.byref(g), ctypes.byref(f), ctypes.byref(sb)),
                "qtt_batch_info")
+        t = ctypes.c_int()
+        _check(load_library().qtt_batch_tensor_ops(self._h, ctypes.byref(t)),
+               "qtt_batch_tensor_ops")
         return {"waves": w.value, "variant": v.value, "grid": g.value, "flops": f.value,
-                "scratch_bytes": sb.value}
+                "scratch_bytes": sb.value, "tensor_ops": t.value}
 
     def close(self):
         if self._h is not None:

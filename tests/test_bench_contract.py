@@ -97,8 +97,8 @@ def test_replica_aggregation_over_two_gloo_ranks():
 
 
 class _Apply:
-    def __init__(self, data, nrhs):
-        self.data, self.nrhs = data, nrhs
+    def __init__(self, data, nrhs, compute="bf16"):
+        self.data, self.nrhs, self.compute = data, nrhs, compute
 
 
 def test_bf16_byte_model_matches_the_launch_lists():
@@ -119,3 +119,20 @@ def test_bf16_byte_model_matches_the_launch_lists():
     _, plan = bench.ApplyRun.fused_bytes(run)
     assert plan == [(0, 1, 2), (3,), (4, 5), (6, 7), (8, 9), (10, 11), (12, 13), (14, 15),
                     (16, 17), (18, 19), (20,), (21, 22, 23)]
+
+
+def test_tf32_byte_model_matches_the_launch_list():
+    """The TF32 tensor-core pairing in the byte model mirrors the library's
+    dispatch: the d = 24, r <= 32 TF32 apply is the head kernel, nine
+    tcgen05 pairs from bit 3 and the tail kernel (11 launches in its ncu
+    launch list), 4-byte elements."""
+    import bench
+    from paper_1511_06029_gb300 import inputs
+    data = inputs.synthetic_operator(24, 32, 2)
+    fb, plan = bench.ApplyRun.fused_bytes(_Apply(data, 1, "tf32"))
+    assert plan == [(0, 1, 2), (3, 4), (5, 6), (7, 8), (9, 10), (11, 12), (13, 14), (15, 16),
+                    (17, 18), (19, 20), (21, 22, 23)]
+    r = data.ranks
+    groups = [(0, 3), (3, 5), (5, 7), (7, 9), (9, 11), (11, 13), (13, 15), (15, 17), (17, 19),
+              (19, 21), (21, 24)]
+    assert fb == sum(r[a] + r[b] for a, b in groups) * data.N * 4

@@ -53,10 +53,15 @@ def test_batch_matches_oracle(qtt, compute, budget):
     B = qtt.Batch(ops, xs, ys, compute=compute, mem_budget=budget)
     info = B.info()
     # at least one wave per rank class (largest rank <= 16, <= 24, <= 32,
-    # <= 48); a budget may split a class further
+    # <= 48); a budget may split a class further.  TF32 operators whose apply
+    # runs tcgen05 pairs leave the waves for that path.
     cls = {0 if r <= 16 else 1 if r <= 24 else 2 if r <= 32 else 3
            for r in (max(dt.ranks) for dt in datas)}
-    assert info["waves"] >= len(cls) and (budget != 0 or info["waves"] == len(cls))
+    if compute == "f32":
+        assert info["tensor_ops"] == 0
+        assert info["waves"] >= len(cls) and (budget != 0 or info["waves"] == len(cls))
+    else:
+        assert info["tensor_ops"] >= 1 and info["waves"] >= 1
     for _ in range(2):  # replaying the graph gives the same result
         B.run()
         B.status()
@@ -64,6 +69,32 @@ def test_batch_matches_oracle(qtt, compute, budget):
         for data, x, y in zip(datas, xh, ys):
             err = rel_l2(y.double().cpu().numpy(), oracle.apply(data, x))
             assert err <= 4 * math.sqrt(data.d) * U[compute], (data.d, data.ranks, err)
+    B.close()
+    for o in ops:
+        o.close()
+
+
+def test_tf32_batch_on_tensor_cores(qtt):
+    """A TF32 batch whose operators all have middle ranks 8..32 runs every one
+    of them on the tcgen05 pair path (no wave); each result matches the
+    oracle within the TF32 bound and a second run gives the same bits."""
+    import torch
+    items = _batch(8, 13, d_range=(10, 14), r_range=(9, 32), rhs_range=(1, 4))
+    datas, ops, xs, ys, xh = _setup(qtt, items, "tf32")
+    B = qtt.Batch(ops, xs, ys, compute="tf32")
+    info = B.info()
+    assert info["tensor_ops"] == len(items) and info["waves"] == 0
+    B.run()
+    B.status()
+    torch.cuda.synchronize()
+    first = [y.clone() for y in ys]
+    for data, x, y in zip(datas, xh, ys):
+        err = rel_l2(y.double().cpu().numpy(), oracle.apply(data, x))
+        assert err <= 4 * math.sqrt(data.d) * U["tf32"], (data.d, data.ranks, err)
+    B.run()
+    B.status()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(first, ys))
     B.close()
     for o in ops:
         o.close()
