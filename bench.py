@@ -602,9 +602,9 @@ class ApplyRun:
             fits = k + 2 < d.d and k + 1 < kend
             if self.compute == "tf32":
                 # TF32 pairs: k >= 3, N >= 1024, 2^(k+2) < N, r_k and r_{k+1}
-                # in 8..32, r_{k+2} <= 32
+                # in 8..40, r_{k+2} <= 40
                 tc2 = fits and k >= 3 and d.N >= 1024 and (1 << (k + 2)) < d.N and \
-                    8 <= r[k] <= 32 and 8 <= r[k + 1] <= 32 and r[k + 2] <= 32
+                    8 <= r[k] <= 40 and 8 <= r[k + 1] <= 40 and r[k + 2] <= 40
                 mma2 = False
             else:
                 tc2 = k >= 4 and d.N >= 256 and r[k] % 8 == 0 and \
@@ -764,14 +764,21 @@ class BatchedRun:
     def roofline(self, mean_s):
         achieved = self.flops / mean_s / 1e9
         kern = f"batch_kernel<{self.variant % 100}>"
+        pk = measured_peaks().get("bf16_tflops")
         if self.info.get("tensor_ops"):
+            # operators on the tcgen05 TF32 pairs: the TF32 tensor peak governs
             kern += (f" waves + {self.info['tensor_ops']} operators on step_tc2f_kernel "
                      "(tcgen05 TF32 pairs)")
+            tpk = (pk or 1900.0) * TF32_PER_BF16
+            return {"bound": "tensor", "kernel": kern, "achieved": achieved / 1e3, "peak": tpk,
+                    "unit": "TFLOP/s", "frac": achieved / 1e3 / tpk, "traffic": None,
+                    "peak_source": "measured BF16 burst (MEASURED_PEAKS.json bf16_tflops) x "
+                                   "1.1/2.25 (nominal dense TF32/BF16)",
+                    "frac_of_fp32_pipe": achieved / fp32_peak_gflops()}
         r = {"bound": "alu", "kernel": kern, "achieved": achieved,
              "peak": fp32_peak_gflops(), "unit": "GFLOP/s",
              "frac": achieved / fp32_peak_gflops(), "traffic": None,
              "peak_source": "FP32 pipe, 152 SMs x 128 FMA/clk x 2.07 GHz"}
-        pk = measured_peaks().get("bf16_tflops")
         if pk and self.compute == "tf32":
             r["frac_of_tensor_peak"] = achieved / (pk * 1e3 * TF32_PER_BF16)
         return r

@@ -800,15 +800,15 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores
       A->t2off.assign(d, -1);
       int64_t to = 0;
       // first-step copy [128][K1], K1 = 2 r_k rounded up to 8, columns 2a + j;
-      // second-step copy [64][K2], K2 = 2 r_k rounded up to 4 per half,
+      // second-step copy [80][K2], K2 = 2 r_k rounded up to 4 per half,
       // columns j (r_k rounded up to 4) + a; padding zero
       for (int k = 0; k < d; ++k) {
-        if (ranks[k] < 8 || ranks[k] > 32 || ranks[k + 1] > 32) continue;
+        if (ranks[k] < 8 || ranks[k] > 40 || ranks[k + 1] > 40) continue;
         const int k1 = (2 * ranks[k] + 7) / 8 * 8, k2 = 2 * ((ranks[k] + 3) / 4 * 4);
         A->toff[k] = to;
         to += (int64_t)128 * k1;
         A->t2off[k] = to;
-        to += (int64_t)64 * k2;
+        to += (int64_t)80 * k2;
       }
       if (e2 == cudaSuccess && to > 0) {
         std::vector<float> m((size_t)to, 0.0f);

@@ -110,9 +110,9 @@ struct qtt_op {
   // TF32 tensor-core copies for the tcgen05 pair kernel, TF32-rounded: core k
   // as the first step of a pair, [128][2 r_k rounded up to 8] (rows 2b+i,
   // zero past 2 r_{k+1}; columns 2a+j) at element offset toff[k], and as the
-  // second, [64][2 r'] with r' = r_k rounded up to 4 (rows 2b+i, zero past
-  // 2 r_{k+1}; columns j r' + a) at t2off[k]; only for 8 <= r_k <= 32 and
-  // r_{k+1} <= 32 (-1 otherwise).
+  // second, [80][2 r'] with r' = r_k rounded up to 4 (rows 2b+i, zero past
+  // 2 r_{k+1}; columns j r' + a) at t2off[k]; only for 8 <= r_k <= 40 and
+  // r_{k+1} <= 40 (-1 otherwise).
   float *mma_tf32 = nullptr;
   std::vector<int64_t> toff, t2off;
   // Reduced-precision packing [a][j][b padded to rpad[k+1]][i]:

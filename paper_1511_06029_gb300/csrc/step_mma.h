@@ -54,7 +54,7 @@ cudaError_t launch_step_tc2_bf16(const StepMMA2 &s, cudaStream_t st);
 // kind::tf32): FP32 planar buffers holding TF32-rounded values.  Cores as
 // TF32 matrices: A1 = M_k as [128][K1] (K1 = 2 r_k rounded up to 8; rows
 // 2b + i, columns 2a + j; rows past 2 r_{k+1} zero), A2 = M_{k+1} as
-// [64][2 r'] (r' = r_{k+1} rounded up to 4; rows 2c + i, columns j r' + b;
+// [80][2 r'] (r' = r_{k+1} rounded up to 4; rows 2c + i, columns j r' + b;
 // rows past 2 r_{k+2} zero).  cudaErrorNotSupported (nothing launched) when
 // the shapes do not fit.
 struct StepTF2 {
@@ -63,7 +63,7 @@ struct StepTF2 {
   float *out;                // y_{k+2}
   int64_t out_rhs_stride;
   const float *A1;           // M_k as [128][K1], columns 2a + j
-  const float *A2;           // M_{k+1} as [64][2 r'], columns j r' + b
+  const float *A2;           // M_{k+1} as [80][2 r'], columns j r' + b
   int k, r0, r1, r2;
   int64_t N, nrhs;
 };

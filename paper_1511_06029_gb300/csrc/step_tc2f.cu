@@ -69,23 +69,25 @@ namespace {
 
 using namespace tcx;
 
-constexpr int kGroups = 2;
+constexpr int kMaxGroups = 2;
 constexpr int kGroupThreads = 128;
 constexpr int kProducerWarp = 0;
 constexpr int kMma1Warp = 1;
 constexpr int kMma2Warp = 2;
 constexpr int kXWarp0 = 4;                  // warps 4-7
 constexpr int kXThreads = 128;
-constexpr int kEpiWarp0 = 8;                // warps 8-15
+constexpr int kEpiWarp0 = 8;                // warps 8-15 (8-11 with one group)
 constexpr int kThreads = 512;
 constexpr int kQ = 64;                      // quads per chunk: two runs of 32
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kTmemX = 0;              // X buffers: columns 0-63, 64-127
-constexpr uint32_t kTmemD = 128;            // group g: D1^T at 128 + 128 g, D2^T 64 later
 constexpr int kNx = 2;                      // X buffers
 constexpr int kMaxStages = 8;
-constexpr int kMaxRank = 32;                // 2 r <= 64: K and N of both MMAs
+constexpr int kMaxRank = 40;                // 2 r <= 80: K and N of both MMAs
 constexpr int kBarBytes = 512;
+// Two shapes: ranks <= 32 with two epilogue groups (K, N <= 64), ranks <= 40
+// with one (K, N <= 80; shared memory holds one T buffer and two stages).
+// TMEM columns: X buffers at 0 and KM; group g's D1^T at 2 KM + 2 KM g, its
+// D2^T KM further.
 
 // Instruction descriptor of kind::tf32, M = 128: D FP32 (bits 4-5 = 1), A and
 // B TF32 (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 clear), N >> 3
@@ -134,28 +136,38 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v) {
       "f"(v[15])
       : "memory");
 }
-// Two loads of 32 columns in flight, then one wait.
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
-  uint32_t r[64];
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(r[32 * h + 0]), "=r"(r[32 * h + 1]), "=r"(r[32 * h + 2]), "=r"(r[32 * h + 3]),
-          "=r"(r[32 * h + 4]), "=r"(r[32 * h + 5]), "=r"(r[32 * h + 6]), "=r"(r[32 * h + 7]),
-          "=r"(r[32 * h + 8]), "=r"(r[32 * h + 9]), "=r"(r[32 * h + 10]), "=r"(r[32 * h + 11]),
-          "=r"(r[32 * h + 12]), "=r"(r[32 * h + 13]), "=r"(r[32 * h + 14]),
-          "=r"(r[32 * h + 15]), "=r"(r[32 * h + 16]), "=r"(r[32 * h + 17]),
-          "=r"(r[32 * h + 18]), "=r"(r[32 * h + 19]), "=r"(r[32 * h + 20]),
-          "=r"(r[32 * h + 21]), "=r"(r[32 * h + 22]), "=r"(r[32 * h + 23]),
-          "=r"(r[32 * h + 24]), "=r"(r[32 * h + 25]), "=r"(r[32 * h + 26]),
-          "=r"(r[32 * h + 27]), "=r"(r[32 * h + 28]), "=r"(r[32 * h + 29]),
-          "=r"(r[32 * h + 30]), "=r"(r[32 * h + 31])
-        : "r"(taddr + 32u * (uint32_t)h));
+// 32 lanes x NC consecutive 32-bit TMEM columns (NC = 64 or 80): loads of
+// 32 (and 16) columns in flight, then one wait.
+__device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+template <int NC>
+__device__ __forceinline__ void tmem_ldn(uint32_t taddr, float (&v)[NC]) {
+  uint32_t r[NC];
+  tmem_ld_x32(taddr, r);
+  tmem_ld_x32(taddr + 32u, r + 32);
+  if constexpr (NC == 80) tmem_ld_x16(taddr + 64u, r + 64);
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-  for (int e = 0; e < 64; ++e) v[e] = __uint_as_float(r[e]);
+  for (int e = 0; e < NC; ++e) v[e] = __uint_as_float(r[e]);
 }
 
 // Round to TF32 (10 explicit mantissa bits), nearest even, as the unfused
@@ -178,7 +190,7 @@ __device__ __forceinline__ unsigned kmaj_off(int rows, int r, int kk) {
 struct Bars {
   unsigned long long full[kMaxStages], empty[kMaxStages];
   unsigned long long xready[kNx], xfree[kNx];
-  unsigned long long d1full[kGroups], tready[kGroups], d2full[kGroups], dfree[kGroups];
+  unsigned long long d1full[kMaxGroups], tready[kMaxGroups], d2full[kMaxGroups], dfree[kMaxGroups];
   uint32_t tmem;
   int abort;
 };
@@ -188,13 +200,13 @@ static_assert(sizeof(Bars) <= kBarBytes, "mbarrier block");
 // K1) and B2 (N2 rows x K2) K-major, per group a T buffer (128 rows x K2,
 // K-major), the stage ring (two boxes of 4 r0 rows of 128 bytes).
 struct PlanF {
-  unsigned b1, b2, t[kGroups], box, boxs, s0, stage, end;
+  unsigned b1, b2, t[kMaxGroups], box, boxs, s0, stage, end;
   int n1, n2, k1, r1p, k2;
 };
 __host__ __device__ inline unsigned kmaj_bytes(int rows, int Kp) {
   return (unsigned)((Kp + 31) / 32) * (unsigned)rows * 128u;
 }
-__host__ __device__ inline PlanF make_plan_f(const StepTF2 &s, int S) {
+__host__ __device__ inline PlanF make_plan_f(const StepTF2 &s, int S, int G) {
   PlanF p;
   p.k1 = (2 * s.r0 + 7) / 8 * 8;
   p.r1p = (s.r1 + 3) / 4 * 4;
@@ -204,7 +216,7 @@ __host__ __device__ inline PlanF make_plan_f(const StepTF2 &s, int S) {
   p.b1 = up1k(kBarBytes);
   p.b2 = up1k(p.b1 + kmaj_bytes(p.n1, p.k1));
   unsigned o = up1k(p.b2 + kmaj_bytes(p.n2, p.k2));
-  for (int g = 0; g < kGroups; ++g) {
+  for (int g = 0; g < G; ++g) {
     p.t[g] = o;
     o = up1k(o + kmaj_bytes(128, p.k2));
   }
@@ -216,11 +228,13 @@ __host__ __device__ inline PlanF make_plan_f(const StepTF2 &s, int S) {
   return p;
 }
 
+template <int G, int KM>
 __global__ void __launch_bounds__(kThreads, 1)
     step_tc2f_kernel(const __grid_constant__ CUtensorMap tin, StepTF2 s, int S) {
+  constexpr uint32_t kTmemX = 0, kTmemD = 2 * KM;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char *base = smraw + ((1024u - (su32(smraw) & 1023u)) & 1023u);
-  const PlanF P = make_plan_f(s, S);
+  const PlanF P = make_plan_f(s, S, G);
   Bars &B = *reinterpret_cast<Bars *>(base);
   const unsigned base32 = su32(base);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -244,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(su32(&B.xready[i]), kXThreads);
       mbar_init(su32(&B.xfree[i]), 1);
     }
-    for (int i = 0; i < kGroups; ++i) {
+    for (int i = 0; i < G; ++i) {
       mbar_init(su32(&B.d1full[i]), 1);
       mbar_init(su32(&B.tready[i]), kGroupThreads);
       mbar_init(su32(&B.d2full[i]), 1);
@@ -317,15 +331,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t id = idesc_tf32(P.n1);
       const int nk = Kp1 / 8;
       for (int n = 0; n < mine; ++n) {
-        const int g = n % kGroups, b = n % kNx;
+        const int g = n % G, b = n % kNx;
         if (!wait_bar(su32(&B.xready[b]), (unsigned)(n / kNx) & 1u, abort)) break;
-        // D1^T of this group was last read by the T write of chunk n - 2
-        if (n >= kGroups &&
-            !wait_bar(su32(&B.tready[g]), (unsigned)(n / kGroups - 1) & 1u, abort))
-          break;
+        // D1^T of this group was last read by the T write of chunk n - G
+        if (n >= G && !wait_bar(su32(&B.tready[g]), (unsigned)(n / G - 1) & 1u, abort)) break;
         tc_fence_after();
-        const uint32_t d = tmem + kTmemD + (uint32_t)(g * 128);
-        const uint32_t xa = tmem + kTmemX + (uint32_t)(b * 64);
+        const uint32_t d = tmem + kTmemD + (uint32_t)(g * 2 * KM);
+        const uint32_t xa = tmem + kTmemX + (uint32_t)(b * KM);
         for (int ks = 0; ks < nk; ++ks) {
           const unsigned bb =
               base32 + P.b1 + (unsigned)((ks >> 2) * P.n1 * 128 + (ks & 3) * 32);
@@ -342,14 +354,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t id = idesc_tf32(P.n2);
       const int nk = Kp2 / 8;
       for (int m = 0; m < mine; ++m) {
-        const int g = m % kGroups;
-        if (!wait_bar(su32(&B.tready[g]), (unsigned)(m / kGroups) & 1u, abort)) break;
-        // D2^T of this group was last read by the O write of chunk m - 2
-        if (m >= kGroups &&
-            !wait_bar(su32(&B.dfree[g]), (unsigned)(m / kGroups - 1) & 1u, abort))
-          break;
+        const int g = m % G;
+        if (!wait_bar(su32(&B.tready[g]), (unsigned)(m / G) & 1u, abort)) break;
+        // D2^T of this group was last read by the y write of chunk m - G
+        if (m >= G && !wait_bar(su32(&B.dfree[g]), (unsigned)(m / G - 1) & 1u, abort)) break;
         tc_fence_after();
-        const uint32_t d = tmem + kTmemD + (uint32_t)(g * 128 + 64);
+        const uint32_t d = tmem + kTmemD + (uint32_t)(g * 2 * KM + KM);
         const unsigned tb = base32 + P.t[g];
         for (int ks = 0; ks < nk; ++ks) {
           const unsigned aa = tb + (unsigned)((ks >> 2) * 128 * 128 + (ks & 3) * 32);
@@ -364,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ stage -> X
     // warp q = w - 4 owns TMEM lanes 32 q .. + 31 = positions (j1, h) =
     // (q / 2, q % 2), t = lane: column kr of X is row R = j1 2 r0 + kr of box
-    // h at position t (columns 2 r0 .. 63 are written as zeros).  k >= 5: a
+    // h at position t (columns 2 r0 .. KM - 1 are written as zeros).  k >= 5: a
     // warp reads whole 128-byte rows, row R at swizzle phase R % 8.
     // k = 3, 4: position t is (hi, x) = (t / 2^k, t % 2^k), at
     // ((hi 4 r0 + R) 2^k + x) floats.
@@ -388,24 +398,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!wait_bar(su32(&B.full[st]), ph, abort)) break;
       if (n >= kNx && !wait_bar(su32(&B.xfree[b]), (unsigned)(n / kNx - 1) & 1u, abort)) break;
       const unsigned char *box = base + P.s0 + (unsigned)st * P.stage + (unsigned)h * P.boxs;
-      float v[64];
+      float v[KM];
       if (swz) {
         const unsigned char *rows = box + rot * 128u;
 #pragma unroll
-        for (int kr = 0; kr < 64; ++kr)
+        for (int kr = 0; kr < KM; ++kr)
           v[kr] = kr < kin ? *reinterpret_cast<const float *>(rows + kr * 128 + pre[kr & 7]) : 0.f;
       } else {
         const unsigned char *rows = box + plain + rot * rstride;
 #pragma unroll
-        for (int kr = 0; kr < 64; ++kr)
+        for (int kr = 0; kr < KM; ++kr)
           v[kr] = kr < kin ? *reinterpret_cast<const float *>(rows + (unsigned)kr * rstride) : 0.f;
       }
       mbar_arrive(su32(&B.empty[st]));  // the stage has been read
+      const uint32_t xb = tl + (uint32_t)(b * KM);
       if (Kp1 <= 16) {
-        tmem_st16(tl + (uint32_t)(b * 64), v);
+        tmem_st16(xb, v);
       } else {
-        tmem_st32(tl + (uint32_t)(b * 64), v);
-        if (Kp1 > 32) tmem_st32(tl + (uint32_t)(b * 64 + 32), v + 32);
+        tmem_st32(xb, v);
+        if (Kp1 > 32) tmem_st32(xb + 32u, v + 32);
+        if constexpr (KM == 80)
+          if (Kp1 > 64) tmem_st16(xb + 64u, v + 64);
       }
       asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
       tc_fence_before();
@@ -415,22 +428,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         ph ^= 1u;
       }
     }
-  } else if (warp >= kEpiWarp0) {
+  } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4 * G) {
     // ------------------------------------------------------------ epilogue
     // T write: thread = input position m = 64 j1 + 32 h + x (j1 = q / 2,
     // h = q % 2, x = lane); y_{k+2} write: thread = output position
     // n = 64 i + 32 h + x (i = q / 2).
     const int g = (warp - kEpiWarp0) >> 2;
     const int qhi = wq >> 1, qh = wq & 1;
-    const uint32_t d1 = tmem + ((uint32_t)(32 * wq) << 16) + kTmemD + (uint32_t)(g * 128);
-    const uint32_t d2 = d1 + 64u;
+    const uint32_t d1 = tmem + ((uint32_t)(32 * wq) << 16) + kTmemD + (uint32_t)(g * 2 * KM);
+    const uint32_t d2 = d1 + (uint32_t)KM;
     const unsigned x7 = (unsigned)lane & 7u;
     unsigned char *T = base + P.t[g];
     const unsigned tk0 = (unsigned)(qhi * P.r1p);  // this thread's half of T's K
     const int64_t bit1 = (int64_t)1 << (s.k + 1);
-    ChunkWalk cw(blockIdx.x + (int64_t)g * NG, (int64_t)kGroups * NG, cpr);
-    for (int n = g; n < mine; n += kGroups, cw.next()) {
-      const unsigned par = (unsigned)(n / kGroups) & 1u;
+    ChunkWalk cw(blockIdx.x + (int64_t)g * NG, (int64_t)G * NG, cpr);
+    for (int n = g; n < mine; n += G, cw.next()) {
+      const unsigned par = (unsigned)(n / G) & 1u;
       if (epi_any<kGroupThreads>(!wait_bar(su32(&B.d1full[g]), par, abort), g)) break;
       tc_fence_after();
       {
@@ -438,14 +451,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         // consecutive b per 16-byte piece, at (K / 32) 16384 + row 128 +
         // ((K / 4 % 8) ^ (row % 8)) 16 (columns b >= r1 of D1^T are zero: the
         // core tile's padding rows).  T was last read by MMA2 of chunk
-        // n - 2, complete before this group's y write of that chunk began.
-        float v[64];
-        tmem_ld64(d1, v);
+        // n - G, complete before this group's y write of that chunk began.
+        float v[KM];
+        tmem_ldn<KM>(d1, v);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
           unsigned char *trow = T + (unsigned)(64 * i + 32 * qh + lane) * 128u;
 #pragma unroll
-          for (int p = 0; p < 8; ++p) {
+          for (int p = 0; p < KM / 8; ++p) {
             if (4 * p < P.r1p) {
               const unsigned kk = tk0 + 4u * (unsigned)p;
               float4 w;
@@ -467,15 +480,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       {
         // D2^T column 2c + i1 -> y_{k+2}[rhs][c][position of quad
         // q0 + 32 h + x with bits (k, k+1) = (i, i1)]
-        float v[64];
-        tmem_ld64(d2, v);
+        float v[KM];
+        tmem_ldn<KM>(d2, v);
         tc_fence_before();
         mbar_arrive(su32(&B.dfree[g]));  // D2^T is in registers
         const int64_t qq = cw.w * kQ + 32 * qh + lane;
         const int64_t pos = ((qq >> s.k) << (s.k + 2)) | ((int64_t)qhi << s.k) | (qq & lowmask);
         float *y = s.out + cw.c * s.out_rhs_stride + pos;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
+        for (int c = 0; c < KM / 2; ++c) {
           if (c < s.r2) {
             y[0] = tf32_rne(v[2 * c]);
             y[bit1] = tf32_rne(v[2 * c + 1]);
@@ -522,19 +535,37 @@ bool encode_view_f32(CUtensorMap *m, const void *ptr, int k, int64_t N, int64_t 
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int stages_for_f(const StepTF2 &s) {
-  const PlanF p0 = make_plan_f(s, 0);
+int stages_for_f(const StepTF2 &s, int G) {
+  const PlanF p0 = make_plan_f(s, 0, G);
   if (p0.end + 2 * p0.stage + 1024 > kSmemLimit) return 0;
   const int S = (int)((kSmemLimit - 1024 - p0.end) / p0.stage);
   return S > kMaxStages ? kMaxStages : S;
+}
+
+template <int G, int KM>
+cudaError_t launch_tc2f(const CUtensorMap &tin, const StepTF2 &s, cudaStream_t st) {
+  const int S = stages_for_f(s, G);
+  if (S < 2) return cudaErrorNotSupported;
+  const size_t smem = make_plan_f(s, S, G).end + 1024;
+  static cudaError_t attr = cudaFuncSetAttribute(
+      step_tc2f_kernel<G, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+  if (attr != cudaSuccess) return attr;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t nchunks = (s.N >> 2) / kQ * s.nrhs;
+  const unsigned grid = (unsigned)(nchunks < sms ? nchunks : sms);
+  step_tc2f_kernel<G, KM><<<grid, kThreads, smem, st>>>(tin, s, S);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 bool tc2f_steps_eligible(int k, int r0, int r1, int r2, int64_t N) {
   // k >= 3: rows of at least 8 positions (32 bytes); whole chunks of 64
-  // quads; ranks 8..32 in and between the steps (K and N of the MMAs at most
-  // 64, at least 16 rows of useful work), r2 <= 32
+  // quads; ranks 8..40 in and between the steps (K and N of the MMAs at most
+  // 80, at least 16 rows of useful work), r2 <= 40
   return k >= 3 && N >= 1024 && ((int64_t)1 << (k + 2)) < N && r0 >= 8 && r0 <= kMaxRank &&
          r1 >= 8 && r1 <= kMaxRank && r2 >= 1 && r2 <= kMaxRank;
 }
@@ -543,23 +574,11 @@ cudaError_t launch_step_tc2_tf32(const StepTF2 &s, cudaStream_t st) {
   if (!tc2f_steps_eligible(s.k, s.r0, s.r1, s.r2, s.N)) return cudaErrorNotSupported;
   if (s.in_rhs_stride != (int64_t)s.r0 * s.N || s.out_rhs_stride != (int64_t)s.r2 * s.N)
     return cudaErrorNotSupported;
-  const int S = stages_for_f(s);
-  if (S < 2) return cudaErrorNotSupported;
-  const size_t smem = make_plan_f(s, S).end + 1024;
   CUtensorMap tin;
-  if (!encode_view_f32(&tin, s.in, s.k, s.N, s.nrhs * s.r0, s.r0))
-    return cudaErrorNotSupported;
-  static cudaError_t attr = cudaFuncSetAttribute(
-      step_tc2f_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
-  if (attr != cudaSuccess) return attr;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t nchunks = (s.N >> 2) / kQ * s.nrhs;
-  const unsigned grid = (unsigned)(nchunks < sms ? nchunks : sms);
-  step_tc2f_kernel<<<grid, kThreads, smem, st>>>(tin, s, S);
-  count_launches(1);
-  return cudaGetLastError();
+  if (!encode_view_f32(&tin, s.in, s.k, s.N, s.nrhs * s.r0, s.r0)) return cudaErrorNotSupported;
+  // ranks <= 32: two epilogue groups; up to 40: one (shared memory)
+  if (s.r0 <= 32 && s.r1 <= 32 && s.r2 <= 32) return launch_tc2f<2, 64>(tin, s, st);
+  return launch_tc2f<1, 80>(tin, s, st);
 }
 
 cudaError_t tcf_status_take(int *status) {

@@ -6,7 +6,8 @@ operands are TF32 (unit roundoff 2^-11) and every stored intermediate is
 rounded to TF32, so the relative error is at most about sqrt(d) 2^-11 --
 the launch count shows that the pairs ran (fewer launches than the plan
 without pairs), and the result agrees with the FP32-pipe TF32 sweep within
-the same bound.  The cases cover ranks 8, 16 and 32 in both MMAs, pairs
+the same bound.  The cases cover ranks from 8 to 40 (powers of two and
+not; above 32 the one-group shape) in both MMAs, pairs
 starting at bits 3 and 4 (unswizzled boxes over several high-bit rows) and
 at 5 and above, an output rank that is not a multiple of anything (5), a
 single chunk per CTA and many chunks per CTA (the stage ring and both
@@ -30,6 +31,9 @@ CASES = [
     ("ranks", [1, 2, 4, 8, 16, 16, 32, 5, 4, 2, 1], None, 2),
     ("ranks", [1, 2, 4, 8, 16, 32, 16, 32, 16, 32, 8, 4, 2, 1], None, 1),
     ("ranks", [1, 2, 4, 8, 8, 16, 8, 32, 8, 4, 2, 1], None, 2),
+    ("profile", 13, 40, 2),
+    ("ranks", [1, 2, 4, 8, 16, 36, 33, 39, 20, 8, 4, 2, 1], None, 2),
+    ("ranks", [1, 2, 4, 8, 12, 27, 9, 31, 23, 17, 8, 4, 2, 1], None, 3),
 ]
 
 
