@@ -866,7 +866,11 @@ qtt_status qtt_batch_autotune(qtt_batch *B, int reps, void *stream, int *chosen,
   cudaEvent_t e0, e1;
   QTT_CUDA_TRY(cudaEventCreate(&e0));
   QTT_CUDA_TRY(cudaEventCreate(&e1));
-  for (int v : {30802, 33202, 33204, 23202, 23204}) {
+  // no waves (every operator on the tensor-core path): nothing to tune, one
+  // timed run reports the time
+  const std::vector<int> cands =
+      B->waves.empty() ? std::vector<int>{best} : std::vector<int>{30802, 33202, 33204, 23202, 23204};
+  for (int v : cands) {
     qtt_status s = qtt_batch_set_variant(B, v, stream);
     if (s != QTT_OK) continue;
     qtt_batch_run(B, stream);  // warm-up
