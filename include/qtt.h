@@ -86,6 +86,23 @@ qtt_status qtt_create(qtt_op **out, int d, const int *ranks,
                       const double *cores, unsigned precision_mask,
                       void *stream);
 
+/* The .qtt operator file (no counterpart in the paper): a 24-byte header --
+ * magic "QTT1", format version 1, d, element type 0 (FP64), core layout 0
+ * (the layout above), a reserved word; every field a little-endian uint32
+ * -- then the d + 1 ranks (uint32) and the cores as little-endian FP64, in
+ * qtt_create's order.  Host-only.
+ * qtt_write_file: d, ranks, cores as for qtt_create; QTT_ERR_INVALID_ARG for
+ *   bad arguments or an I/O failure.
+ * qtt_read_file: sets *d and *cores_len (sum_k 4 r_k r_{k+1}); fills ranks
+ *   (ranks_cap >= d + 1) and cores (cores_cap >= *cores_len) when they are
+ *   not NULL, so a first call with NULL arrays sizes the buffers.
+ *   QTT_ERR_INVALID_ARG for a missing or malformed file (magic, d, ranks,
+ *   length) or too small a buffer, QTT_ERR_UNSUPPORTED for another version,
+ *   element type or layout. */
+qtt_status qtt_write_file(const char *path, int d, const int *ranks, const double *cores);
+qtt_status qtt_read_file(const char *path, int *d, int *ranks, int ranks_cap, double *cores,
+                         int64_t cores_cap, int64_t *cores_len);
+
 /* qtt_destroy -- release the operator.  Returns at once: its device memory
  * goes back to the library's pool once the work already queued that reads
  * it has finished (every apply, solve, plan replay and batch run records

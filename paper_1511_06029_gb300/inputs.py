@@ -70,6 +70,41 @@ class QTTData:
 
 
 # ---------------------------------------------------------------- structure
+# The .qtt operator file (header: magic "QTT1", version, d, element type,
+# core layout, reserved -- little-endian uint32 -- then d + 1 uint32 ranks
+# and the FP64 cores in QTTData's order).  The library reads and writes the
+# same format; this is an independent numpy version for the generators.
+_QTT_MAGIC = b"QTT1"
+
+
+def save_qtt(path: str, data: QTTData) -> None:
+    head = np.array([1, data.d, 0, 0, 0], dtype="<u4").tobytes()
+    body = np.asarray(data.ranks, dtype="<u4").tobytes() + b"".join(
+        np.ascontiguousarray(c, dtype="<f8").tobytes() for c in data.cores)
+    with open(path, "wb") as f:
+        f.write(_QTT_MAGIC + head + body)
+
+
+def load_qtt(path: str) -> QTTData:
+    raw = open(path, "rb").read()
+    if raw[:4] != _QTT_MAGIC or len(raw) < 24:
+        raise ValueError(f"{path}: not a .qtt file")
+    version, d, etype, layout, _ = np.frombuffer(raw, dtype="<u4", count=5, offset=4)
+    if version != 1 or etype != 0 or layout != 0:
+        raise ValueError(f"{path}: unsupported .qtt version, element type or layout")
+    ranks = [int(r) for r in np.frombuffer(raw, dtype="<u4", count=d + 1, offset=24)]
+    off = 24 + 4 * (d + 1)
+    cores = []
+    for k in range(d):
+        n = 4 * ranks[k] * ranks[k + 1]
+        cores.append(np.frombuffer(raw, dtype="<f8", count=n, offset=off)
+                     .reshape(ranks[k], 2, 2, ranks[k + 1]).astype(np.float64))
+        off += 8 * n
+    if off != len(raw):
+        raise ValueError(f"{path}: length does not match the ranks")
+    return QTTData(ranks, cores, {"kind": "file", "path": path})
+
+
 def rank_profile(d: int, rmax: int) -> list:
     return [min(2 ** k, 2 ** (d - k), rmax) for k in range(d + 1)]
 

@@ -78,6 +78,9 @@ SIGNATURES = {
     "qtt_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                             ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_size_t)]),
     "qtt_batch_tensor_ops": (_I, [_P, ctypes.POINTER(_I)]),
+    "qtt_write_file": (_I, [ctypes.c_char_p, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "qtt_read_file": (_I, [ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(_I), _I,
+                           ctypes.POINTER(_D), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "qtt_batch_destroy": (_I, [_P]),
     "qtt_server_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _P]),
     "qtt_server_submit": (_I, [_P, _P, _P, _P, _P, _L, ctypes.POINTER(_L)]),
@@ -758,6 +761,39 @@ class Server:
 def kernel_launches() -> int:
     """Kernels the library has launched so far (qtt_kernel_launches)."""
     return int(load_library().qtt_kernel_launches())
+
+
+def write_file(path: str, ranks, cores) -> None:
+    """Write an operator (ranks[0..d], cores[k] shaped (r_k, 2, 2, r_{k+1}))
+    as a .qtt file (qtt_write_file)."""
+    ranks = [int(r) for r in ranks]
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.float64).ravel()
+                                                for c in cores]))
+    rk = (ctypes.c_int * len(ranks))(*ranks)
+    _check(load_library().qtt_write_file(os.fsencode(path), len(ranks) - 1, rk,
+                                         flat.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "qtt_write_file")
+
+
+def read_file(path: str):
+    """Read a .qtt file (qtt_read_file): returns (ranks, cores), cores[k]
+    shaped (r_k, 2, 2, r_{k+1})."""
+    lib = load_library()
+    d, n = ctypes.c_int(), ctypes.c_int64()
+    _check(lib.qtt_read_file(os.fsencode(path), ctypes.byref(d), None, 0, None, 0,
+                             ctypes.byref(n)), "qtt_read_file")
+    rk = (ctypes.c_int * (d.value + 1))()
+    flat = np.empty(n.value, dtype=np.float64)
+    _check(lib.qtt_read_file(os.fsencode(path), ctypes.byref(d), rk, d.value + 1,
+                             flat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.value,
+                             ctypes.byref(n)), "qtt_read_file")
+    ranks = list(rk)
+    cores, o = [], 0
+    for k in range(d.value):
+        sz = 4 * ranks[k] * ranks[k + 1]
+        cores.append(flat[o:o + sz].reshape(ranks[k], 2, 2, ranks[k + 1]).copy())
+        o += sz
+    return ranks, cores
 
 
 def selftest_wait(seconds: float, stream=None):
