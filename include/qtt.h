@@ -56,7 +56,8 @@ typedef enum {
   QTT_ERR_CUDA = 3,
   QTT_ERR_NOT_CONVERGED = 4,
   QTT_ERR_TIMEOUT = 5,
-  QTT_ERR_UNSUPPORTED = 6
+  QTT_ERR_UNSUPPORTED = 6,
+  QTT_ERR_CHECK = 7  /* checked build only: a kernel met an out-of-range index */
 } qtt_status;
 
 /* Element / arithmetic types.  QTT_TF32 names FP32 storage with operands
@@ -544,6 +545,16 @@ const char *qtt_status_string(qtt_status s);
 uint64_t qtt_kernel_launches(void);
 /* Message of the last failing call on this thread ("" if none). */
 const char *qtt_last_error(void);
+/* 1 in the checked build (libqtt_checked.so, compiled with -DQTT_CHECKED:
+ * the kernels check their derived indices, clamp an out-of-range one to a
+ * valid index and record where; qtt_sync_status then returns QTT_ERR_CHECK
+ * once), 0 otherwise. */
+int qtt_checked_build(void);
+/* Checked build: launches a kernel that derives one index out of its range
+ * on purpose (clamped, so nothing is accessed out of bounds); the next
+ * qtt_sync_status returns QTT_ERR_CHECK.  QTT_ERR_UNSUPPORTED in the normal
+ * build. */
+qtt_status qtt_check_selftest(void *stream);
 /* Synchronise `stream` and report device-side errors (QTT_ERR_CUDA for a
  * sticky CUDA error, QTT_ERR_TIMEOUT if a bounded wait in a library kernel
  * gave up).  The status word is cleared once reported. */

@@ -30,6 +30,7 @@
 #include <new>
 #include <vector>
 
+#include "checked.cuh"
 #include "qtt_internal.h"
 #include "step_lp.h"
 
@@ -335,9 +336,9 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(BWave w) {
     wait_item(w, it, &s_abort);
     __syncthreads();
     if (s_abort) break;
-    const BSeg sg = w.segs[it.seg];
+    const BSeg sg = w.segs[QTT_CK(it.seg, w.nseg, 401)];
     const BOp &op = w.ops[sg.op];
-    const int k = sg.k;
+    const int k = (int)QTT_CK(sg.k, op.d, 402);
     const int rin = op.ranks[k], rout = op.ranks[k + 1];
     const int rpad = op.rpad[k + 1];
     const int64_t N = op.N, npairs = N >> 1;
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(BWave w) {
       for (int e = tid; e < 2 * rin * 2 * rpad; e += kThreads) sG[e] = __ldg(G + e);
       gseg = it.seg;
     }
-    const int64_t c_begin = (it.idx - sg.first) * sg.slice;
+    const int64_t c_begin = QTT_CK((it.idx - sg.first) * sg.slice, sg.nchunks, 403);
     const int64_t c_end = c_begin + sg.slice < sg.nchunks ? c_begin + sg.slice : sg.nchunks;
     const bool round_in = w.tf32 && k == 0;          // x itself is not TF32-rounded
     const bool round_out = w.tf32 && k < op.d - 1;   // intermediates are stored rounded

@@ -10,7 +10,9 @@
 #include <mutex>
 #include <new>
 #include <unordered_map>
+#include <vector>
 
+#include "checked.cuh"
 #include "qtt_internal.h"
 #include "step_lp.h"
 #include "step_mma.h"
@@ -18,6 +20,33 @@
 namespace qtt {
 
 static thread_local std::string g_last_error;
+
+// Readers of the translation units' index-check words (the checked build;
+// empty otherwise).  Filled by static initialisers, so constructed on first
+// use.
+static std::vector<cudaError_t (*)(int *)> &check_words() {
+  static std::vector<cudaError_t (*)(int *)> w;
+  return w;
+}
+bool register_check_word(cudaError_t (*take)(int *site)) {
+  check_words().push_back(take);
+  return true;
+}
+
+#ifdef QTT_CHECKED
+// The self-test of the checked build: one index derived past its range on
+// purpose (site 501); QTT_CK clamps it, so the store lands in bounds.
+__device__ int g_check_selftest_cell[4];
+__global__ void check_selftest_kernel(int over) {
+  const int64_t i = QTT_CK(3 + over, 4, 501);
+  g_check_selftest_cell[i] = 1;
+}
+cudaError_t launch_check_selftest(cudaStream_t st) {
+  check_selftest_kernel<<<1, 1, 0, st>>>(1);
+  count_launches(1);
+  return cudaGetLastError();
+}
+#endif
 static std::atomic<uint64_t> g_launches{0};
 
 static thread_local uint64_t t_launches = 0;  // this thread's launches (plan recording)
@@ -646,6 +675,7 @@ const char *qtt_status_string(qtt_status s) {
     case QTT_ERR_NOT_CONVERGED: return "not converged";
     case QTT_ERR_TIMEOUT: return "device wait timed out";
     case QTT_ERR_UNSUPPORTED: return "unsupported combination";
+    case QTT_ERR_CHECK: return "checked build: a kernel met an out-of-range index";
   }
   return "unknown status";
 }
@@ -1149,9 +1179,41 @@ qtt_status qtt_selftest_wait(double seconds, void *stream) {
   return QTT_OK;
 }
 
+int qtt_checked_build(void) {
+#ifdef QTT_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+qtt_status qtt_check_selftest(void *stream) {
+#ifdef QTT_CHECKED
+  const cudaError_t e = launch_check_selftest(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "qtt_check_selftest");
+  return QTT_OK;
+#else
+  (void)stream;
+  return fail(QTT_ERR_UNSUPPORTED, "qtt_check_selftest: not the checked build");
+#endif
+}
+
 qtt_status qtt_sync_status(void *stream) {
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "qtt_sync_status");
+  {
+    // checked build: every translation unit's index-check word
+    int first = 0;
+    for (auto take : check_words()) {
+      int site = 0;
+      e = take(&site);
+      if (e != cudaSuccess) return cuda_fail(e, "qtt_sync_status: check word");
+      if (site != 0 && first == 0) first = site;
+    }
+    if (first != 0)
+      return fail(QTT_ERR_CHECK, "checked build: out-of-range index at site " +
+                                     std::to_string(first));
+  }
   int h = 0;
   e = tc_status_take(&h);
   int hf = 0;

@@ -201,6 +201,10 @@ struct LpEpilogue {
 qtt_status apply_lp(const qtt_op *A, qtt_dtype compute, const void *x, qtt_dtype xt, void *y,
                     qtt_dtype yt, int64_t nrhs, int64_t ld, cudaStream_t st,
                     const LpEpilogue &epi);
+#ifdef QTT_CHECKED
+cudaError_t launch_check_selftest(cudaStream_t st);
+#endif
+
 // Number of step pairs a TF32 apply of A runs on the tcgen05 tensor cores
 // under its current plan (0 when none: no TF32 tensor-core copy, fusion or
 // pairs off, or no eligible pair).

@@ -14,6 +14,7 @@
 // stored TF32-rounded by the previous step (rounding at the store instead of
 // at every use gives the same products), so no rounding happens here except
 // on the stored result.
+#include "checked.cuh"
 #include "qtt_internal.h"
 #include "step_lp.h"
 
@@ -102,7 +103,7 @@ __device__ __forceinline__ void chunk_block(const float *sb, const float *sG, co
   const int64_t bit = (int64_t)1 << s.k, low = bit - 1, npairs = s.N >> 1;
   const int64_t q = q0 + 4 * lane;
   if (q >= npairs) return;
-  const int64_t p0 = ((q & ~low) << 1) | (q & low);
+  const int64_t p0 = QTT_CK(((q & ~low) << 1) | (q & low), s.N - bit, 203);
 #pragma unroll
   for (int t = 0; t < TB; ++t) {
     const int b = b0 + t;
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(kThreads) step_f32s_kernel(StepLP s) {
     cpa_wait<kStages - 1>();
     __syncthreads();
     const float *sb = sB + cur * stage;
-    const int64_t c = t / cpr, q0 = (t % cpr) * kPC;
+    const int64_t c = QTT_CK(t / cpr, s.nrhs, 204), q0 = (t % cpr) * kPC;
     float *out = static_cast<float *>(s.out) + c * s.out_rhs_stride;
     if (b0 < s.rout) {
       switch (TB) {

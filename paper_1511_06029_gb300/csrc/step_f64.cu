@@ -15,6 +15,7 @@
 // output rank b (both row bits) and TN position pairs, giving 2 TN
 // independent FMA chains; the warp shares b, so each core element is a
 // broadcast load, and the 32 lanes read 32 consecutive pairs (coalesced).
+#include "checked.cuh"
 #include "qtt_internal.h"
 
 namespace qtt {
@@ -35,6 +36,7 @@ __device__ __forceinline__ void step_f64_tn_body(const StepF64 &s, int64_t cta, 
   const int nrb = (s.rout + by - 1) / by;
   const int b = (int)(cta % nrb) * by + ty;
   if (b >= s.rout) return;
+  c = QTT_CK(c, s.nrhs, 101);
   const int64_t npairs = s.N >> 1;
   const int64_t bit = (int64_t)1 << s.k;
   const int64_t low = bit - 1;
@@ -47,6 +49,7 @@ __device__ __forceinline__ void step_f64_tn_body(const StepF64 &s, int64_t cta, 
     const int64_t q = q0 + 32 * m;
     ok[m] = q < npairs;
     p0[m] = ((q & ~low) << 1) | (q & low);
+    if (ok[m]) p0[m] = QTT_CK(p0[m], s.N - bit, 102);  // p0 and p0 + 2^k in range
   }
   const double *in = s.in + c * s.in_rhs_stride;
   const double2 *Mb = reinterpret_cast<const double2 *>(s.M) + (int64_t)b * 2 * s.rin;
@@ -121,7 +124,9 @@ __device__ __forceinline__ void step_f64_small_body(const StepF64 &s, int64_t ct
   const int64_t low = bit - 1;
   const int64_t q = (cta / nrg) * 32 + lane;
   const bool ok = q < npairs && b < s.rout;
-  const int64_t p0 = ((q & ~low) << 1) | (q & low);
+  c = QTT_CK(c, s.nrhs, 103);
+  int64_t p0 = ((q & ~low) << 1) | (q & low);
+  if (ok) p0 = QTT_CK(p0, s.N - bit, 104);
   double acc0 = 0.0, acc1 = 0.0;
   if (ok) {
     const double *in = s.in + c * s.in_rhs_stride;

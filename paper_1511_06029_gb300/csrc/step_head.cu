@@ -20,6 +20,7 @@
 // launches.
 #include <cuda_bf16.h>
 
+#include "checked.cuh"
 #include "qtt_internal.h"
 #include "step_lp.h"
 
@@ -112,8 +113,9 @@ __global__ void __launch_bounds__(kThreads, 2) step_head_kernel(const __grid_con
   const int64_t tidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = tidx < 2 * groups;
   const int h = (int)(tidx & 1);
-  const int64_t c = blockIdx.y;
-  const int64_t pbase = (tidx >> 1) * P + h * T;  // first position of this thread
+  const int64_t c = QTT_CK(blockIdx.y, s.nrhs, 205);
+  int64_t pbase = (tidx >> 1) * P + h * T;  // first position of this thread
+  if (active) pbase = QTT_CK(pbase, s.N - T + 1, 206);  // pbase .. pbase + T - 1
   float y[kR][T], z[kR][T];
   {
     const TIN *in = static_cast<const TIN *>(s.in) + c * s.in_rhs_stride + pbase;
@@ -265,8 +267,8 @@ __global__ void __launch_bounds__(kThreads, 2) step_tail_kernel(const __grid_con
   const int64_t tidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = tidx < 2 * lowN;
   const int h = (int)(tidx & 1);
-  const int64_t plow = tidx >> 1;
-  const int64_t c = blockIdx.y;
+  const int64_t plow = active ? QTT_CK(tidx >> 1, lowN, 208) : tidx >> 1;
+  const int64_t c = QTT_CK(blockIdx.y, s.nrhs, 207);
   auto pos = [&](int q) { return plow + ((int64_t)(q + h * T) << s.k0); };
   float y[kR][T], z[kR][T];
   {

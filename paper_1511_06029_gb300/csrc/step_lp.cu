@@ -20,6 +20,7 @@
 // block (broadcast core loads, 2 x 16-byte loads per (a, j)) and read 32
 // consecutive pairs (coalesced).  Cores are packed [a][j][b padded to TB][i]
 // so the TB x 2 values of one (a, j) are contiguous.
+#include "checked.cuh"
 #include "qtt_internal.h"
 #include "step_lp.h"
 
@@ -114,7 +115,7 @@ step_lp_kernel(StepLP s) {
   const int bb = (int)(blockIdx.x % ngrp) * blockDim.y + threadIdx.y;  // rank block
   const int b0 = bb * kTB;
   if (b0 >= s.rout) return;
-  const int64_t c = blockIdx.z;
+  const int64_t c = QTT_CK(blockIdx.z, s.nrhs, 201);
   const int64_t npairs = s.N >> 1;
   const int64_t bit = (int64_t)1 << s.k;
   const int64_t low = bit - 1;
@@ -126,6 +127,7 @@ step_lp_kernel(StepLP s) {
     const int64_t q = q0 + 32 * m;
     ok[m] = q < npairs;
     p0[m] = ((q & ~low) << 1) | (q & low);
+    if (ok[m]) p0[m] = QTT_CK(p0[m], s.N - bit, 202);  // p0 and p0 + 2^k in range
   }
   const TIN *in = static_cast<const TIN *>(s.in) + c * s.in_rhs_stride;
   const TCORE *G = static_cast<const TCORE *>(s.M);

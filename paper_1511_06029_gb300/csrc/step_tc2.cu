@@ -64,6 +64,7 @@
 #include <cstdlib>
 #include <cuda_bf16.h>
 
+#include "checked.cuh"
 #include "qtt_internal.h"
 #include "step_mma.h"
 #include "tc_common.cuh"
@@ -264,11 +265,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (;; ++n, cw.next()) {
         if (cw.t >= nchunks) break;
         if (n >= S && !wait_bar(su32(&B.empty[st]), ph ^ 1u, abort)) break;
-        const int64_t q0 = cw.w * kQ;
+        // the box: quads q0 .. q0 + kQ - 1 of right-hand side c
+        const int64_t q0 = QTT_CK(cw.w * kQ, (s.N >> 2) - kQ + 1, 301);
+        const int64_t cc = QTT_CK(cw.c, s.nrhs, 302);
         const unsigned fb = su32(&B.full[st]);
         expect_tx(fb, P.stage);
         tma_load5(base32 + P.s0 + (unsigned)st * P.stage, &tin, (int)(q0 & lowmask), 0,
-                  (int)(cw.c * s.r0), 0, (int)(q0 >> s.k), fb);
+                  (int)(cc * s.r0), 0, (int)(q0 >> s.k), fb);
         if (++st == S) {
           st = 0;
           ph ^= 1u;
@@ -421,11 +424,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       fence_async_smem();
       epi_sync<kGroupThreads>(g);
       if (leader) {
-        const int64_t q0 = cw.w * kQ;
+        const int64_t q0 = QTT_CK(cw.w * kQ, (s.N >> 2) - kQ + 1, 303);
+        const int64_t cc = QTT_CK(cw.c, s.nrhs, 304);
         if constexpr (XLOG < 6)
-          tma_store3(&tout, su32(O), 0, (int)(cw.c * s.r2), (int)(q0 >> 4));
+          tma_store3(&tout, su32(O), 0, (int)(cc * s.r2), (int)(q0 >> 4));
         else
-          tma_store5(&tout, su32(O), (int)(q0 & lowmask), 0, (int)(cw.c * s.r2), 0,
+          tma_store5(&tout, su32(O), (int)(q0 & lowmask), 0, (int)(cc * s.r2), 0,
                      (int)(q0 >> s.k));
         bulk_commit();
       }

@@ -57,6 +57,7 @@
 // QTT_ERR_TIMEOUT in this file's status word, read by qtt_sync_status).
 #include <cstdlib>
 
+#include "checked.cuh"
 #include "qtt_internal.h"
 #include "step_mma.h"
 #include "tc_common.cuh"
@@ -307,9 +308,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         expect_tx(fb, 2 * P.box);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int64_t q = cw.w * kQ + 32 * h;
+          // the box: quads q .. q + 31 of right-hand side c
+          const int64_t q = QTT_CK(cw.w * kQ + 32 * h, (s.N >> 2) - 31, 311);
+          const int64_t cc = QTT_CK(cw.c, s.nrhs, 312);
           tma_load5(base32 + P.s0 + (unsigned)st * P.stage + (unsigned)h * P.boxs, &tin,
-                    (int)(q & lowmask), 0, (int)(cw.c * s.r0), 0, (int)(q >> s.k), fb);
+                    (int)(q & lowmask), 0, (int)(cc * s.r0), 0, (int)(q >> s.k), fb);
         }
         if (++st == S) {
           st = 0;
@@ -485,8 +488,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_before();
         mbar_arrive(su32(&B.dfree[g]));  // D2^T is in registers
         const int64_t qq = cw.w * kQ + 32 * qh + lane;
-        const int64_t pos = ((qq >> s.k) << (s.k + 2)) | ((int64_t)qhi << s.k) | (qq & lowmask);
-        float *y = s.out + cw.c * s.out_rhs_stride + pos;
+        // pos and pos + 2^(k+1) in range, right-hand side c in range
+        const int64_t pos = QTT_CK(((qq >> s.k) << (s.k + 2)) | ((int64_t)qhi << s.k) | (qq & lowmask),
+                                   s.N - bit1, 313);
+        float *y = s.out + QTT_CK(cw.c, s.nrhs, 314) * s.out_rhs_stride + pos;
 #pragma unroll
         for (int c = 0; c < KM / 2; ++c) {
           if (c < s.r2) {

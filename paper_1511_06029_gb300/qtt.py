@@ -26,6 +26,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libqtt.so")
 
 QTT_OK, QTT_ERR_INVALID_ARG, QTT_ERR_OOM, QTT_ERR_CUDA = 0, 1, 2, 3
 QTT_ERR_NOT_CONVERGED, QTT_ERR_TIMEOUT, QTT_ERR_UNSUPPORTED = 4, 5, 6
+QTT_ERR_CHECK = 7
 DTYPES = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3}
 PACKS = {"f32": 1 << 1, "tf32": 1 << 2, "bf16": 1 << 3}
 SOLVE_KINDS = {"direct": 0, "gmres": 1, "refine": 2}
@@ -78,6 +79,8 @@ SIGNATURES = {
     "qtt_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                             ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_size_t)]),
     "qtt_batch_tensor_ops": (_I, [_P, ctypes.POINTER(_I)]),
+    "qtt_checked_build": (_I, []),
+    "qtt_check_selftest": (_I, [_P]),
     "qtt_write_file": (_I, [ctypes.c_char_p, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "qtt_read_file": (_I, [ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(_I), _I,
                            ctypes.POINTER(_D), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),

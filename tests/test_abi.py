@@ -80,3 +80,12 @@ def test_apply_rejects_null_operator(lib):
     n = ctypes.c_int64(-1)
     assert lib.qtt_apply_tt_size(None, None, ctypes.byref(n)) == qtt.QTT_ERR_INVALID_ARG
     assert lib.qtt_apply_tt(None, None, None, None, None) == qtt.QTT_ERR_INVALID_ARG
+
+
+def test_normal_build_is_not_the_checked_build():
+    """The normal library reports itself unchecked and refuses the checked
+    build's self-test (host-side, no device work)."""
+    from paper_1511_06029_gb300 import qtt
+    lib = qtt.load_library()
+    assert lib.qtt_checked_build() == 0
+    assert lib.qtt_check_selftest(None) == qtt.QTT_ERR_UNSUPPORTED
