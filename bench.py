@@ -765,9 +765,12 @@ class BatchedRun:
         achieved = self.flops / mean_s / 1e9
         kern = f"batch_kernel<{self.variant % 100}>"
         pk = measured_peaks().get("bf16_tflops")
-        if self.info.get("tensor_ops"):
+        if self.info.get("direct_ops") and self.compute == "f32":
+            kern += (f" waves + {self.info['direct_ops']} operators through the single-operator "
+                     "apply (step_f32s_kernel)")
+        if self.info.get("direct_ops") and self.compute == "tf32":
             # operators on the tcgen05 TF32 pairs: the TF32 tensor peak governs
-            kern += (f" waves + {self.info['tensor_ops']} operators on step_tc2f_kernel "
+            kern += (f" waves + {self.info['direct_ops']} operators on step_tc2f_kernel "
                      "(tcgen05 TF32 pairs)")
             tpk = (pk or 1900.0) * TF32_PER_BF16
             return {"bound": "tensor", "kernel": kern, "achieved": achieved / 1e3, "peak": tpk,
@@ -790,7 +793,7 @@ class BatchedRun:
                 "total_rhs": sum(it["nrhs"] for it in self.items),
                 "flops_per_step_per_gpu": self.flops, "compute": self.compute,
                 "waves": self.info["waves"], "grid": self.info["grid"],
-                "tensor_core_operators": self.info.get("tensor_ops", 0),
+                "operators_applied_directly": self.info.get("direct_ops", 0),
                 "autotuned_pairs_per_lane": self.variant % 100,
                 "autotuned_chunks_per_item": (self.variant // 100) % 100,
                 "autotuned_ring_depth": self.variant // 10000,

@@ -443,11 +443,12 @@ qtt_status qtt_solve(const qtt_op *K, const qtt_op *P, const double *f,
  * core step, right-hand side, chunk of position pairs) items, each item one
  * Algorithm 2 contraction; an item waits (bounded) until its operator's
  * previous step is complete.  All waves are captured in one CUDA graph at
- * creation; qtt_batch_run replays it.  With QTT_TF32, an operator whose TF32
- * apply runs step pairs on the tcgen05 tensor cores (ranks 8..32 in its middle
- * steps, QTT_PACK_TF32) is not put in a wave: qtt_batch_run applies it with
- * that path after the graph, on the same stream.  The paper has no batched
- * form; it is the same Algorithm 2 per operator.
+ * creation; qtt_batch_run replays it.  Some operators are not put in a wave
+ * but applied with the single-operator apply after the graph, on the same
+ * stream: with QTT_TF32 every operator whose TF32 apply runs step pairs on
+ * the tcgen05 tensor cores (ranks 8..40 in its middle steps), with QTT_F32
+ * every operator with d >= 16 (one such operator fills the GPU).  The paper
+ * has no batched form; it is the same Algorithm 2 per operator.
  *   ops[i], nrhs[i] (>= 1), x[i], y[i] (device FP32, N_i x nrhs[i], leading
  *   dimension ld[i] >= N_i), bound at creation and read at every run.
  *   compute     : QTT_F32 or QTT_TF32 (operands rounded to TF32, FP32
@@ -485,9 +486,9 @@ qtt_status qtt_batch_autotune(qtt_batch *B, int reps, void *stream,
                               int *chosen, double *seconds_per_run);
 qtt_status qtt_batch_info(const qtt_batch *B, int *waves, int *variant,
                           int *grid, double *flops, size_t *scratch_bytes);
-/* Number of the batch's operators applied on the tcgen05 TF32 path instead of
- * a wave (0 unless compute is QTT_TF32). */
-qtt_status qtt_batch_tensor_ops(const qtt_batch *B, int *count);
+/* Number of the batch's operators applied with the single-operator apply
+ * instead of in a wave. */
+qtt_status qtt_batch_direct_ops(const qtt_batch *B, int *count);
 qtt_status qtt_batch_destroy(qtt_batch *B);
 
 /* ---------------------------------------------------------- solve server */

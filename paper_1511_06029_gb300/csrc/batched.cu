@@ -410,6 +410,13 @@ struct WaveDev {
 
 }  // namespace qtt
 
+namespace qtt {
+// FP32 batches: operators with d at least this large go through the
+// single-operator apply (staged FP32 steps), which keeps more of the FP32
+// pipe busy than a shared wave once one operator fills the GPU
+constexpr int kDirectMinD = 16;
+}  // namespace qtt
+
 struct qtt_batch {
   std::vector<const qtt_op *> ops;
   std::vector<int64_t> nrhs, ld;
@@ -434,9 +441,10 @@ struct qtt_batch {
   cudaGraphExec_t exec = nullptr;
   double flops = 0.0;
   int grid = 0;
-  // TF32 batches: operators whose apply runs step pairs on the tcgen05 tensor
-  // cores go through that apply after the waves, not into a wave
-  std::vector<int> tc_ops;
+  // operators applied with the single-operator apply after the waves, not in
+  // a wave: TF32 ones whose apply runs tcgen05 step pairs, FP32 ones with
+  // d >= kDirectMinD
+  std::vector<int> direct_ops;
 };
 
 namespace qtt {
@@ -484,10 +492,12 @@ qtt_status build_plan(qtt_batch *B, cudaStream_t st) {
     return r <= 16 ? 0 : r <= 24 ? 1 : r <= 32 ? 2 : 3;
   };
   std::vector<int> order;
-  B->tc_ops.clear();
+  B->direct_ops.clear();
   for (size_t i = 0; i < B->ops.size(); ++i) {
-    if (B->compute == QTT_TF32 && tf32_tc_pairs(B->ops[i]) > 0)
-      B->tc_ops.push_back((int)i);
+    const qtt_op *A = B->ops[i];
+    if ((B->compute == QTT_TF32 && tf32_tc_pairs(A) > 0) ||
+        (B->compute == QTT_F32 && A->d >= kDirectMinD))
+      B->direct_ops.push_back((int)i);
     else
       order.push_back((int)i);
   }
@@ -785,8 +795,8 @@ qtt_status qtt_batch_run(qtt_batch *B, void *stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaGraphLaunch(B->exec, st);
   if (e != cudaSuccess) return cuda_fail(e, "qtt_batch_run: graph launch");
-  for (int i : B->tc_ops) {
-    const qtt_status s = apply_lp(B->ops[i], QTT_TF32, B->x[i], QTT_F32, B->y[i], QTT_F32,
+  for (int i : B->direct_ops) {
+    const qtt_status s = apply_lp(B->ops[i], B->compute, B->x[i], QTT_F32, B->y[i], QTT_F32,
                                   B->nrhs[i], B->ld[i], st, LpEpilogue{});
     if (s != QTT_OK) return s;
   }
@@ -896,9 +906,9 @@ qtt_status qtt_batch_autotune(qtt_batch *B, int reps, void *stream, int *chosen,
   return s;
 }
 
-qtt_status qtt_batch_tensor_ops(const qtt_batch *B, int *count) {
-  if (!B || !count) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_tensor_ops: no batch");
-  *count = (int)B->tc_ops.size();
+qtt_status qtt_batch_direct_ops(const qtt_batch *B, int *count) {
+  if (!B || !count) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_direct_ops: no batch");
+  *count = (int)B->direct_ops.size();
   return QTT_OK;
 }
 

@@ -78,7 +78,7 @@ SIGNATURES = {
     "qtt_batch_autotune": (_I, [_P, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "qtt_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                             ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_size_t)]),
-    "qtt_batch_tensor_ops": (_I, [_P, ctypes.POINTER(_I)]),
+    "qtt_batch_direct_ops": (_I, [_P, ctypes.POINTER(_I)]),
     "qtt_checked_build": (_I, []),
     "qtt_check_selftest": (_I, [_P]),
     "qtt_write_file": (_I, [ctypes.c_char_p, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
@@ -657,10 +657,10 @@ class Batch:
                                              ctypes.byref(g), ctypes.byref(f), ctypes.byref(sb)),
                "qtt_batch_info")
         t = ctypes.c_int()
-        _check(load_library().qtt_batch_tensor_ops(self._h, ctypes.byref(t)),
-               "qtt_batch_tensor_ops")
+        _check(load_library().qtt_batch_direct_ops(self._h, ctypes.byref(t)),
+               "qtt_batch_direct_ops")
         return {"waves": w.value, "variant": v.value, "grid": g.value, "flops": f.value,
-                "scratch_bytes": sb.value, "tensor_ops": t.value}
+                "scratch_bytes": sb.value, "direct_ops": t.value}
 
     def close(self):
         if self._h is not None:
