@@ -77,15 +77,21 @@ typedef enum { QTT_F64 = 0, QTT_F32 = 1, QTT_TF32 = 2, QTT_BF16 = 3 } qtt_dtype;
  *   d      : number of cores, 1 <= d <= 30.
  *   ranks  : host array of d+1 ints, ranks[0] = ranks[d] = 1, 1 <= ranks[k]
  *            <= 4096.
- *   cores  : host array, sum_k 4 ranks[k] ranks[k+1] doubles (layout above).
- *            Copied; the caller keeps ownership.
+ *   cores  : host array of d pointers; cores[k] holds the 4 ranks[k]
+ *            ranks[k+1] doubles of core k (layout above).  Copied; the
+ *            caller keeps ownership.
  *   precision_mask : QTT_PACK_* bits for the reduced-precision copies.
  *   stream : stream for the uploads; the call returns after they finish.
  * Errors: QTT_ERR_INVALID_ARG (bad d, ranks, NULL pointers),
  *         QTT_ERR_OOM, QTT_ERR_CUDA. */
 qtt_status qtt_create(qtt_op **out, int d, const int *ranks,
-                      const double *cores, unsigned precision_mask,
+                      const double *const *cores, unsigned precision_mask,
                       void *stream);
+/* qtt_create_flat -- the same, with the cores concatenated in one host array
+ * (core k at offset sum_{l<k} 4 ranks[l] ranks[l+1]). */
+qtt_status qtt_create_flat(qtt_op **out, int d, const int *ranks,
+                           const double *cores, unsigned precision_mask,
+                           void *stream);
 
 /* The .qtt operator file (no counterpart in the paper): a 24-byte header --
  * magic "QTT1", format version 1, d, element type 0 (FP64), core layout 0

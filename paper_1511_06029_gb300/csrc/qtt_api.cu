@@ -684,8 +684,26 @@ const char *qtt_last_error(void) { return g_last_error.c_str(); }
 
 uint64_t qtt_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
-qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *cores,
+qtt_status qtt_create(qtt_op **out, int d, const int *ranks, const double *const *cores,
                       unsigned precision_mask, void *stream) {
+  if (!out) return fail(QTT_ERR_INVALID_ARG, "qtt_create: out is NULL");
+  *out = nullptr;
+  if (d < 1 || d > 30) return fail(QTT_ERR_INVALID_ARG, "qtt_create: d must be in [1, 30]");
+  if (!ranks || !cores) return fail(QTT_ERR_INVALID_ARG, "qtt_create: NULL ranks or cores");
+  for (int k = 0; k <= d; ++k)
+    if (ranks[k] < 1 || ranks[k] > 4096)
+      return fail(QTT_ERR_INVALID_ARG, "qtt_create: ranks must be in [1, 4096]");
+  std::vector<double> flat;
+  for (int k = 0; k < d; ++k) {
+    if (!cores[k]) return fail(QTT_ERR_INVALID_ARG, "qtt_create: NULL core pointer");
+    const size_t n = (size_t)4 * ranks[k] * ranks[k + 1];
+    flat.insert(flat.end(), cores[k], cores[k] + n);
+  }
+  return qtt_create_flat(out, d, ranks, flat.data(), precision_mask, stream);
+}
+
+qtt_status qtt_create_flat(qtt_op **out, int d, const int *ranks, const double *cores,
+                           unsigned precision_mask, void *stream) {
   if (!out) return fail(QTT_ERR_INVALID_ARG, "qtt_create: out is NULL");
   *out = nullptr;
   if (d < 1 || d > 30) return fail(QTT_ERR_INVALID_ARG, "qtt_create: d must be in [1, 30]");

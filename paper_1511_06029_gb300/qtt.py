@@ -35,6 +35,7 @@ SOLVE_KINDS = {"direct": 0, "gmres": 1, "refine": 2}
 _I, _U, _L, _D, _P = ctypes.c_int, ctypes.c_uint, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 SIGNATURES = {
     "qtt_create": (_I, [ctypes.POINTER(_P), _I, _P, _P, _U, _P]),
+    "qtt_create_flat": (_I, [ctypes.POINTER(_P), _I, _P, _P, _U, _P]),
     "qtt_destroy": (_I, [_P]),
     "qtt_op_d": (_I, [_P]),
     "qtt_op_rank": (_I, [_P, _I]),
@@ -222,14 +223,15 @@ class Operator:
         _torch()
         ranks = np.ascontiguousarray(np.asarray(data.ranks, dtype=np.int32))
         d = len(ranks) - 1
-        flat = np.ascontiguousarray(np.concatenate(
-            [np.ascontiguousarray(c, dtype=np.float64).ravel() for c in data.cores]))
+        cores = [np.ascontiguousarray(c, dtype=np.float64) for c in data.cores]
+        flat = np.ascontiguousarray(np.concatenate([c.ravel() for c in cores]))
         mask = 0
         for p in packs:
             mask |= PACKS[p]
         h = ctypes.c_void_p()
+        ptrs = (ctypes.c_void_p * d)(*[c.ctypes.data for c in cores])
         _check(lib.qtt_create(ctypes.byref(h), d, ranks.ctypes.data_as(_P),
-                              flat.ctypes.data_as(_P), mask, _stream_handle(stream)),
+                              ctypes.cast(ptrs, _P), mask, _stream_handle(stream)),
                "qtt_create")
         self._h = h
         self.d = d

@@ -46,10 +46,17 @@ static int host_checks(void) {
   qtt_op *A = NULL;
   const int bad_ranks[3] = {2, 3, 1};
   const double cores[64] = {0};
-  CHECK(qtt_create(&A, 2, bad_ranks, cores, 0, NULL) == QTT_ERR_INVALID_ARG,
-        "qtt_create accepted ranks[0] = 2");
-  CHECK(A == NULL, "qtt_create left a handle after failing");
-  CHECK(qtt_create(&A, 0, bad_ranks, cores, 0, NULL) == QTT_ERR_INVALID_ARG, "d = 0 accepted");
+  const double *core_ptrs[2] = {cores, NULL};
+  CHECK(qtt_create_flat(&A, 2, bad_ranks, cores, 0, NULL) == QTT_ERR_INVALID_ARG,
+        "qtt_create_flat accepted ranks[0] = 2");
+  CHECK(A == NULL, "qtt_create_flat left a handle after failing");
+  CHECK(qtt_create(&A, 0, bad_ranks, core_ptrs, 0, NULL) == QTT_ERR_INVALID_ARG,
+        "d = 0 accepted");
+  {
+    const int ranks[3] = {1, 2, 1};
+    CHECK(qtt_create(&A, 2, ranks, core_ptrs, 0, NULL) == QTT_ERR_INVALID_ARG,
+          "qtt_create accepted a NULL core pointer");
+  }
   CHECK(qtt_destroy(NULL) == QTT_OK, "qtt_destroy(NULL) failed");
   CHECK(strcmp(qtt_status_string(QTT_OK), "ok") == 0, "status string of QTT_OK");
   CHECK(qtt_apply(NULL, NULL, NULL, 1, 1, QTT_F64, QTT_F64, NULL) == QTT_ERR_INVALID_ARG,
@@ -75,8 +82,18 @@ static int device_checks(const char *tmpdir) {
   for (int64_t e = 0; e < np; ++e) cores[e] = next_uniform() * 0.3;
   for (int64_t e = 0; e < N * NRHS; ++e) x[e] = next_uniform();
 
+  /* the per-core form of qtt_create: one pointer per core */
+  const double *core_ptrs[D];
+  {
+    int64_t off = 0;
+    for (int k = 0; k < D; ++k) {
+      core_ptrs[k] = cores + off;
+      off += 4 * (int64_t)ranks[k] * ranks[k + 1];
+    }
+  }
   qtt_op *A = NULL;
-  CHECK(qtt_create(&A, D, ranks, cores, 0, NULL) == QTT_OK, "qtt_create: %s", qtt_last_error());
+  CHECK(qtt_create(&A, D, ranks, core_ptrs, 0, NULL) == QTT_OK, "qtt_create: %s",
+        qtt_last_error());
   CHECK(qtt_op_d(A) == D && qtt_op_rank(A, 5) == ranks[5], "operator queries");
   double *xd = NULL, *yd = NULL;
   CHECK(cudaMalloc((void **)&xd, sizeof(double) * N * NRHS) == cudaSuccess, "cudaMalloc x");

@@ -57,8 +57,8 @@ def test_create_rejects_bad_arguments_without_gpu(lib):
 
     def create(d, ranks, mask=0):
         r = np.asarray(ranks, dtype=np.int32)
-        return lib.qtt_create(ctypes.byref(h), d, r.ctypes.data_as(P), cores.ctypes.data_as(P),
-                              mask, None)
+        return lib.qtt_create_flat(ctypes.byref(h), d, r.ctypes.data_as(P),
+                                   cores.ctypes.data_as(P), mask, None)
 
     assert create(0, [1]) == qtt.QTT_ERR_INVALID_ARG
     assert create(31, [1] * 32) == qtt.QTT_ERR_INVALID_ARG
@@ -69,6 +69,12 @@ def test_create_rejects_bad_arguments_without_gpu(lib):
     assert h.value is None
     assert lib.qtt_create(None, 2, None, None, 0, None) == qtt.QTT_ERR_INVALID_ARG
     assert b"out" in lib.qtt_last_error()
+    # the per-core form: a NULL core pointer is refused before anything is read
+    r = np.asarray([1, 2, 1], dtype=np.int32)
+    ptrs = (ctypes.c_void_p * 2)(cores.ctypes.data, None)
+    assert lib.qtt_create(ctypes.byref(h), 2, r.ctypes.data_as(P), ctypes.cast(ptrs, P), 0,
+                          None) == qtt.QTT_ERR_INVALID_ARG
+    assert b"NULL core" in lib.qtt_last_error() and h.value is None
 
 
 def test_apply_rejects_null_operator(lib):
