@@ -10,7 +10,10 @@ times, on samples the oracle can afford:
   operators and one right-hand side of a d = 20 operator against the oracle;
 * the BF16 apply of the d = 21, r_max = 48 operator to 64 right-hand sides
   (head kernel, tcgen05 step pairs, single steps): two of the 64 outputs
-  against the oracle's FP64 apply of the same BF16 inputs.
+  against the oracle's FP64 apply of the same BF16 inputs;
+* the FP32, TF32 and BF16 applies of the d = 24, r_max = 32 operator to one
+  right-hand side under the tuned plan: 2048 sampled outputs against the
+  oracle's entry formula.
 """
 import math
 
@@ -110,3 +113,37 @@ def test_bf16_apply_full_size_samples(qtt):
         ref = oracle.apply(data, xc)
         err = rel_l2(y[c:c + 1].double().cpu().numpy(), ref)
         assert err <= 4 * math.sqrt(data.d) * 2.0 ** -8, (c, err)
+
+
+@pytest.mark.parametrize("compute", ["f32", "tf32", "bf16"])
+def test_low_precision_apply_d24_sampled_outputs(qtt, compute):
+    """d = 24, r_max = 32 in FP32, TF32 and BF16, in the launch configuration
+    the benchmark times (the plan the library's tuner picks for one
+    right-hand side).  x has 6 nonzeros (values representable in the input
+    type), so each output is y(i) = sum_s x(j_s) A(i, j_s); 2048 sampled
+    outputs are checked against the oracle's entry formula within the
+    arithmetic's bound 4 sqrt(d) u."""
+    import torch
+    dt = {"f32": torch.float32, "tf32": torch.float32, "bf16": torch.bfloat16}[compute]
+    u = {"f32": 2.0 ** -24, "tf32": 2.0 ** -11, "bf16": 2.0 ** -8}[compute]
+    op_data = inputs.synthetic_operator(24, 32, 2)
+    N = op_data.N
+    rng = np.random.default_rng(91)
+    J = rng.choice(N, size=6, replace=False)
+    c = torch.from_numpy(rng.standard_normal(6)).to(dt)
+    x = torch.zeros(1, N, dtype=dt, device="cuda")
+    x[0, torch.from_numpy(J).cuda()] = c.cuda()
+    op = qtt.Operator(op_data, packs=(compute,))
+    op.autotune(1, compute, reps=1)
+    y = op.apply(x, compute=compute)
+    qtt.sync_status()
+    y = y[0].double().cpu().numpy()
+    op.close()
+    I = np.concatenate([rng.integers(0, N, size=2040),
+                        [0, N - 1, 1, N - 2, 2 ** 23, 4321, 2 ** 23 - 1, 7]])
+    cd = c.double().numpy()
+    ref = np.zeros(I.shape[0])
+    for s in range(6):
+        ref += cd[s] * oracle.entries(op_data, I, np.full(I.shape[0], J[s]))
+    err = rel_l2(y[I], ref)
+    assert err <= 4 * math.sqrt(op_data.d) * u, (compute, err)
