@@ -1234,11 +1234,14 @@ qtt_status qtt_sync_status(void *stream) {
   }
   int h = 0;
   e = tc_status_take(&h);
-  int hf = 0;
+  int hf = 0, ht = 0;
   if (e == cudaSuccess) e = tcf_status_take(&hf);
+  if (e == cudaSuccess) e = tail_status_take(&ht);
   if (e != cudaSuccess) return cuda_fail(e, "qtt_sync_status: device status word");
   if (h != 0 || hf != 0)
     return fail(QTT_ERR_TIMEOUT, "tensor-core kernel: an mbarrier wait ran out of its budget");
+  if (ht != 0)
+    return fail(QTT_ERR_TIMEOUT, "staged tail kernel: an mbarrier wait ran out of its budget");
   return QTT_OK;
 }
 

@@ -23,6 +23,7 @@
 #include "checked.cuh"
 #include "qtt_internal.h"
 #include "step_lp.h"
+#include "tc_common.cuh"
 
 namespace qtt {
 namespace {
@@ -256,31 +257,20 @@ __device__ __forceinline__ void st_acc(double *p, float v) { *p = (double)v; }
 __device__ __forceinline__ void st_acc(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st_acc(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
+// Steps d-m .. d-1 on one lane's half of a group: y[a][q] holds plane a of
+// y_{d-m} (rounded to the mode's precision) at the lane's positions
+// p + (q + h T) 2^(d-m); on return z[0][q] is the FP32 sum of the last step
+// (r_d = 1) at those positions.  Steps d-m .. d-2 run in registers, step d-1
+// (the top bit, = h) exchanges halves with the partner lane by shuffles, so
+// all 32 lanes of the warp call it together.  Every output is summed over
+// (a, j) in ascending order, intermediates rounded as the one-step kernel
+// stores them.
 // HALF: the ranks are 8, 4, 2, 1 (M = 3), known at compile time (as in the
 // head kernel); otherwise they come from s.r (every rank <= 8).
-template <int MODE, typename TMID, typename TOUT, int M, bool HALF>
-__global__ void __launch_bounds__(kThreads, 2) step_tail_kernel(const __grid_constant__ StepTail s) {
-  static_assert(!HALF || M == 3, "the halving profile has three steps");
-  constexpr int P = 1 << M;
-  constexpr int T = P / 2;
-  const int64_t lowN = (int64_t)1 << s.k0;      // positions below the tail's bits
-  const int64_t tidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = tidx < 2 * lowN;
-  const int h = (int)(tidx & 1);
-  const int64_t plow = active ? QTT_CK(tidx >> 1, lowN, 208) : tidx >> 1;
-  const int64_t c = QTT_CK(blockIdx.y, s.nrhs, 207);
-  auto pos = [&](int q) { return plow + ((int64_t)(q + h * T) << s.k0); };
-  float y[kR][T], z[kR][T];
-  {
-    const TMID *in = static_cast<const TMID *>(s.in) + c * s.in_rhs_stride;
-#pragma unroll
-    for (int a = 0; a < kR; ++a)
-#pragma unroll
-      for (int q = 0; q < T; ++q)
-        y[a][q] = active && a < (HALF ? 8 : s.r[0])
-                      ? round_mode<MODE>(to_f(in[(int64_t)a * s.N + pos(q)]))
-                      : 0.0f;
-  }
+template <int MODE, int M, bool HALF>
+__device__ __forceinline__ void tail_math(const StepTail &s, int h, float (&y)[kR][1 << (M - 1)],
+                                          float (&z)[kR][1 << (M - 1)]) {
+  constexpr int T = 1 << (M - 1);
   int rin = HALF ? 8 : s.r[0];
 #pragma unroll
   for (int k = 0; k < M; ++k) {
@@ -334,22 +324,209 @@ __global__ void __launch_bounds__(kThreads, 2) step_tail_kernel(const __grid_con
     }
     rin = rout;
   }
-  if (!active) return;
-  // r_d = 1: the last step's accumulators z[0][q] are y at pos(q)
+}
+
+// The last step's accumulator z at position p of right-hand side c, through
+// the one-step kernel's output conversion and epilogue.
+template <typename TOUT>
+__device__ __forceinline__ void tail_store(const StepTail &s, int64_t c, int64_t p, float z) {
   TOUT *out = static_cast<TOUT *>(s.out) + c * s.out_rhs_stride;
   if (s.epi) {
     const TOUT *u = s.u ? static_cast<const TOUT *>(s.u) + c * s.u_rhs_stride : nullptr;
     const TOUT *v = s.v ? static_cast<const TOUT *>(s.v) + c * s.u_rhs_stride : nullptr;
-#pragma unroll
-    for (int q = 0; q < T; ++q) st_out(out + pos(q), tail_epi(u, v, pos(q), s, z[0][q]));
+    st_out(out + p, tail_epi(u, v, p, s, z));
   } else {
-#pragma unroll
-    for (int q = 0; q < T; ++q) st_acc(out + pos(q), z[0][q]);
+    st_acc(out + p, z);
   }
+}
+
+// One thread per (low position, half), plain loads: the form for small
+// problems and unaligned intermediates.
+template <int MODE, typename TMID, typename TOUT, int M, bool HALF>
+__global__ void __launch_bounds__(kThreads, 2) step_tail_kernel(const __grid_constant__ StepTail s) {
+  static_assert(!HALF || M == 3, "the halving profile has three steps");
+  constexpr int P = 1 << M;
+  constexpr int T = P / 2;
+  const int64_t lowN = (int64_t)1 << s.k0;      // positions below the tail's bits
+  const int64_t tidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = tidx < 2 * lowN;
+  const int h = (int)(tidx & 1);
+  const int64_t plow = active ? QTT_CK(tidx >> 1, lowN, 208) : tidx >> 1;
+  const int64_t c = QTT_CK(blockIdx.y, s.nrhs, 207);
+  auto pos = [&](int q) { return plow + ((int64_t)(q + h * T) << s.k0); };
+  float y[kR][T], z[kR][T];
+  {
+    const TMID *in = static_cast<const TMID *>(s.in) + c * s.in_rhs_stride;
+#pragma unroll
+    for (int a = 0; a < kR; ++a)
+#pragma unroll
+      for (int q = 0; q < T; ++q)
+        y[a][q] = active && a < (HALF ? 8 : s.r[0])
+                      ? round_mode<MODE>(to_f(in[(int64_t)a * s.N + pos(q)]))
+                      : 0.0f;
+  }
+  tail_math<MODE, M, HALF>(s, h, y, z);
+  if (!active) return;
+  // r_d = 1: the last step's accumulators z[0][q] are y at pos(q)
+#pragma unroll
+  for (int q = 0; q < T; ++q) tail_store<TOUT>(s, c, pos(q), z[0][q]);
+}
+
+// ------------------------------------------------------- staged tail
+// The plain tail kernel reads, per warp, 2^m r_{d-m} runs of 64 bytes that
+// lie 2^(d-m) positions apart; with every SM doing the same, the DRAM serves
+// short runs from many rows at once.  The staged form is persistent (one CTA
+// per SM): a tile is kTailPos consecutive low positions of one right-hand
+// side, and one producer thread brings each of its r_{d-m} 2^m runs into
+// shared memory with one bulk copy (kTailPos elements: 1 KB in FP32, 512
+// bytes in BF16), kTailStages tiles ahead.  The compute warps take lane
+// pairs as the plain kernel does, read their values from shared memory and
+// run the same arithmetic (tail_math), so the two forms agree bitwise.
+//
+// Every wait is bounded; a compute warp decides uniformly (all lanes) to
+// stop, and the producer, once stopped, waits (bounded) for its copies in
+// flight before the CTA leaves.  A timeout is recorded in g_tail_status.
+constexpr int kTailPos = 256;                    // low positions per tile
+constexpr int kTailCompute = 2 * kTailPos;       // two lanes per position
+constexpr int kTailThreads = kTailCompute + 32;  // + the producer warp
+constexpr int kTailMaxStages = 8;
+constexpr unsigned kTailSmem = 200 * 1024;
+
+__device__ int g_tail_status = 0;
+
+// Row pitch of a staged run: kTailPos elements plus 64/T bytes, so that the
+// two lanes of a pair (rows T apart) read banks 16 words apart.
+template <typename TMID, int T>
+__host__ __device__ constexpr unsigned tail_row_bytes() {
+  return kTailPos * (unsigned)sizeof(TMID) + 64u / T;
+}
+
+template <int MODE, typename TMID, typename TOUT, int M, bool HALF>
+__global__ void __launch_bounds__(kTailThreads, 1)
+    step_tail_staged_kernel(const __grid_constant__ StepTail s, int stages, int64_t tiles) {
+  using namespace tcx;
+  static_assert(!HALF || M == 3, "the halving profile has three steps");
+  constexpr int P = 1 << M;
+  constexpr int T = P / 2;
+  constexpr unsigned row = tail_row_bytes<TMID, T>();
+  extern __shared__ __align__(128) unsigned char tile_smem[];
+  __shared__ __align__(8) uint64_t full[kTailMaxStages], empty[kTailMaxStages];
+  __shared__ int abort_flag;
+  const int r0 = HALF ? 8 : s.r[0];
+  const unsigned stage_bytes = (unsigned)(r0 * P) * row;
+  const int64_t tpr = ((int64_t)1 << s.k0) / kTailPos;  // tiles per right-hand side
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int i = 0; i < stages; ++i) {
+      mbar_init(su32(&full[i]), 1);
+      mbar_init(su32(&empty[i]), kTailCompute / 32);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  volatile int *abort = &abort_flag;
+  const unsigned sbase = su32(tile_smem);
+
+  if (tid >= kTailCompute) {
+    if (tid != kTailCompute) return;
+    // producer: tile t = (c, w), runs (a, q) at a N + q 2^k0 + w kTailPos
+    int64_t n = 0;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++n) {
+      const int st = (int)(n % stages);
+      if (n >= stages && !wait_bar(su32(&empty[st]), (unsigned)(n / stages - 1) & 1u, abort)) break;
+      const int64_t c = QTT_CK(t / tpr, s.nrhs, 209);
+      const int64_t w = t % tpr;
+      const TMID *src = static_cast<const TMID *>(s.in) + c * s.in_rhs_stride + w * kTailPos;
+      const unsigned fb = su32(&full[st]);
+      expect_tx(fb, (unsigned)(r0 * P) * kTailPos * (unsigned)sizeof(TMID));
+      for (int a = 0; a < r0; ++a)
+        for (int q = 0; q < P; ++q)
+          bulk_load1d(sbase + (unsigned)st * stage_bytes + (unsigned)(a * P + q) * row,
+                   src + (int64_t)a * s.N + ((int64_t)q << s.k0),
+                   kTailPos * (unsigned)sizeof(TMID), fb);
+    }
+    if (*abort) {
+      volatile int never = 0;
+      for (int64_t m = n - stages < 0 ? 0 : n - stages; m < n; ++m)
+        wait_bar(su32(&full[m % stages]), (unsigned)(m / stages) & 1u, &never);
+      atomicCAS(&g_tail_status, 0, (int)QTT_ERR_TIMEOUT);
+    }
+    return;
+  }
+  // compute lanes: pair (2 l, 2 l + 1) holds low position l of the tile
+  const int h = tid & 1;
+  const int pl = tid >> 1;
+  int64_t n = 0;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++n) {
+    const int st = (int)(n % stages);
+    const bool ok = wait_bar(su32(&full[st]), (unsigned)(n / stages) & 1u, abort);
+    if (!__all_sync(0xffffffffu, ok)) {
+      *abort = 1;
+      break;
+    }
+    const unsigned char *stg = tile_smem + (size_t)st * stage_bytes + (size_t)pl * sizeof(TMID);
+    float y[kR][T], z[kR][T];
+#pragma unroll
+    for (int a = 0; a < kR; ++a)
+#pragma unroll
+      for (int q = 0; q < T; ++q)
+        y[a][q] = a < r0 ? round_mode<MODE>(to_f(*reinterpret_cast<const TMID *>(
+                               stg + (size_t)(a * P + q + h * T) * row)))
+                         : 0.0f;
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(su32(&empty[st]));
+    tail_math<MODE, M, HALF>(s, h, y, z);
+    const int64_t c = t / tpr;
+    const int64_t plow = (t % tpr) * kTailPos + pl;
+#pragma unroll
+    for (int q = 0; q < T; ++q)
+      tail_store<TOUT>(s, c, plow + ((int64_t)(q + h * T) << s.k0), z[0][q]);
+  }
+  if (*abort && tid == 0) atomicCAS(&g_tail_status, 0, (int)QTT_ERR_TIMEOUT);
+}
+
+template <int MODE, typename TMID, typename TOUT, int M, bool HALF>
+cudaError_t launch_tail_staged(const StepTail &s, cudaStream_t st) {
+  constexpr int T = 1 << (M - 1);
+  const int r0 = HALF ? 8 : s.r[0];
+  const unsigned stage_bytes = (unsigned)(r0 * 2 * T) * tail_row_bytes<TMID, T>();
+  int stages = (int)(kTailSmem / stage_bytes);
+  if (stages > kTailMaxStages) stages = kTailMaxStages;
+  if (stages < 2) return cudaErrorNotSupported;
+  static cudaError_t attr =
+      cudaFuncSetAttribute(step_tail_staged_kernel<MODE, TMID, TOUT, M, HALF>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem);
+  if (attr != cudaSuccess) return attr;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (((int64_t)1 << s.k0) / kTailPos) * s.nrhs;
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
+  step_tail_staged_kernel<MODE, TMID, TOUT, M, HALF>
+      <<<grid, kTailThreads, (size_t)stages * stage_bytes, st>>>(s, stages, tiles);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// The staged form needs whole tiles (2^k0 a multiple of kTailPos) and every
+// run 16-byte aligned: the intermediate's base, plane and right-hand-side
+// strides in bytes multiples of 16.
+template <typename TMID>
+bool tail_staged_eligible(const StepTail &s) {
+  const int64_t e = (int64_t)sizeof(TMID);
+  return s.k0 >= 8 && (reinterpret_cast<uintptr_t>(s.in) & 15) == 0 && (s.N * e) % 16 == 0 &&
+         (s.in_rhs_stride * e) % 16 == 0 && s.nrhs >= 1;
 }
 
 template <int MODE, typename TMID, typename TOUT>
 cudaError_t launch_tail_t(const StepTail &s, cudaStream_t st) {
+  if (tail_staged_eligible<TMID>(s)) {
+    if (s.m == 2) return launch_tail_staged<MODE, TMID, TOUT, 2, false>(s, st);
+    if (s.r[0] == 8 && s.r[1] == 4 && s.r[2] == 2)
+      return launch_tail_staged<MODE, TMID, TOUT, 3, true>(s, st);
+    return launch_tail_staged<MODE, TMID, TOUT, 3, false>(s, st);
+  }
   const int64_t lanes = (int64_t)2 << s.k0;
   const unsigned gx = (unsigned)((lanes + kThreads - 1) / kThreads);
   for (int64_t c0 = 0; c0 < s.nrhs; c0 += 65535) {
@@ -398,6 +575,13 @@ cudaError_t launch_step_tail(const StepTail &s, cudaStream_t st) {
     case LP_BF16: return tail_by_output<LP_BF16, __nv_bfloat16>(s, st);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t tail_status_take(int *status) {
+  int zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(status, g_tail_status, sizeof(int));
+  if (e == cudaSuccess && *status != 0) e = cudaMemcpyToSymbol(g_tail_status, &zero, sizeof(int));
+  return e;
 }
 
 int head_steps(const int *ranks, int d) {

@@ -81,6 +81,8 @@ struct StepTail {
 // Steps the tail kernel takes (0: none), given the head's steps.
 int tail_steps(const int *ranks, int d, int head);
 cudaError_t launch_step_tail(const StepTail &s, cudaStream_t st);
+// Reads and clears the staged tail kernel's timeout word (0: none).
+cudaError_t tail_status_take(int *status);
 
 // Staged (cp.async, persistent) FP32/TF32 step for intermediate-to-
 // intermediate steps with k >= 2 -- see step_f32s.cu.

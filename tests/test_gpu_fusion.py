@@ -1,11 +1,18 @@
 """Multi-step launches against one launch per step.
 
 The head kernel (steps 0 .. m-1 in registers, ranks <= 8) and the tail
-kernel (the last steps, ranks <= 8, writing y) follow the one-step kernel's
+kernel (the last steps, ranks <= 8, writing y; plain loads below 256 low
+positions, bulk-copy staging from there) follow the one-step kernel's
 numerics step by step, so their result must be bitwise the unfused one in
 every reduced precision and for every input and output type.  The
 unfused reference runs in a child process with QTT_NO_FUSION=1 (the switch
-is read once per process); one child computes every case."""
+is read once per process); one child computes every case.
+
+The cases of the staged tail kernel (2^(d-m) >= 256) run both sides with
+QTT_NO_TENSOR_CORES=1: unfused, the tail's steps of rank >= 4 would
+otherwise go to the BF16 tensor-core single-step kernel, whose FP32 sums
+run in another order (so a rare BF16 rounding differs at a million
+outputs), and a fused run would take tensor-core step pairs."""
 import itertools
 import os
 import pickle
@@ -31,7 +38,19 @@ CASES = [
     ([1, 2, 4, 8, 12, 12, 8, 4, 2, 1], 2),   # head, three single steps, tail of 3
     ([1, 4, 8, 12, 6, 3, 1], 3),    # head of 2, two single steps, tail of 2
 ]
+# 2^(d-m) >= 256 low positions: the staged (bulk-copy) tail kernel; both
+# sides without tensor cores
+STAGED = [
+    ([1, 2, 4, 8, 8, 8, 8, 8, 8, 8, 4, 2, 1], 2),       # d = 12, tail 8-4-2-1
+    ([1, 2, 4, 8, 8, 8, 8, 8, 12, 8, 6, 1], 3),         # d = 11, tail of 2
+    ([1, 4, 8, 8, 8, 8, 8, 8, 8, 8, 7, 3, 1], 1),       # d = 12, tail 8-7-3-1
+    ([1, 2, 4] + [8] * 12 + [8, 4, 2, 1], 16),          # d = 18: the stage ring wraps
+]
+NPLAIN = len(CASES)
+CASES = CASES + STAGED
 GRID = list(itertools.product(range(len(CASES)), ["f32", "tf32", "bf16"], ["f64", "f32", "bf16"]))
+PLAIN = [i for i, g in enumerate(GRID) if g[0] < NPLAIN]
+NO_TC = [i for i, g in enumerate(GRID) if g[0] >= NPLAIN]
 
 CHILD = r"""
 import pickle, sys, numpy as np, torch
@@ -65,19 +84,32 @@ def qtt():
     return q
 
 
-@pytest.fixture(scope="module")
-def unfused(tmp_path_factory):
-    d = tmp_path_factory.mktemp("fusion")
-    spec, out = d / "specs.pkl", d / "unfused.pkl"
-    pickle.dump([_spec(*g) for g in GRID], open(spec, "wb"))
-    env = dict(os.environ, QTT_NO_FUSION="1")
+def _run_child(tmp, name, idxs, env_extra):
+    spec, out = tmp / (name + "_specs.pkl"), tmp / (name + ".pkl")
+    pickle.dump([_spec(*GRID[i]) for i in idxs], open(spec, "wb"))
+    env = dict(os.environ, **env_extra)
     r = subprocess.run([sys.executable, "-c", CHILD, ROOT, str(spec), str(out)], env=env,
                        capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
-    return pickle.load(open(out, "rb"))
+    return dict(zip(idxs, pickle.load(open(out, "rb"))))
 
 
-@pytest.mark.parametrize("idx", range(len(GRID)))
+@pytest.fixture(scope="module")
+def unfused(tmp_path_factory):
+    d = tmp_path_factory.mktemp("fusion")
+    ref = _run_child(d, "unfused", PLAIN, {"QTT_NO_FUSION": "1"})
+    ref.update(_run_child(d, "unfused_no_tc", NO_TC,
+                          {"QTT_NO_FUSION": "1", "QTT_NO_TENSOR_CORES": "1"}))
+    return ref
+
+
+@pytest.fixture(scope="module")
+def fused_no_tc(tmp_path_factory):
+    return _run_child(tmp_path_factory.mktemp("fusion_no_tc"), "fused_no_tc", NO_TC,
+                      {"QTT_NO_TENSOR_CORES": "1"})
+
+
+@pytest.mark.parametrize("idx", PLAIN)
 def test_head_is_bitwise_the_unfused_sweep(qtt, unfused, idx):
     import torch
     sp = _spec(*GRID[idx])
@@ -87,3 +119,9 @@ def test_head_is_bitwise_the_unfused_sweep(qtt, unfused, idx):
     fused = op.apply(x, compute=sp["compute"]).double().cpu().numpy()
     op.close()
     assert np.array_equal(fused.view(np.uint64), unfused[idx].view(np.uint64))
+
+
+@pytest.mark.parametrize("idx", NO_TC)
+def test_staged_tail_is_bitwise_the_unfused_sweep(qtt, unfused, fused_no_tc, idx):
+    a, b = fused_no_tc[idx], unfused[idx]
+    assert a.shape == b.shape and np.array_equal(a.view(np.uint64), b.view(np.uint64))
