@@ -24,6 +24,7 @@
 #include "qtt_internal.h"
 #include "step_lp.h"
 #include "tc_common.cuh"
+#include "tf32.cuh"
 
 namespace qtt {
 namespace {
@@ -31,17 +32,9 @@ namespace {
 constexpr int kR = kHeadMaxRank;  // register tile bound on every rank
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ float tf32_rne(float x) {
-  unsigned u = __float_as_uint(x);
-  if ((u & 0x7f800000u) != 0x7f800000u) {
-    u += 0x0fffu + ((u >> 13) & 1u);
-    u &= 0xffffe000u;
-  }
-  return __uint_as_float(u);
-}
 template <int MODE>
 __device__ __forceinline__ float round_mode(float v) {
-  if (MODE == LP_TF32) return tf32_rne(v);
+  if (MODE == LP_TF32) return tf32_rn(v);
   if (MODE == LP_BF16) return __bfloat162float(__float2bfloat16_rn(v));
   return v;
 }
@@ -341,7 +334,9 @@ __device__ __forceinline__ void tail_store(const StepTail &s, int64_t c, int64_t
 }
 
 // One thread per (low position, half), plain loads: the form for small
-// problems and unaligned intermediates.
+// problems and unaligned intermediates.  The intermediate arrives in the
+// mode's precision (every kernel that writes one rounds it), so it is read
+// as it is.
 template <int MODE, typename TMID, typename TOUT, int M, bool HALF>
 __global__ void __launch_bounds__(kThreads, 2) step_tail_kernel(const __grid_constant__ StepTail s) {
   static_assert(!HALF || M == 3, "the halving profile has three steps");
@@ -361,9 +356,7 @@ __global__ void __launch_bounds__(kThreads, 2) step_tail_kernel(const __grid_con
     for (int a = 0; a < kR; ++a)
 #pragma unroll
       for (int q = 0; q < T; ++q)
-        y[a][q] = active && a < (HALF ? 8 : s.r[0])
-                      ? round_mode<MODE>(to_f(in[(int64_t)a * s.N + pos(q)]))
-                      : 0.0f;
+        y[a][q] = active && a < (HALF ? 8 : s.r[0]) ? to_f(in[(int64_t)a * s.N + pos(q)]) : 0.0f;
   }
   tail_math<MODE, M, HALF>(s, h, y, z);
   if (!active) return;
@@ -375,22 +368,28 @@ __global__ void __launch_bounds__(kThreads, 2) step_tail_kernel(const __grid_con
 // ------------------------------------------------------- staged tail
 // The plain tail kernel reads, per warp, 2^m r_{d-m} runs of 64 bytes that
 // lie 2^(d-m) positions apart; with every SM doing the same, the DRAM serves
-// short runs from many rows at once.  The staged form is persistent (one CTA
-// per SM): a tile is kTailPos consecutive low positions of one right-hand
-// side, and one producer thread brings each of its r_{d-m} 2^m runs into
-// shared memory with one bulk copy (kTailPos elements: 1 KB in FP32, 512
-// bytes in BF16), kTailStages tiles ahead.  The compute warps take lane
-// pairs as the plain kernel does, read their values from shared memory and
-// run the same arithmetic (tail_math), so the two forms agree bitwise.
+// short runs from many rows at once.  The staged form is persistent: a tile
+// is kTailPos consecutive low positions of one right-hand side, and one
+// producer thread per CTA brings each of its r_{d-m} 2^m runs into shared
+// memory with one bulk copy (kTailPos elements: 512 bytes in FP32, 256 in
+// BF16), `stages` tiles ahead.  Two or three CTAs share an SM (as registers
+// allow), so their compute warps, which all wake on the same barrier within
+// a CTA, do not all wait at once.  The compute warps take lane pairs as the
+// plain kernel does, read their values from shared memory and run the same
+// arithmetic (tail_math), so the two forms agree bitwise.
+//
+// The intermediate arrives in the mode's precision (every kernel that
+// writes one rounds it: BF16 storage, TF32-rounded FP32), so it is not
+// rounded again when read.
 //
 // Every wait is bounded; a compute warp decides uniformly (all lanes) to
 // stop, and the producer, once stopped, waits (bounded) for its copies in
 // flight before the CTA leaves.  A timeout is recorded in g_tail_status.
-constexpr int kTailPos = 256;                    // low positions per tile
+constexpr int kTailPos = 128;                    // low positions per tile
 constexpr int kTailCompute = 2 * kTailPos;       // two lanes per position
 constexpr int kTailThreads = kTailCompute + 32;  // + the producer warp
 constexpr int kTailMaxStages = 8;
-constexpr unsigned kTailSmem = 200 * 1024;
+constexpr unsigned kTailSmemPerSM = 210 * 1024;  // shared by the CTAs of an SM
 
 __device__ int g_tail_status = 0;
 
@@ -402,7 +401,7 @@ __host__ __device__ constexpr unsigned tail_row_bytes() {
 }
 
 template <int MODE, typename TMID, typename TOUT, int M, bool HALF>
-__global__ void __launch_bounds__(kTailThreads, 1)
+__global__ void __launch_bounds__(kTailThreads, 2)
     step_tail_staged_kernel(const __grid_constant__ StepTail s, int stages, int64_t tiles) {
   using namespace tcx;
   static_assert(!HALF || M == 3, "the halving profile has three steps");
@@ -439,12 +438,15 @@ __global__ void __launch_bounds__(kTailThreads, 1)
       const int64_t w = t % tpr;
       const TMID *src = static_cast<const TMID *>(s.in) + c * s.in_rhs_stride + w * kTailPos;
       const unsigned fb = su32(&full[st]);
+      const unsigned dst = sbase + (unsigned)st * stage_bytes;
       expect_tx(fb, (unsigned)(r0 * P) * kTailPos * (unsigned)sizeof(TMID));
-      for (int a = 0; a < r0; ++a)
+      for (int a = 0; a < r0; ++a) {
+        const TMID *sa = src + (int64_t)a * s.N;
+#pragma unroll
         for (int q = 0; q < P; ++q)
-          bulk_load1d(sbase + (unsigned)st * stage_bytes + (unsigned)(a * P + q) * row,
-                   src + (int64_t)a * s.N + ((int64_t)q << s.k0),
-                   kTailPos * (unsigned)sizeof(TMID), fb);
+          bulk_load1d(dst + (unsigned)(a * P + q) * row, sa + ((int64_t)q << s.k0),
+                      kTailPos * (unsigned)sizeof(TMID), fb);
+      }
     }
     if (*abort) {
       volatile int never = 0;
@@ -471,8 +473,8 @@ __global__ void __launch_bounds__(kTailThreads, 1)
     for (int a = 0; a < kR; ++a)
 #pragma unroll
       for (int q = 0; q < T; ++q)
-        y[a][q] = a < r0 ? round_mode<MODE>(to_f(*reinterpret_cast<const TMID *>(
-                               stg + (size_t)(a * P + q + h * T) * row)))
+        y[a][q] = a < r0 ? to_f(*reinterpret_cast<const TMID *>(
+                               stg + (size_t)(a * P + q + h * T) * row))
                          : 0.0f;
     __syncwarp();
     if ((tid & 31) == 0) mbar_arrive(su32(&empty[st]));
@@ -489,22 +491,34 @@ __global__ void __launch_bounds__(kTailThreads, 1)
 template <int MODE, typename TMID, typename TOUT, int M, bool HALF>
 cudaError_t launch_tail_staged(const StepTail &s, cudaStream_t st) {
   constexpr int T = 1 << (M - 1);
+  auto kern = step_tail_staged_kernel<MODE, TMID, TOUT, M, HALF>;
   const int r0 = HALF ? 8 : s.r[0];
   const unsigned stage_bytes = (unsigned)(r0 * 2 * T) * tail_row_bytes<TMID, T>();
-  int stages = (int)(kTailSmem / stage_bytes);
-  if (stages > kTailMaxStages) stages = kTailMaxStages;
-  if (stages < 2) return cudaErrorNotSupported;
-  static cudaError_t attr =
-      cudaFuncSetAttribute(step_tail_staged_kernel<MODE, TMID, TOUT, M, HALF>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem);
+  static cudaError_t attr = cudaFuncSetAttribute(
+      kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemPerSM / 2);
   if (attr != cudaSuccess) return attr;
+  // CTAs per SM as registers allow (at most 3), then the stages that fit
+  // their share of shared memory
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTailThreads,
+                                                                2 * (size_t)stage_bytes);
+  if (e != cudaSuccess) return e;
+  if (per_sm > 3) per_sm = 3;
+  int stages = 0;
+  for (; per_sm >= 1; --per_sm) {
+    stages = (int)(kTailSmemPerSM / (unsigned)per_sm / stage_bytes);
+    if (stages > kTailMaxStages) stages = kTailMaxStages;
+    if ((size_t)stages * stage_bytes > kTailSmemPerSM / 2) stages = (int)(kTailSmemPerSM / 2 / stage_bytes);
+    if (stages >= 2) break;
+  }
+  if (per_sm < 1 || stages < 2) return cudaErrorNotSupported;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t tiles = (((int64_t)1 << s.k0) / kTailPos) * s.nrhs;
-  const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
-  step_tail_staged_kernel<MODE, TMID, TOUT, M, HALF>
-      <<<grid, kTailThreads, (size_t)stages * stage_bytes, st>>>(s, stages, tiles);
+  const int64_t cap = (int64_t)sms * per_sm;
+  const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+  kern<<<grid, kTailThreads, (size_t)stages * stage_bytes, st>>>(s, stages, tiles);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -515,7 +529,7 @@ cudaError_t launch_tail_staged(const StepTail &s, cudaStream_t st) {
 template <typename TMID>
 bool tail_staged_eligible(const StepTail &s) {
   const int64_t e = (int64_t)sizeof(TMID);
-  return s.k0 >= 8 && (reinterpret_cast<uintptr_t>(s.in) & 15) == 0 && (s.N * e) % 16 == 0 &&
+  return s.k0 >= 7 && (reinterpret_cast<uintptr_t>(s.in) & 15) == 0 && (s.N * e) % 16 == 0 &&
          (s.in_rhs_stride * e) % 16 == 0 && s.nrhs >= 1;
 }
 

@@ -61,6 +61,7 @@
 #include "qtt_internal.h"
 #include "step_mma.h"
 #include "tc_common.cuh"
+#include "tf32.cuh"
 
 namespace qtt {
 
@@ -169,15 +170,6 @@ __device__ __forceinline__ void tmem_ldn(uint32_t taddr, float (&v)[NC]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
   for (int e = 0; e < NC; ++e) v[e] = __uint_as_float(r[e]);
-}
-
-// Round to TF32 (10 explicit mantissa bits), nearest even, as the unfused
-// TF32 sweep stores its intermediates: the conversion instruction, its 13
-// low bits cleared.
-__device__ __forceinline__ float tf32_rne(float x) {
-  unsigned r;
-  asm("cvt.rn.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r & 0xffffe000u);
 }
 
 // Byte offset of element (row r, K index kk) of a K-major 128-byte-swizzled
@@ -465,10 +457,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (4 * p < P.r1p) {
               const unsigned kk = tk0 + 4u * (unsigned)p;
               float4 w;
-              w.x = tf32_rne(v[8 * p + i]);
-              w.y = tf32_rne(v[8 * p + 2 + i]);
-              w.z = tf32_rne(v[8 * p + 4 + i]);
-              w.w = tf32_rne(v[8 * p + 6 + i]);
+              w.x = tf32_rn(v[8 * p + i]);
+              w.y = tf32_rn(v[8 * p + 2 + i]);
+              w.z = tf32_rn(v[8 * p + 4 + i]);
+              w.w = tf32_rn(v[8 * p + 6 + i]);
               *reinterpret_cast<float4 *>(trow + (kk >> 5) * 16384u +
                                           ((((kk >> 2) & 7u) ^ x7) << 4)) = w;
             }
@@ -495,8 +487,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int c = 0; c < KM / 2; ++c) {
           if (c < s.r2) {
-            y[0] = tf32_rne(v[2 * c]);
-            y[bit1] = tf32_rne(v[2 * c + 1]);
+            y[0] = tf32_rn(v[2 * c]);
+            y[bit1] = tf32_rn(v[2 * c + 1]);
             y += s.N;
           }
         }
