@@ -370,9 +370,11 @@ __global__ void __launch_bounds__(kThreads, 2) step_tail_kernel(const __grid_con
 // lie 2^(d-m) positions apart; with every SM doing the same, the DRAM serves
 // short runs from many rows at once.  The staged form is persistent: a tile
 // is kTailPos consecutive low positions of one right-hand side, and one
-// producer thread per CTA brings each of its r_{d-m} 2^m runs into shared
-// memory with one bulk copy (kTailPos elements: 512 bytes in FP32, 256 in
-// BF16), `stages` tiles ahead.  Two or three CTAs share an SM (as registers
+// producer thread per CTA brings all of its r_{d-m} 2^m runs into shared
+// memory with one TMA load of a 4-D box (positions, top bits, planes, one
+// right-hand side), `stages` tiles ahead.  The box is a few positions wider
+// than the tile (the next tile's first values, or zeros past the end) so
+// that its rows land 64/T bytes further apart than kTailPos elements.  Two or three CTAs share an SM (as registers
 // allow), so their compute warps, which all wake on the same barrier within
 // a CTA, do not all wait at once.  The compute warps take lane pairs as the
 // plain kernel does, read their values from shared memory and run the same
@@ -400,9 +402,16 @@ __host__ __device__ constexpr unsigned tail_row_bytes() {
   return kTailPos * (unsigned)sizeof(TMID) + 64u / T;
 }
 
+// Box width in elements (kTailPos plus the row pad).
+template <typename TMID, int T>
+__host__ __device__ constexpr unsigned tail_box_x() {
+  return tail_row_bytes<TMID, T>() / (unsigned)sizeof(TMID);
+}
+
 template <int MODE, typename TMID, typename TOUT, int M, bool HALF>
 __global__ void __launch_bounds__(kTailThreads, 2)
-    step_tail_staged_kernel(const __grid_constant__ StepTail s, int stages, int64_t tiles) {
+    step_tail_staged_kernel(const __grid_constant__ CUtensorMap tin,
+                            const __grid_constant__ StepTail s, int stages, int64_t tiles) {
   using namespace tcx;
   static_assert(!HALF || M == 3, "the halving profile has three steps");
   constexpr int P = 1 << M;
@@ -425,7 +434,8 @@ __global__ void __launch_bounds__(kTailThreads, 2)
   }
   __syncthreads();
   volatile int *abort = &abort_flag;
-  const unsigned sbase = su32(tile_smem);
+  const unsigned sbase = (su32(tile_smem) + 127u) & ~127u;  // TMA destinations: 128-byte aligned
+  const unsigned char *tiles_base = tile_smem + (sbase - su32(tile_smem));
 
   if (tid >= kTailCompute) {
     if (tid != kTailCompute) return;
@@ -436,17 +446,9 @@ __global__ void __launch_bounds__(kTailThreads, 2)
       if (n >= stages && !wait_bar(su32(&empty[st]), (unsigned)(n / stages - 1) & 1u, abort)) break;
       const int64_t c = QTT_CK(t / tpr, s.nrhs, 209);
       const int64_t w = t % tpr;
-      const TMID *src = static_cast<const TMID *>(s.in) + c * s.in_rhs_stride + w * kTailPos;
       const unsigned fb = su32(&full[st]);
-      const unsigned dst = sbase + (unsigned)st * stage_bytes;
-      expect_tx(fb, (unsigned)(r0 * P) * kTailPos * (unsigned)sizeof(TMID));
-      for (int a = 0; a < r0; ++a) {
-        const TMID *sa = src + (int64_t)a * s.N;
-#pragma unroll
-        for (int q = 0; q < P; ++q)
-          bulk_load1d(dst + (unsigned)(a * P + q) * row, sa + ((int64_t)q << s.k0),
-                      kTailPos * (unsigned)sizeof(TMID), fb);
-      }
+      expect_tx(fb, stage_bytes);  // the whole box, zeros past the end included
+      tma_load4(sbase + (unsigned)st * stage_bytes, &tin, (int)(w * kTailPos), 0, 0, (int)c, fb);
     }
     if (*abort) {
       volatile int never = 0;
@@ -467,7 +469,7 @@ __global__ void __launch_bounds__(kTailThreads, 2)
       *abort = 1;
       break;
     }
-    const unsigned char *stg = tile_smem + (size_t)st * stage_bytes + (size_t)pl * sizeof(TMID);
+    const unsigned char *stg = tiles_base + (size_t)st * stage_bytes + (size_t)pl * sizeof(TMID);
     float y[kR][T], z[kR][T];
 #pragma unroll
     for (int a = 0; a < kR; ++a)
@@ -495,13 +497,34 @@ cudaError_t launch_tail_staged(const StepTail &s, cudaStream_t st) {
   const int r0 = HALF ? 8 : s.r[0];
   const unsigned stage_bytes = (unsigned)(r0 * 2 * T) * tail_row_bytes<TMID, T>();
   static cudaError_t attr = cudaFuncSetAttribute(
-      kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemPerSM / 2);
+      kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemPerSM / 2 + 128);
   if (attr != cudaSuccess) return attr;
+  // 4-D view of the intermediate: positions below bit k0, the m top bits,
+  // the r_{d-m} planes, the right-hand sides
+  CUtensorMap tin;
+  {
+    const cuuint64_t es = sizeof(TMID);
+    const cuuint64_t dims[4] = {(cuuint64_t)1 << s.k0, (cuuint64_t)(2 * T), (cuuint64_t)r0,
+                                (cuuint64_t)s.nrhs};
+    const cuuint64_t strides[3] = {((cuuint64_t)1 << s.k0) * es, (cuuint64_t)s.N * es,
+                                   (cuuint64_t)s.in_rhs_stride * es};
+    const cuuint32_t box[4] = {tail_box_x<TMID, T>(), (cuuint32_t)(2 * T), (cuuint32_t)r0, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = tcx::tensor_map_encoder();
+    if (!encode ||
+        encode(&tin,
+               sizeof(TMID) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+               4, const_cast<void *>(s.in), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorNotSupported;
+  }
   // CTAs per SM as registers allow (at most 3), then the stages that fit
   // their share of shared memory
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTailThreads,
-                                                                2 * (size_t)stage_bytes);
+                                                                2 * (size_t)stage_bytes + 128);
   if (e != cudaSuccess) return e;
   if (per_sm > 3) per_sm = 3;
   int stages = 0;
@@ -518,7 +541,7 @@ cudaError_t launch_tail_staged(const StepTail &s, cudaStream_t st) {
   const int64_t tiles = (((int64_t)1 << s.k0) / kTailPos) * s.nrhs;
   const int64_t cap = (int64_t)sms * per_sm;
   const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
-  kern<<<grid, kTailThreads, (size_t)stages * stage_bytes, st>>>(s, stages, tiles);
+  kern<<<grid, kTailThreads, (size_t)stages * stage_bytes + 128, st>>>(tin, s, stages, tiles);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -96,6 +96,14 @@ __device__ __forceinline__ void tma_load5(unsigned dst, const CUtensorMap *m, in
       "l"(m), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(mbar)
       : "memory");
 }
+__device__ __forceinline__ void tma_load4(unsigned dst, const CUtensorMap *m, int c0, int c1,
+                                          int c2, int c3, unsigned mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3, %4, %5}], [%6];\n" ::"r"(dst),
+      "l"(m), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+      : "memory");
+}
 __device__ __forceinline__ void tma_store5(const CUtensorMap *m, unsigned src, int c0, int c1,
                                            int c2, int c3, int c4) {
   asm volatile(
