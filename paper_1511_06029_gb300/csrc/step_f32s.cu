@@ -70,17 +70,21 @@ template <int TB>
 __device__ __forceinline__ void chunk_block(const float *sb, const float *sG, const StepLP &s,
                                             int b0, int lane, float *out, int64_t q0,
                                             bool tf32) {
-  float acc[TB][2][4];
+  // acc[t][i][0] holds positions 0, 1 of the lane's four, acc[t][i][1]
+  // positions 2, 3: each multiply-add is a two-lane FP32 FMA (each lane
+  // rounded as fmaf), half the issue slots of scalar FMAs
+  float2 acc[TB][2][2];
 #pragma unroll
   for (int t = 0; t < TB; ++t)
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int m = 0; m < 4; ++m) acc[t][i][m] = 0.0f;
+      for (int m = 0; m < 2; ++m) acc[t][i][m] = make_float2(0.0f, 0.0f);
   const int rpad = s.rout_pad;
 #pragma unroll 4
   for (int kk = 0; kk < 2 * s.rin; ++kk) {
     const float4 v = *reinterpret_cast<const float4 *>(sb + kk * kPC + 4 * lane);
+    const float2 v01 = make_float2(v.x, v.y), v23 = make_float2(v.z, v.w);
     const float4 *g4 = reinterpret_cast<const float4 *>(sG + (kk * rpad + b0) * 2);
 #pragma unroll
     for (int t2 = 0; t2 < TB / 2; ++t2) {
@@ -91,12 +95,10 @@ __device__ __forceinline__ void chunk_block(const float *sb, const float *sG, co
       for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-          float *a = acc[2 * t2 + h][i];
-          const float c = gg[2 * h + i];
-          a[0] = fmaf(c, v.x, a[0]);
-          a[1] = fmaf(c, v.y, a[1]);
-          a[2] = fmaf(c, v.z, a[2]);
-          a[3] = fmaf(c, v.w, a[3]);
+          float2 *a = acc[2 * t2 + h][i];
+          const float2 c = make_float2(gg[2 * h + i], gg[2 * h + i]);
+          a[0] = __ffma2_rn(c, v01, a[0]);
+          a[1] = __ffma2_rn(c, v23, a[1]);
         }
     }
   }
@@ -111,7 +113,7 @@ __device__ __forceinline__ void chunk_block(const float *sb, const float *sG, co
     float *ob = out + (int64_t)b * s.N + p0;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-      float4 o = make_float4(acc[t][i][0], acc[t][i][1], acc[t][i][2], acc[t][i][3]);
+      float4 o = make_float4(acc[t][i][0].x, acc[t][i][0].y, acc[t][i][1].x, acc[t][i][1].y);
       if (tf32) {
         o.x = tf32_round(o.x);
         o.y = tf32_round(o.y);
