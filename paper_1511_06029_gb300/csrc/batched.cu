@@ -131,32 +131,42 @@ __device__ __forceinline__ void rank_block(const float *sm, const float *sG, int
                                            float *out, int64_t N, int64_t q0, int k,
                                            int64_t npairs, bool round_out) {
 
-  float acc[TB][2][TN];
+  // acc2[t][m] = (output i = 0, output i = 1) of rank b0 + t at pair m: the
+  // two coefficients (b, 0), (b, 1) sit side by side in the core row, so
+  // each multiply-add is one two-lane FP32 FMA (each lane rounded as fmaf)
+  float2 acc2[TB][TN];
 #pragma unroll
   for (int t = 0; t < TB; ++t)
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int m = 0; m < TN; ++m) acc[t][i][m] = 0.0f;
+    for (int m = 0; m < TN; ++m) acc2[t][m] = make_float2(0.0f, 0.0f);
 #pragma unroll 4
   for (int kk = 0; kk < 2 * rin; ++kk) {
     float v[TN];
     load_v<TN>(sm + (size_t)kk * npair_chunk + TN * lane, v);
+    float2 vv[TN];
+#pragma unroll
+    for (int m = 0; m < TN; ++m) vv[m] = make_float2(v[m], v[m]);
     const float4 *g4 = reinterpret_cast<const float4 *>(sG + (kk * rpad + b0) * 2);
 #pragma unroll
     for (int t2 = 0; t2 < TB / 2; ++t2) {
       // ranks past the padded row contribute nothing (rpad is a multiple of 4)
       const float4 g = b0 + 2 * t2 < rpad ? g4[t2] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float gg[4] = {g.x, g.y, g.z, g.w};
+      const float2 gp[2] = {make_float2(g.x, g.y), make_float2(g.z, g.w)};
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-          for (int m = 0; m < TN; ++m)
-            acc[2 * t2 + h][i][m] = fmaf(gg[2 * h + i], v[m], acc[2 * t2 + h][i][m]);
+        for (int m = 0; m < TN; ++m)
+          acc2[2 * t2 + h][m] = __ffma2_rn(gp[h], vv[m], acc2[2 * t2 + h][m]);
     }
   }
+  float acc[TB][2][TN];
+#pragma unroll
+  for (int t = 0; t < TB; ++t)
+#pragma unroll
+    for (int m = 0; m < TN; ++m) {
+      acc[t][0][m] = acc2[t][m].x;
+      acc[t][1][m] = acc2[t][m].y;
+    }
   if (round_out) {
 #pragma unroll
     for (int t = 0; t < TB; ++t)

@@ -70,36 +70,31 @@ template <int TB>
 __device__ __forceinline__ void chunk_block(const float *sb, const float *sG, const StepLP &s,
                                             int b0, int lane, float *out, int64_t q0,
                                             bool tf32) {
-  // acc[t][i][0] holds positions 0, 1 of the lane's four, acc[t][i][1]
-  // positions 2, 3: each multiply-add is a two-lane FP32 FMA (each lane
-  // rounded as fmaf), half the issue slots of scalar FMAs
-  float2 acc[TB][2][2];
+  // acc[t][m] = (output i = 0, output i = 1) of rank b0 + t at the lane's
+  // pair m: the coefficients (b, 0), (b, 1) sit side by side in the core
+  // row, so each multiply-add is one two-lane FP32 FMA (each lane rounded
+  // as fmaf) with the input value in both lanes
+  float2 acc[TB][4];
 #pragma unroll
   for (int t = 0; t < TB; ++t)
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int m = 0; m < 2; ++m) acc[t][i][m] = make_float2(0.0f, 0.0f);
+    for (int m = 0; m < 4; ++m) acc[t][m] = make_float2(0.0f, 0.0f);
   const int rpad = s.rout_pad;
 #pragma unroll 4
   for (int kk = 0; kk < 2 * s.rin; ++kk) {
     const float4 v = *reinterpret_cast<const float4 *>(sb + kk * kPC + 4 * lane);
-    const float2 v01 = make_float2(v.x, v.y), v23 = make_float2(v.z, v.w);
+    const float2 vv[4] = {make_float2(v.x, v.x), make_float2(v.y, v.y), make_float2(v.z, v.z),
+                          make_float2(v.w, v.w)};
     const float4 *g4 = reinterpret_cast<const float4 *>(sG + (kk * rpad + b0) * 2);
 #pragma unroll
     for (int t2 = 0; t2 < TB / 2; ++t2) {
       // ranks past the padded row contribute nothing (rpad is a multiple of 4)
       const float4 g = b0 + 2 * t2 < rpad ? g4[t2] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float gg[4] = {g.x, g.y, g.z, g.w};
+      const float2 gp[2] = {make_float2(g.x, g.y), make_float2(g.z, g.w)};
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          float2 *a = acc[2 * t2 + h][i];
-          const float2 c = make_float2(gg[2 * h + i], gg[2 * h + i]);
-          a[0] = __ffma2_rn(c, v01, a[0]);
-          a[1] = __ffma2_rn(c, v23, a[1]);
-        }
+        for (int m = 0; m < 4; ++m) acc[2 * t2 + h][m] = __ffma2_rn(gp[h], vv[m], acc[2 * t2 + h][m]);
     }
   }
   const int64_t bit = (int64_t)1 << s.k, low = bit - 1, npairs = s.N >> 1;
@@ -113,7 +108,8 @@ __device__ __forceinline__ void chunk_block(const float *sb, const float *sG, co
     float *ob = out + (int64_t)b * s.N + p0;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-      float4 o = make_float4(acc[t][i][0].x, acc[t][i][0].y, acc[t][i][1].x, acc[t][i][1].y);
+      float4 o = i ? make_float4(acc[t][0].y, acc[t][1].y, acc[t][2].y, acc[t][3].y)
+                   : make_float4(acc[t][0].x, acc[t][1].x, acc[t][2].x, acc[t][3].x);
       if (tf32) {
         o.x = tf32_round(o.x);
         o.y = tf32_round(o.y);

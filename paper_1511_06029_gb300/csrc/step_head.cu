@@ -38,6 +38,18 @@ __device__ __forceinline__ float round_mode(float v) {
   if (MODE == LP_BF16) return __bfloat162float(__float2bfloat16_rn(v));
   return v;
 }
+// Two multiply-adds as one two-lane FP32 FMA, each lane rounded as fmaf:
+// (z0, z1) += (g.x, g.y) v, and (z0, z1) += g (v0, v1).
+__device__ __forceinline__ void fma_pair(float2 g, float v, float &z0, float &z1) {
+  const float2 r = __ffma2_rn(g, make_float2(v, v), make_float2(z0, z1));
+  z0 = r.x;
+  z1 = r.y;
+}
+__device__ __forceinline__ void fma_both(float g, float v0, float v1, float &z0, float &z1) {
+  const float2 r = __ffma2_rn(make_float2(g, g), make_float2(v0, v1), make_float2(z0, z1));
+  z0 = r.x;
+  z1 = r.y;
+}
 __device__ __forceinline__ float to_f(double v) { return (float)v; }
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -136,13 +148,12 @@ __global__ void __launch_bounds__(kThreads, 2) step_head_kernel(const __grid_con
 #pragma unroll
           for (int b = 0; b < kR; ++b) {
             if (b >= rout) break;
-            const float g0 = s.G[k][2 * a + j][b][0], g1 = s.G[k][2 * a + j][b][1];
+            const float2 g = make_float2(s.G[k][2 * a + j][b][0], s.G[k][2 * a + j][b][1]);
 #pragma unroll
             for (int q = 0; q < T; ++q) {
               if (((q >> k) & 1) != 0) continue;  // q = pair base (bit k clear)
               const float v = y[a][q | (j << k)];
-              z[b][q] = fmaf(g0, v, z[b][q]);
-              z[b][q | (1 << k)] = fmaf(g1, v, z[b][q | (1 << k)]);
+              fma_pair(g, v, z[b][q], z[b][q | (1 << k)]);
             }
           }
         }
@@ -163,7 +174,9 @@ __global__ void __launch_bounds__(kThreads, 2) step_head_kernel(const __grid_con
             if (b >= rout) break;
             const float g = h ? s.G[k][2 * a + j][b][1] : s.G[k][2 * a + j][b][0];
 #pragma unroll
-            for (int q = 0; q < T; ++q) z[b][q] = fmaf(g, j == h ? y[a][q] : other[q], z[b][q]);
+            for (int q = 0; q < T; q += 2)
+              fma_both(g, j == h ? y[a][q] : other[q], j == h ? y[a][q + 1] : other[q + 1],
+                       z[b][q], z[b][q + 1]);
           }
         }
       }
@@ -281,13 +294,12 @@ __device__ __forceinline__ void tail_math(const StepTail &s, int h, float (&y)[k
 #pragma unroll
           for (int b = 0; b < kR; ++b) {
             if (b >= rout) break;
-            const float g0 = s.G[k][2 * a + j][b][0], g1 = s.G[k][2 * a + j][b][1];
+            const float2 g = make_float2(s.G[k][2 * a + j][b][0], s.G[k][2 * a + j][b][1]);
 #pragma unroll
             for (int q = 0; q < T; ++q) {
-              if (((q >> k) & 1) != 0) continue;
+              if (((q >> k) & 1) != 0) continue;  // q = pair base (bit k clear)
               const float v = y[a][q | (j << k)];
-              z[b][q] = fmaf(g0, v, z[b][q]);
-              z[b][q | (1 << k)] = fmaf(g1, v, z[b][q | (1 << k)]);
+              fma_pair(g, v, z[b][q], z[b][q | (1 << k)]);
             }
           }
         }
@@ -310,7 +322,9 @@ __device__ __forceinline__ void tail_math(const StepTail &s, int h, float (&y)[k
             if (b >= rout) break;
             const float g = h ? s.G[k][2 * a + j][b][1] : s.G[k][2 * a + j][b][0];
 #pragma unroll
-            for (int q = 0; q < T; ++q) z[b][q] = fmaf(g, j == h ? y[a][q] : other[q], z[b][q]);
+            for (int q = 0; q < T; q += 2)
+              fma_both(g, j == h ? y[a][q] : other[q], j == h ? y[a][q + 1] : other[q + 1],
+                       z[b][q], z[b][q + 1]);
           }
         }
       }
