@@ -20,6 +20,8 @@
 // launches.
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include "checked.cuh"
 #include "qtt_internal.h"
 #include "step_lp.h"
@@ -535,20 +537,29 @@ cudaError_t launch_tail_staged(const StepTail &s, cudaStream_t st) {
       return cudaErrorNotSupported;
   }
   // CTAs per SM as registers allow (at most 3), then the stages that fit
-  // their share of shared memory
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTailThreads,
-                                                                2 * (size_t)stage_bytes + 128);
-  if (e != cudaSuccess) return e;
-  if (per_sm > 3) per_sm = 3;
-  int stages = 0;
-  for (; per_sm >= 1; --per_sm) {
-    stages = (int)(kTailSmemPerSM / (unsigned)per_sm / stage_bytes);
-    if (stages > kTailMaxStages) stages = kTailMaxStages;
-    if ((size_t)stages * stage_bytes > kTailSmemPerSM / 2) stages = (int)(kTailSmemPerSM / 2 / stage_bytes);
-    if (stages >= 2) break;
+  // their share of shared memory; worked out once per rank r_{d-m} (the
+  // occupancy query costs more host time than a small tail's kernel)
+  static std::atomic<int> plan_for_r0[kR + 1];
+  int per_sm = 0, stages = 0;
+  const int cached = plan_for_r0[r0].load(std::memory_order_relaxed);
+  if (cached) {
+    per_sm = cached >> 8;
+    stages = cached & 255;
+  } else {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, kern, kTailThreads, 2 * (size_t)stage_bytes + 128);
+    if (e != cudaSuccess) return e;
+    if (per_sm > 3) per_sm = 3;
+    for (; per_sm >= 1; --per_sm) {
+      stages = (int)(kTailSmemPerSM / (unsigned)per_sm / stage_bytes);
+      if (stages > kTailMaxStages) stages = kTailMaxStages;
+      if ((size_t)stages * stage_bytes > kTailSmemPerSM / 2)
+        stages = (int)(kTailSmemPerSM / 2 / stage_bytes);
+      if (stages >= 2) break;
+    }
+    if (per_sm < 1 || stages < 2) return cudaErrorNotSupported;
+    plan_for_r0[r0].store(per_sm << 8 | stages, std::memory_order_relaxed);
   }
-  if (per_sm < 1 || stages < 2) return cudaErrorNotSupported;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
