@@ -547,14 +547,18 @@ class ApplyRun:
         self.op.apply(self.x, out=self.y, compute=self.compute, stream=self.stream)
 
     def e2e_step(self):
-        self.xd.copy_(self.xh, non_blocking=True)
         if self.spec.get("plan"):
+            # the recorded graph works on fixed device buffers: copy around it
+            self.xd.copy_(self.xh, non_blocking=True)
             if getattr(self, "_plan_e2e", None) is None:
                 self._plan_e2e = self.op.plan(self.xd, self.yd, compute=self.compute)
             self._plan_e2e.run()
+            self.yh.copy_(self.yd, non_blocking=True)
         else:
-            self.op.apply(self.xd, out=self.yd, compute=self.compute)
-        self.yh.copy_(self.yd, non_blocking=True)
+            # the C-ABI call with host buffers (qtt_apply_host): the copies in
+            # and out are the library's, overlapped with the applies chunk by
+            # chunk when there are several right-hand sides
+            self.op.apply_host(self.xh, out=self.yh, compute=self.compute)
 
     def e2e_bytes(self):
         b = self.x.numel() * self.x.element_size()

@@ -149,6 +149,31 @@ qtt_status qtt_apply(const qtt_op *A, const void *x, void *y, int64_t nrhs,
                      int64_t ld, qtt_dtype io_dtype, qtt_dtype compute,
                      void *stream);
 
+/* qtt_apply_host -- qtt_apply with x and y in HOST memory: x goes to the
+ * device, the apply runs, y comes back, all ordered on `stream`.  With more
+ * than one chunk the right-hand sides pass through two device staging slots
+ * so that the copy of chunk i+1 in, the apply of chunk i and the copy of
+ * chunk i-1 out overlap (the copies on two streams the library keeps per
+ * device, ordered by events; the applies on `stream`).
+ *   x_host, y_host : host pointers, N x nrhs, leading dimension ld, element
+ *                    type io_dtype (QTT_F64, QTT_F32 or QTT_BF16); they must
+ *                    not overlap.  Page-locked memory (cudaHostAlloc,
+ *                    cudaHostRegister) lets the copies run asynchronously;
+ *                    pageable memory works, but then the copies block the
+ *                    calling thread and nothing overlaps.
+ *   nrhs, ld, io_dtype, compute : as for qtt_apply.
+ *   chunk  : right-hand sides per chunk; 0 lets the library choose (a
+ *            quarter of nrhs, at most 1 GiB of staging for x and y).
+ *   stream : cudaStream_t; the call returns once the work is queued, and
+ *            y_host holds the result when the stream has drained.
+ * Staging (2 slots x chunk x N x element size, for x and y) comes from the
+ * library's stream-ordered pool.  Every right-hand side's result is bitwise
+ * what qtt_apply gives it.  Rows ld > N of y_host keep their padding.
+ * Errors: as qtt_apply; QTT_ERR_UNSUPPORTED for a device index above 63. */
+qtt_status qtt_apply_host(const qtt_op *A, const void *x_host, void *y_host,
+                          int64_t nrhs, int64_t ld, qtt_dtype io_dtype,
+                          qtt_dtype compute, int64_t chunk, void *stream);
+
 /* ------------------------------------------------------------ fusion plan */
 /* How an apply in each arithmetic runs -- which steps are merged into one
  * launch and on which kernels -- is a per-operator plan; the paper has no

@@ -41,6 +41,7 @@ SIGNATURES = {
     "qtt_op_rank": (_I, [_P, _I]),
     "qtt_op_flops": (_D, [_P]),
     "qtt_apply": (_I, [_P, _P, _P, _L, _L, _I, _I, _P]),
+    "qtt_apply_host": (_I, [_P, _P, _P, _L, _L, _I, _I, _L, _P]),
     "qtt_residual": (_I, [_P, _D, _P, _P, _P, _L, _L, _P]),
     "qtt_apply_noalloc": (_I, [_P, _P, _P, _L, _L, _P]),
     "qtt_apply_tt_size": (_I, [_P, _P, ctypes.POINTER(_L)]),
@@ -166,10 +167,11 @@ def _io_name(t) -> str:
     return m[t.dtype]
 
 
-def _block(t, N, what):
+def _block(t, N, what, host=False):
     """(nrhs, N) view with unit inner stride -> (nrhs, ld)."""
-    if not t.is_cuda:
-        raise QTTError(QTT_ERR_INVALID_ARG, what, "tensor must be on the GPU")
+    if t.is_cuda == host:
+        raise QTTError(QTT_ERR_INVALID_ARG, what,
+                       "tensor must be in host memory" if host else "tensor must be on the GPU")
     if t.dim() == 1:
         if t.shape[0] != N or t.stride(0) != 1:
             raise QTTError(QTT_ERR_INVALID_ARG, what, "bad vector shape/stride")
@@ -270,6 +272,32 @@ class Operator:
                                         ctypes.c_void_p(out.data_ptr()), nrhs, ld,
                                         DTYPES[io], DTYPES[compute], _stream_handle(stream)),
                "qtt_apply")
+        return out
+
+    def apply_host(self, x, out=None, compute: str = "f64", chunk: int = 0, stream=None):
+        """y = A x with x and y in host memory (qtt_apply_host): the copies to
+        and from the device are part of the call, overlapped with the applies
+        chunk by chunk.  x: (N,) or (nrhs, N) CPU tensor of float64 / float32 /
+        bfloat16, best page-locked (x.pin_memory()); y has the same dtype and
+        shape (a page-locked tensor is made when `out` is not given).  The call
+        returns once the work is queued on `stream`; synchronise the stream
+        before reading y."""
+        torch = _torch()
+        nrhs, ld = _block(x, self.N, "qtt_apply_host", host=True)
+        if out is None:
+            out = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+        n2, ld2 = _block(out, self.N, "qtt_apply_host", host=True)
+        if n2 != nrhs or out.dtype != x.dtype:
+            raise QTTError(QTT_ERR_INVALID_ARG, "qtt_apply_host", "out shape/dtype mismatch")
+        if ld2 != ld:
+            raise QTTError(QTT_ERR_INVALID_ARG, "qtt_apply_host",
+                           "x and out need the same row stride")
+        io = _io_name(x)
+        _check(load_library().qtt_apply_host(self.handle, ctypes.c_void_p(x.data_ptr()),
+                                             ctypes.c_void_p(out.data_ptr()), nrhs, ld,
+                                             DTYPES[io], DTYPES[compute], int(chunk),
+                                             _stream_handle(stream)),
+               "qtt_apply_host")
         return out
 
     def apply_tt(self, b_ranks, b_cores, out=None, stream=None):
