@@ -494,6 +494,19 @@ qtt_status qtt_batch_create(qtt_batch **out, int nops, const qtt_op *const *ops,
                             void *stream);
 /* Launch the captured graph on `stream` (asynchronous). */
 qtt_status qtt_batch_run(qtt_batch *B, void *stream);
+/* qtt_batch_run_host -- the same run with every operator's x and y in HOST
+ * memory: x_host[i] and y_host[i] are N_i x nrhs_i FP32 arrays, compact
+ * (leading dimension N_i = 2^d_i), best page-locked.  The batch's device
+ * vectors (given at creation) serve as the staging: the wave operators'
+ * inputs are copied in, the waves run, their outputs are copied out while
+ * the directly applied operators run, each of those with its input copied
+ * in ahead and its output copied out behind it (two copy streams the
+ * library keeps per device, ordered by events; the applies on `stream`).
+ * Returns once queued; y_host is complete when `stream` has drained.  The
+ * results are bitwise qtt_batch_run's.
+ * Errors: QTT_ERR_INVALID_ARG (NULL arrays or vectors), QTT_ERR_CUDA. */
+qtt_status qtt_batch_run_host(qtt_batch *B, const float *const *x_host,
+                              float *const *y_host, void *stream);
 /* Synchronise `stream`; QTT_ERR_TIMEOUT if a dependency wait in the last
  * runs gave up (the status word is then cleared). */
 qtt_status qtt_batch_status(qtt_batch *B, void *stream);

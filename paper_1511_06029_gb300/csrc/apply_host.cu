@@ -27,9 +27,7 @@ namespace {
 constexpr int kMaxDevices = 64;
 constexpr size_t kStagingBudget = (size_t)1 << 30;  // both slots, x and y
 
-struct CopyStreams {
-  cudaStream_t in = nullptr, out = nullptr;
-};
+}  // namespace
 
 // The copy streams of the current device, created on first use and kept
 // until the process ends.
@@ -38,24 +36,26 @@ qtt_status copy_streams(CopyStreams *cs) {
   static CopyStreams per_device[kMaxDevices];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "qtt_apply_host: cudaGetDevice");
+  if (e != cudaSuccess) return cuda_fail(e, "host copy streams: cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices)
-    return fail(QTT_ERR_UNSUPPORTED, "qtt_apply_host: device index above 63");
+    return fail(QTT_ERR_UNSUPPORTED, "host copy streams: device index above 63");
   std::lock_guard<std::mutex> lock(mu);
   CopyStreams &c = per_device[dev];
   if (!c.in) {
     e = cudaStreamCreateWithFlags(&c.in, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return cuda_fail(e, "qtt_apply_host: copy stream");
+    if (e != cudaSuccess) return cuda_fail(e, "host copy streams: cudaStreamCreate");
     e = cudaStreamCreateWithFlags(&c.out, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
       cudaStreamDestroy(c.in);
       c.in = nullptr;
-      return cuda_fail(e, "qtt_apply_host: copy stream");
+      return cuda_fail(e, "host copy streams: cudaStreamCreate");
     }
   }
   *cs = c;
   return QTT_OK;
 }
+
+namespace {
 
 size_t io_size(qtt_dtype t) { return t == QTT_F64 ? 8 : (t == QTT_BF16 ? 2 : 4); }
 

@@ -455,6 +455,10 @@ struct qtt_batch {
   // a wave: TF32 ones whose apply runs tcgen05 step pairs, FP32 ones with
   // d >= kDirectMinD
   std::vector<int> direct_ops;
+  // qtt_batch_run_host: events ordering the copies against the applies
+  // (created on its first call; [0] start, [1] wave inputs in, [2] waves
+  // done, [3] copies out done, then one pair per direct operator)
+  std::vector<cudaEvent_t> host_events;
 };
 
 namespace qtt {
@@ -821,6 +825,89 @@ qtt_status qtt_batch_run(qtt_batch *B, void *stream) {
   return QTT_OK;
 }
 
+qtt_status qtt_batch_run_host(qtt_batch *B, const float *const *x_host, float *const *y_host,
+                              void *stream) {
+  if (!B || !B->exec) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_run_host: no batch");
+  if (!x_host || !y_host) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_run_host: NULL array");
+  const size_t nops = B->ops.size();
+  for (size_t i = 0; i < nops; ++i)
+    if (!x_host[i] || !y_host[i])
+      return fail(QTT_ERR_INVALID_ARG, "qtt_batch_run_host: NULL vector");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CopyStreams cs;
+  qtt_status s = copy_streams(&cs);
+  if (s != QTT_OK) return s;
+  cudaError_t e = cudaSuccess;
+  const size_t nev = 4 + 2 * B->direct_ops.size();
+  while (B->host_events.size() < nev && e == cudaSuccess) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) B->host_events.push_back(ev);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "qtt_batch_run_host: events");
+  cudaEvent_t *ev = B->host_events.data();
+  std::vector<char> direct(nops, 0);
+  for (int i : B->direct_ops) direct[i] = 1;
+  // host rows are compact (leading dimension N); the batch's device vectors
+  // have leading dimension ld
+  auto copy_in = [&](size_t i) {
+    const size_t row = ((size_t)1 << B->ops[i]->d) * sizeof(float);
+    return cudaMemcpy2DAsync(const_cast<float *>(B->x[i]), (size_t)B->ld[i] * sizeof(float),
+                             x_host[i], row, row, (size_t)B->nrhs[i], cudaMemcpyHostToDevice,
+                             cs.in);
+  };
+  auto copy_out = [&](size_t i) {
+    const size_t row = ((size_t)1 << B->ops[i]->d) * sizeof(float);
+    return cudaMemcpy2DAsync(y_host[i], row, B->y[i], (size_t)B->ld[i] * sizeof(float), row,
+                             (size_t)B->nrhs[i], cudaMemcpyDeviceToHost, cs.out);
+  };
+  // nothing starts before the work already on the caller's stream (an
+  // earlier run may still read x or write y)
+  e = cudaEventRecord(ev[0], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.in, ev[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.out, ev[0], 0);
+  // the waves' inputs, the waves, their outputs
+  for (size_t i = 0; i < nops && e == cudaSuccess; ++i)
+    if (!direct[i]) e = copy_in(i);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], cs.in);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[1], 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(B->exec, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.out, ev[2], 0);
+  for (size_t i = 0; i < nops && e == cudaSuccess; ++i)
+    if (!direct[i]) e = copy_out(i);
+  // each direct operator: its input in, its apply, its output out
+  for (size_t j = 0; j < B->direct_ops.size() && e == cudaSuccess && s == QTT_OK; ++j) {
+    const int i = B->direct_ops[j];
+    cudaEvent_t in_done = ev[4 + 2 * j], applied = ev[5 + 2 * j];
+    e = copy_in(i);
+    if (e == cudaSuccess) e = cudaEventRecord(in_done, cs.in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, in_done, 0);
+    if (e != cudaSuccess) break;
+    s = apply_lp(B->ops[i], B->compute, B->x[i], QTT_F32, B->y[i], QTT_F32, B->nrhs[i],
+                 B->ld[i], st, LpEpilogue{});
+    if (s != QTT_OK) break;
+    e = cudaEventRecord(applied, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs.out, applied, 0);
+    if (e == cudaSuccess) e = copy_out(i);
+  }
+  // the caller's stream ends after the last copy out (also after an error)
+  cudaError_t e2 = cudaEventRecord(ev[3], cs.out);
+  if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st, ev[3], 0);
+  if (e2 != cudaSuccess) {
+    cudaStreamSynchronize(cs.in);
+    cudaStreamSynchronize(cs.out);
+  }
+  for (const qtt_op *A : B->ops) note_use(A, st);
+  if (!B->last_run && cudaEventCreateWithFlags(&B->last_run, cudaEventDisableTiming) != cudaSuccess)
+    return fail(QTT_ERR_CUDA, "qtt_batch_run_host: event");
+  cudaEventRecord(B->last_run, st);
+  if (s != QTT_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(e, "qtt_batch_run_host");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "qtt_batch_run_host: final ordering");
+  return QTT_OK;
+}
+
 qtt_status qtt_batch_selftest_timeout(qtt_batch *B, double seconds, void *stream) {
   if (!B || B->waves.empty()) return fail(QTT_ERR_INVALID_ARG, "qtt_batch_selftest_timeout: no batch");
   if (!(seconds > 0.0 && seconds <= 10.0))
@@ -940,6 +1027,7 @@ qtt_status qtt_batch_destroy(qtt_batch *B) {
   free_waves(B);
   release(B, {B->scratch, B->d_next, B->d_status});
   if (B->last_run) cudaEventDestroy(B->last_run);
+  for (cudaEvent_t ev : B->host_events) cudaEventDestroy(ev);  // released when complete
   delete B;
   return QTT_OK;
 }

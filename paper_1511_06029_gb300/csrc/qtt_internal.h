@@ -78,6 +78,14 @@ inline bool decode_plan(int code, ApplyPlan *p) {
 void note_use(const qtt_op *A, cudaStream_t stream);
 // QTT_ERR_INVALID_ARG unless the current device is the one A lives on.
 qtt_status check_device(const qtt_op *A, const char *where);
+
+// Two streams per device for host <-> device copies that overlap the work
+// on the caller's stream (qtt_apply_host, qtt_batch_run_host): created on
+// first use, kept until the process ends.
+struct CopyStreams {
+  cudaStream_t in = nullptr, out = nullptr;
+};
+qtt_status copy_streams(CopyStreams *cs);
 // Commit the static array of qtt_apply_noalloc on the current device (loads
 // its module); done by qtt_create, which allocates anyway.
 qtt_status noalloc_prepare();

@@ -74,6 +74,7 @@ SIGNATURES = {
     "qtt_sync_status": (_I, [_P]),
     "qtt_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _P, _P, _P, _P, _I, ctypes.c_size_t, _P]),
     "qtt_batch_run": (_I, [_P, _P]),
+    "qtt_batch_run_host": (_I, [_P, _P, _P, _P]),
     "qtt_batch_status": (_I, [_P, _P]),
     "qtt_batch_selftest_timeout": (_I, [_P, _D, _P]),
     "qtt_batch_set_variant": (_I, [_P, _I, _P]),
@@ -658,6 +659,28 @@ class Batch:
 
     def run(self, stream=None):
         _check(load_library().qtt_batch_run(self._h, _stream_handle(stream)), "qtt_batch_run")
+
+    def run_host(self, xs_host, ys_host, stream=None):
+        """The run with every operator's vectors in host memory
+        (qtt_batch_run_host): xs_host / ys_host are lists of contiguous FP32
+        CPU tensors shaped like the batch's xs / ys, best page-locked; the
+        copies overlap the run.  Returns once queued on `stream`."""
+        torch = _torch()
+        ops, xs, _ = self._keep
+        if not (len(xs_host) == len(ys_host) == len(ops)):
+            raise QTTError(QTT_ERR_INVALID_ARG, "qtt_batch_run_host", "one x and y per operator")
+        for x, xh, yh in zip(xs, xs_host, ys_host):
+            for t in (xh, yh):
+                if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() \
+                        or t.numel() != x.numel():
+                    raise QTTError(QTT_ERR_INVALID_ARG, "qtt_batch_run_host",
+                                   "host vectors: contiguous FP32 CPU tensors of nrhs x N")
+        n = len(ops)
+        xp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in xs_host])
+        yp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in ys_host])
+        self._host_keep = (xs_host, ys_host)
+        _check(load_library().qtt_batch_run_host(self._h, ctypes.cast(xp, _P), ctypes.cast(yp, _P),
+                                                 _stream_handle(stream)), "qtt_batch_run_host")
 
     def status(self, stream=None):
         _check(load_library().qtt_batch_status(self._h, _stream_handle(stream)), "qtt_batch_status")

@@ -86,6 +86,7 @@ def test_apply_rejects_null_operator(lib):
     n = ctypes.c_int64(-1)
     assert lib.qtt_apply_tt_size(None, None, ctypes.byref(n)) == qtt.QTT_ERR_INVALID_ARG
     assert lib.qtt_apply_tt(None, None, None, None, None) == qtt.QTT_ERR_INVALID_ARG
+    assert lib.qtt_batch_run_host(None, None, None, None) == qtt.QTT_ERR_INVALID_ARG
     assert lib.qtt_apply_host(None, None, None, 1, 4, 0, 0, 0, None) == qtt.QTT_ERR_INVALID_ARG
 
 

@@ -164,3 +164,38 @@ def test_batch_odd_leading_dimension(qtt):
     B.close()
     for o in ops:
         o.close()
+
+
+@pytest.mark.parametrize("compute,d_range", [("f32", (12, 17)), ("tf32", (6, 13))])
+def test_batch_run_host_is_bitwise_the_device_run(qtt, compute, d_range):
+    """qtt_batch_run_host (vectors in page-locked host memory, copies
+    overlapping the run) gives every operator bitwise what qtt_batch_run
+    gives it; the batches hold both wave operators and directly applied ones
+    (FP32: d >= 16; TF32: operators with a tcgen05 pair), and two host runs
+    in a row agree."""
+    import torch
+    items = _batch(12, 21, d_range=d_range, r_range=(3, 32), rhs_range=(1, 3))
+    datas, ops, xs, ys, xh = _setup(qtt, items, compute)
+    B = qtt.Batch(ops, xs, ys, compute=compute)
+    info = B.info()
+    assert info["direct_ops"] >= 1 and info["waves"] >= 1, info
+    B.run()
+    B.status()
+    torch.cuda.synchronize()
+    ref = [y.cpu().clone() for y in ys]
+    xs_host = [torch.from_numpy(x.astype(np.float32)).pin_memory() for x in xh]
+    for _ in range(2):
+        for y in ys:
+            y.fill_(float("nan"))
+        ys_host = [torch.full(x.shape, float("nan"), dtype=torch.float32).pin_memory()
+                   for x in xs_host]
+        B.run_host(xs_host, ys_host)
+        B.status()
+        torch.cuda.synchronize()
+        for a, b in zip(ys_host, ref):
+            assert torch.equal(a.view(torch.int32), b.contiguous().view(torch.int32))
+    with pytest.raises(qtt.QTTError):
+        B.run_host(xs_host[:-1], ys_host[:-1])
+    B.close()
+    for o in ops:
+        o.close()
