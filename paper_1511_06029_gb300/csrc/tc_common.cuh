@@ -124,16 +124,6 @@ __device__ __forceinline__ void expect_tx(unsigned mbar, unsigned bytes) {
                "r"(bytes)
                : "memory");
 }
-// 1-D bulk copy of `bytes` from global to shared memory (both addresses
-// 16-byte aligned, bytes a multiple of 16), counted as transaction bytes on
-// the mbarrier at `mbar`.
-__device__ __forceinline__ void bulk_load1d(unsigned dst, const void *src, unsigned bytes,
-                                            unsigned mbar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(mbar)
-      : "memory");
-}
 __device__ __forceinline__ void bulk_commit() {
   asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
 }

@@ -1,8 +1,8 @@
 """Multi-step launches against one launch per step.
 
 The head kernel (steps 0 .. m-1 in registers, ranks <= 8) and the tail
-kernel (the last steps, ranks <= 8, writing y; plain loads below 256 low
-positions, bulk-copy staging from there) follow the one-step kernel's
+kernel (the last steps, ranks <= 8, writing y; plain loads below 128 low
+positions, TMA-staged tiles from there) follow the one-step kernel's
 numerics step by step, so their result must be bitwise the unfused one in
 every reduced precision and for every input and output type.  The
 unfused reference runs in a child process with QTT_NO_FUSION=1 (the switch
@@ -38,7 +38,7 @@ CASES = [
     ([1, 2, 4, 8, 12, 12, 8, 4, 2, 1], 2),   # head, three single steps, tail of 3
     ([1, 4, 8, 12, 6, 3, 1], 3),    # head of 2, two single steps, tail of 2
 ]
-# 2^(d-m) >= 256 low positions: the staged (bulk-copy) tail kernel; both
+# 2^(d-m) >= 128 low positions: the staged (TMA) tail kernel; both
 # sides without tensor cores
 STAGED = [
     ([1, 2, 4, 8, 8, 8, 8, 8, 8, 8, 4, 2, 1], 2),       # d = 12, tail 8-4-2-1
