@@ -61,6 +61,11 @@ static int host_checks(void) {
   CHECK(strcmp(qtt_status_string(QTT_OK), "ok") == 0, "status string of QTT_OK");
   CHECK(qtt_apply(NULL, NULL, NULL, 1, 1, QTT_F64, QTT_F64, NULL) == QTT_ERR_INVALID_ARG,
         "qtt_apply accepted a NULL operator");
+  CHECK(qtt_apply_host(NULL, NULL, NULL, 1, 1, QTT_F64, QTT_F64, 0, NULL) ==
+            QTT_ERR_INVALID_ARG,
+        "qtt_apply_host accepted a NULL operator");
+  CHECK(qtt_batch_run_host(NULL, NULL, NULL, NULL) == QTT_ERR_INVALID_ARG,
+        "qtt_batch_run_host accepted a NULL batch");
   CHECK(strlen(qtt_last_error()) > 0, "no message after a failing call");
   return 0;
 }
